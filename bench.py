@@ -1,0 +1,351 @@
+"""Benchmark of the PFAC scan on one GB300 (or N GPUs, one process each).
+
+Workload (one step = one scan of the whole text): the genome-scale single scan —
+256 Mi bases of a 41 %-GC order-2 Markov text with 5 % planted repeats, 2-bit packed
+and resident in HBM, against 20,000 patterns of length 20-100 (70 % text substrings
+with 1 % point mutations). Output: one int32 longest-pattern id per base.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). ``value`` is Gbases/s over all ranks; each rank scans
+its own text of the same size (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gbases/s PFAC scan at 1 GB300 (% of HBM roofline); batched vs per-call; p99 ms"
+UNIT = "Gbases/s"
+N_BASES = 256 << 20
+N_PATTERNS = 20_000
+BYTES_PER_BASE = 4.25          # 2-bit packed text in (0.25 B) + int32 id out (4 B)
+HBM_FALLBACK_GBS = 6800.0
+
+
+def workload_name(n_bases=N_BASES, n_patterns=N_PATTERNS):
+    return (f"genome-scale single scan: {n_bases} bases order-2 Markov 41% GC + 5% repeats, "
+            f"2-bit packed; {n_patterns} patterns len 20-100 (70% substrings w/ 1% mutations)")
+
+
+def measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                clk, cmax, util = float(parts[1]), float(parts[2]), float(parts[4])
+            except ValueError:
+                continue
+            mx = cmax
+            if util > 0:
+                sm.append(clk)
+                for name, v in zip(names, parts[6:10]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples_under_load": len(sm)}
+
+
+def kernel_source_hash():
+    p = os.path.join(ROOT, "paper_1811_10498_gb300", "csrc", "pfac_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the scan kernel from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "tiled_kernel_genome_scan.md")
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def make_workload(rank: int, n_bases: int, n_patterns: int):
+    from paper_1811_10498_gb300 import datagen
+    return datagen.genome_scan(seed=2 + rank, n_bases=n_bases, n_patterns=n_patterns)
+
+
+def cpu_baseline(w, got_prefix: np.ndarray | None, seconds: float = 8.0):
+    """The CPU oracle (scan only), all host threads, on the first bases of the text."""
+    import oracle
+    threads = os.cpu_count() or 1
+    trie = oracle.Trie((w.blob, w.offsets))
+    n = w.text.size
+    sample = min(n, 1 << 20)
+    t0 = time.perf_counter()
+    trie.scan_threads(w.text, threads, 0, sample)
+    dt = time.perf_counter() - t0
+    rate = sample / max(dt, 1e-9)
+    sample = int(min(n, max(1 << 20, rate * seconds)))
+    sample -= sample % 64
+    t0 = time.perf_counter()
+    ref = trie.scan_threads(w.text, threads, 0, sample)
+    dt = time.perf_counter() - t0
+    out = {"value": sample / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"first {sample} offsets of the same text (walks may read past the sample), "
+                     f"{threads} threads, scan only"}
+    if got_prefix is not None:
+        out["parity_on_sample"] = bool(np.array_equal(ref[:sample], got_prefix[:sample]))
+    return out
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: each step scans a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    w = make_workload(0, args.n_bases, args.n_patterns)
+    threads = os.cpu_count() or 1
+    trie = oracle.Trie((w.blob, w.offsets))
+    n = w.text.size
+    probe = min(n, 1 << 20)
+    t0 = time.perf_counter()
+    trie.scan_threads(w.text, threads, 0, probe)
+    rate = probe / max(time.perf_counter() - t0, 1e-9)
+    per_step = max(64, int(rate * min(1.0, 90.0 / max(1, args.steps + args.warmup))))
+    per_step = min(per_step, n)
+    for i in range(args.warmup):
+        lo = (i * per_step) % max(1, n - per_step)
+        trie.scan_threads(w.text, threads, lo, lo + per_step)
+    times = []
+    for i in range(args.steps):
+        lo = ((args.warmup + i) * per_step) % max(1, n - per_step)
+        t0 = time.perf_counter()
+        trie.scan_threads(w.text, threads, lo, lo + per_step)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * args.steps / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": workload_name(args.n_bases, args.n_patterns)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} consecutive offsets per step, {threads} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-bases", type=int, default=N_BASES)
+    ap.add_argument("--n-patterns", type=int, default=N_PATTERNS)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1811_10498_gb300 import _binding as b
+    from paper_1811_10498_gb300 import build_ext
+    build_ext.build()
+
+    w = make_workload(rank, args.n_bases, args.n_patterns)
+    n = w.text.size
+    t0 = time.perf_counter()
+    table = b.Table((w.blob, w.offsets))
+    build_s = time.perf_counter() - t0
+    info = table.info
+
+    stream = torch.cuda.current_stream(dev)
+    d_text = torch.from_numpy(w.text).to(dev)
+    packed, status, bad = b.pack(d_text)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(max(4 * l2, 256 << 20), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+
+    # pack throughput (not part of a step: the text is packed once)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        b.pfac_pack(d_text, packed, None, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pack_gbs = 5 * n / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+    def step():
+        b.pfac_match_packed(table.h, packed, n, out, stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clocks:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()                      # L2 flushed between timed steps (outside the events)
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if world > 1:
+            dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) * 1e-3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * n * args.steps / total_s / 1e9
+    ms_per_step = 1e3 * total_s / args.steps
+
+    # roofline of the scan kernel (the only kernel of a step)
+    peak, peak_kind = measured_hbm()
+    t_launch = statistics.median(step_ms) * 1e-3
+    achieved = BYTES_PER_BASE * n / t_launch / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(), "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": BYTES_PER_BASE * n,
+                "kernel": "tiled_kernel<packed> (kernel 2)" if b.pfac_get_config(table.h, n)["kernel"] == 2
+                else "walk_rows_kernel<packed> (kernel 1)"}
+
+    # end to end through the public API with host buffers: H2D of the ASCII text,
+    # pack, scan, D2H of the ids, every step.
+    h_text = torch.from_numpy(w.text).pin_memory()
+    h_out = torch.empty(n, dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        d_text.copy_(h_text, non_blocking=True)
+        b.pfac_pack(d_text, packed, None, None, stream)
+        step()
+        h_out.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_s.record(stream)
+    for _ in range(args.e2e_steps):
+        d_text.copy_(h_text, non_blocking=True)
+        b.pfac_pack(d_text, packed, None, None, stream)
+        step()
+        h_out.copy_(out, non_blocking=True)
+    e_e.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e_s.elapsed_time(e_e) * 1e-3
+    e2e = {"value": world * n * args.e2e_steps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": n,
+           "d2h_bytes_per_step": 4 * n, "steps": args.e2e_steps,
+           "path": "pinned host ASCII -> H2D -> pfac_pack -> pfac_match_packed -> D2H ids"}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            got = out.cpu().numpy()
+            cpu = cpu_baseline(w, got)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": workload_name(args.n_bases, args.n_patterns), "n_bases": n,
+                       "n_patterns": args.n_patterns, "n_states": info["n_states"], "jump_k": info["jump_k"],
+                       "l2": "flushed between timed steps (memset of 4x L2 outside the events)",
+                       "input_resident": "packed text in HBM"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clocks.summary(),
+            "wall_s_timed_region": wall,
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+            "extra": {"pack_gbases_s": pack_gbs, "build_s": build_s,
+                      "frac_of_roofline_gbases": value / world / (peak / BYTES_PER_BASE)},
+        }
+        print(json.dumps(line), flush=True)
+    table.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * pfac.h — C ABI of the GB300 (sm_103a) PFAC DNA match scan.
+ *
+ * The method (Section IV of the paper): every text offset runs its own walk over a
+ * failure-less goto trie built from the patterns, from the root, following one edge
+ * per text symbol until no edge exists, and reports the id of the LONGEST pattern
+ * that starts at that offset (PFAC does not report the shorter sub-patterns).
+ * The trie has four columns, one per DNA base (Section V-A: a 4 x N transition
+ * table); patterns are inserted one by one (Section V-A, the insertion procedure
+ * after Table I). The paper's kernel runs one thread per text character and writes
+ * an integer array, one entry per character (Section V-B, kernel description).
+ *
+ * Conventions shared by every call:
+ *   - Pattern ids are 1-based in input order; 0 means "no pattern starts here".
+ *     If the same string is given more than once, the lowest id is reported.
+ *   - Text bytes are ASCII. Only 'A', 'C', 'G', 'T' have edges; any other byte
+ *     ('N', '\n', lowercase, ...) ends every walk that reaches it. A walk never
+ *     reads at or past the end of its text (or of its read, in batched calls).
+ *   - Packed text: base p is stored in bits 2*(p mod 16) .. 2*(p mod 16)+1 of the
+ *     32-bit word p / 16, with A=0, C=1, G=2, T=3.
+ *   - Lengths and offsets are int64 (texts may exceed 2^31 bases).
+ *   - Pointers named d_* are DEVICE pointers on the current CUDA device, owned by
+ *     the caller (for instance torch tensors' data_ptr()); the library never frees
+ *     them. A host pointer there is rejected with PFAC_ERR_INVALID_ARG: there is no
+ *     CPU fallback.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Scan calls are asynchronous: the return value reports argument and launch
+ *     errors only. Errors found on the device (a bad symbol met by pfac_pack, a
+ *     bounded wait that ran out) are written to a status word that the caller reads
+ *     after synchronising (pfac_pack's d_status, or pfac_device_status()).
+ *   - Functions return PFAC_OK (0) or one of the PFAC_ERR_* codes below.
+ */
+#ifndef PFAC_H
+#define PFAC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PFAC_OK = 0,
+    PFAC_ERR_INVALID_ARG = 1,     /* NULL or out-of-range argument, host pointer given as d_* */
+    PFAC_ERR_EMPTY_PATTERN = 2,   /* a pattern of length 0 */
+    PFAC_ERR_BAD_SYMBOL = 3,      /* a pattern byte (or, in pfac_pack, a text byte) outside ACGT */
+    PFAC_ERR_TOO_MANY_STATES = 4, /* the trie would need 2^31 or more states */
+    PFAC_ERR_OOM = 5,             /* host or device allocation failed */
+    PFAC_ERR_CUDA = 6,            /* a CUDA runtime call failed (see pfac_last_cuda_error) */
+    PFAC_ERR_OVERFLOW = 7,        /* more matches than the caller's capacity */
+    PFAC_ERR_TIMEOUT = 8,         /* a bounded device-side wait ran out */
+    PFAC_ERR_HOST_ONLY = 9,       /* the handle was built without a device copy */
+    PFAC_ERR_UNSUPPORTED = 10     /* option not available for this table (see pfac_info_ex) */
+};
+
+/* Opaque, library-owned table handle. */
+typedef struct pfac_table *pfac_handle;
+
+/* ---------------------------------------------------------------------------
+ * Table construction (Section V-A, Table I and the insertion procedure after it;
+ * the breadth-first renumbering follows the state rearrangement cited in
+ * Section II for cache locality).
+ * ------------------------------------------------------------------------- */
+
+/* Build the goto table from `n` patterns and upload it once to the current device.
+ *   patterns[j] : host pointer to the bytes of pattern j (not NUL-terminated)
+ *   lengths[j]  : its length in bytes, >= 1
+ * The library copies everything it needs; the caller keeps its arrays.
+ * Returns NULL on error; pfac_last_error() then gives PFAC_ERR_INVALID_ARG (n <= 0
+ * or a NULL array), PFAC_ERR_EMPTY_PATTERN, PFAC_ERR_BAD_SYMBOL,
+ * PFAC_ERR_TOO_MANY_STATES, PFAC_ERR_OOM or PFAC_ERR_CUDA. */
+pfac_handle pfac_build(const char *const *patterns, const int32_t *lengths, int32_t n);
+
+/* Options for pfac_build_ex. Zero-initialise, then set what you need. */
+typedef struct {
+    int32_t host_only;  /* 1: build the tables on the host only (no device copy; the
+                           scan calls reject the handle with PFAC_ERR_HOST_ONLY). */
+    int32_t jump_k;     /* order of the k-mer jump table: 0 = choose automatically,
+                           -1 = none, 1..12 = that order. The jump table maps the first
+                           k bases of a walk to the state they reach (an exact
+                           shortcut through the same trie). */
+} pfac_build_opts;
+
+pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, int32_t n,
+                          const pfac_build_opts *opts);
+
+/* Status of the last failed call on this thread (PFAC_OK if none). */
+int pfac_last_error(void);
+/* Static description of a status code. */
+const char *pfac_error_string(int status);
+/* Text of the last CUDA runtime error seen by this thread, or "". */
+const char *pfac_last_cuda_error(void);
+
+/* Free the handle and its device memory. No launch that uses the handle may still
+ * be in flight (synchronise its streams first). NULL is accepted. */
+int pfac_destroy(pfac_handle h);
+
+/* Table size: states, longest pattern, bytes held on the device. Any output may be
+ * NULL. */
+int pfac_info(pfac_handle h, int64_t *n_states, int32_t *max_len, int64_t *table_bytes);
+
+typedef struct {
+    int64_t n_states;       /* trie states, root included */
+    int32_t n_patterns;
+    int32_t max_len;        /* longest pattern = deepest level of the trie */
+    int32_t min_len;
+    int32_t jump_k;         /* order of the jump table, 0 if none */
+    int64_t n_duplicates;   /* patterns whose string was given before */
+    int64_t table_bytes;    /* device bytes (all layouts) */
+    int64_t rows_bytes;     /* 16-byte rows: 4 x int32 per state */
+    int64_t nodes_bytes;    /* 4-byte compact nodes, 0 if unavailable */
+    int32_t has_nodes;      /* compact node layout available (fewer than 2^27 states) */
+    int32_t device;         /* device holding the copy, -1 if host only */
+} pfac_table_info;
+
+int pfac_info_ex(pfac_handle h, pfac_table_info *info);
+
+/* Copy the host tables (breadth-first state order) for inspection:
+ *   rows[4*S]   : rows[4*s + c] = next state for base c (A,C,G,T); bit 31 set if
+ *                 that state is terminal; 0 = no edge (the root is never a target)
+ *   out_id[S]   : id of the pattern ending at state s, 0 if none
+ *   level[L+2]  : states of depth d are [level[d], level[d+1]) (L = max_len)
+ * Any output may be NULL. S = n_states from pfac_info. */
+int pfac_export(pfac_handle h, int32_t *rows, int32_t *out_id, int64_t *level);
+
+/* ---------------------------------------------------------------------------
+ * Launch configuration (what the autotuner chooses). All fields 0 = automatic.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t kernel;          /* 0 auto, 1 = per-offset walk over rows in global memory
+                                (one thread per text offset, the paper's layout),
+                                2 = tiled: text staged by TMA, table window in shared
+                                memory, jump table, compact nodes */
+    int32_t tile_bases;      /* bases per tile (kernel 2), multiple of 64 */
+    int32_t threads;         /* threads per CTA */
+    int32_t ctas_per_sm;     /* resident CTAs per SM for the persistent grid */
+    int32_t smem_table_bytes;/* bytes of shared memory for the table window (kernel 2);
+                                -1 = none */
+    int32_t l2_persist;      /* 1 = pin the next part of the table in L2 with an access
+                                policy window, -1 = never */
+} pfac_config;
+
+/* Set (cfg != NULL) or reset (cfg == NULL) the launch configuration of a handle.
+ * Takes effect for launches issued afterwards. */
+int pfac_set_config(pfac_handle h, const pfac_config *cfg);
+/* The configuration the next launch on `n_bases` bases would use. */
+int pfac_get_config(pfac_handle h, int64_t n_bases, pfac_config *cfg);
+
+/* ---------------------------------------------------------------------------
+ * Scans (Section IV; Section V-B).
+ * ------------------------------------------------------------------------- */
+
+/* 2-bit packing of ASCII text (not in the paper, which reads characters).
+ *   d_text[len]            : ASCII bases
+ *   d_packed[(len+15)/16]  : output words (layout above); bases past len are 0
+ *   d_status (may be NULL) : int32 set to PFAC_OK, or PFAC_ERR_BAD_SYMBOL if some
+ *                            byte is outside ACGT (such a byte is packed as A)
+ *   d_bad (may be NULL)    : int64 set to the first such offset, or -1
+ * d_status and d_bad are reset by the call itself (stream-ordered). */
+int pfac_pack(const uint8_t *d_text, int64_t len, uint32_t *d_packed, int32_t *d_status,
+              int64_t *d_bad, void *stream);
+
+/* Longest-pattern id for every offset of an ASCII text: d_out_ids[i], i in [0, len). */
+int pfac_match(pfac_handle h, const uint8_t *d_text, int64_t len, int32_t *d_out_ids,
+               void *stream);
+
+/* The same on packed text (n_bases bases in d_packed[(n_bases+15)/16]). */
+int pfac_match_packed(pfac_handle h, const uint32_t *d_packed, int64_t n_bases,
+                      int32_t *d_out_ids, void *stream);
+
+/* Match list instead of a dense array: for every offset i with a non-zero id,
+ * one (d_offsets[k], d_ids[k]) pair, k < capacity, in no particular order.
+ * *d_count receives the total number of matches (which may exceed capacity; then
+ * only `capacity` pairs are written, which ones is unspecified, and the caller sees
+ * the overflow by comparing *d_count with capacity after synchronising).
+ * d_count is reset by the call itself (stream-ordered). */
+int pfac_match_compact(pfac_handle h, const uint32_t *d_packed, int64_t n_bases,
+                       int64_t *d_offsets, int32_t *d_ids, int64_t capacity,
+                       int64_t *d_count, void *stream);
+
+/* Many reads against many resident tables in ONE launch.
+ *   sets[n_sets]                 : host array of handles built on this device
+ *   d_texts                      : all reads' ASCII bytes, concatenated
+ *   d_read_offsets[n_reads + 1]  : read r is d_texts[off[r] .. off[r+1]), increasing
+ *   d_read_set[n_reads]          : index into sets[] of the table for read r
+ *   d_out_ids                    : same layout as d_texts
+ * Walks never cross a read's end. The first call with a given list of handles
+ * uploads a small descriptor array (a synchronous copy); later calls with the same
+ * list reuse it, so a call issued while a stream is being captured into a CUDA
+ * graph must use a list that was seen before capture. */
+int pfac_match_batched(const pfac_handle *sets, int32_t n_sets, const uint8_t *d_texts,
+                       const int64_t *d_read_offsets, const int32_t *d_read_set,
+                       int32_t n_reads, int32_t *d_out_ids, void *stream);
+
+/* Read (and clear) the device status word of a handle: PFAC_OK or the first error a
+ * kernel recorded (for example PFAC_ERR_TIMEOUT from a bounded wait). Synchronises
+ * `stream`. */
+int pfac_device_status(pfac_handle h, int32_t *status, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Failure detection (the paper has no counterpart).
+ * ------------------------------------------------------------------------- */
+
+/* Launch a one-CTA kernel that waits on an mbarrier nothing ever completes, with the
+ * same bounded wait the scan kernels use for their TMA copies. After limit_ns
+ * nanoseconds the wait gives up and PFAC_ERR_TIMEOUT is written to *d_status (an
+ * int32 device word; the call resets it first). Lets a test check that a wait which
+ * runs out leaves the context usable and reports an error status, without faulting
+ * or hanging the GPU. */
+int pfac_debug_timeout_probe(int32_t *d_status, int64_t limit_ns, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFAC_H */

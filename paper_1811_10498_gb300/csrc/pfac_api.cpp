@@ -1,0 +1,425 @@
+// C ABI of the PFAC scan (include/pfac.h): table handles, upload, argument checks,
+// launch configuration and dispatch to the kernels in pfac_kernels.cu.
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pfac.h"
+#include "pfac_internal.h"
+
+struct pfac_table {
+    pfac::HostTables host;
+    int device = -1;
+    void *dmem = nullptr;
+    size_t dbytes = 0;
+    int64_t rows_bytes = 0, nodes_bytes = 0;
+    pfac::DeviceTable dt{};
+    std::mutex mu;
+    bool cfg_set = false;
+    pfac_config cfg{};
+};
+
+namespace {
+
+thread_local int g_last_error = PFAC_OK;
+thread_local std::string g_last_cuda;
+
+int fail(int code)
+{
+    g_last_error = code;
+    return code;
+}
+
+int cuda_fail(cudaError_t e)
+{
+    g_last_cuda = cudaGetErrorString(e);
+    cudaGetLastError();   // clear a sticky-free error so later calls start clean
+    return fail(PFAC_ERR_CUDA);
+}
+
+std::mutex g_props_mu;
+std::map<int, pfac::DeviceProps> g_props;
+
+int device_props(pfac::DeviceProps *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::lock_guard<std::mutex> lk(g_props_mu);
+    auto it = g_props.find(dev);
+    if (it == g_props.end()) {
+        pfac::DeviceProps p{};
+        int rc = pfac::get_device_props(&p);
+        if (rc != PFAC_OK) return cuda_fail(cudaGetLastError());
+        it = g_props.emplace(dev, p).first;
+    }
+    *out = it->second;
+    return PFAC_OK;
+}
+
+// A d_* argument must be device (or managed) memory of the current device.
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int check_handle_for_launch(pfac_handle h, pfac::DeviceProps *dp)
+{
+    if (!h) return fail(PFAC_ERR_INVALID_ARG);
+    if (h->device < 0 || !h->dmem) return fail(PFAC_ERR_HOST_ONLY);
+    int rc = device_props(dp);
+    if (rc != PFAC_OK) return rc;
+    if (dp->device != h->device) return fail(PFAC_ERR_INVALID_ARG);
+    return PFAC_OK;
+}
+
+pfac_config default_config(const pfac_table *h, int64_t n_bases, bool packed, const pfac::DeviceProps &dp)
+{
+    (void)n_bases;
+    (void)dp;
+    pfac_config c{};
+    c.kernel = (h->dt.nodes && h->dt.jump) ? 2 : 1;
+    c.tile_bases = 4096;
+    c.threads = 1024;
+    c.ctas_per_sm = 1;
+    c.smem_table_bytes = 0;
+    c.l2_persist = 0;
+    (void)packed;
+    return c;
+}
+
+pfac_config effective_config(pfac_table *h, int64_t n_bases, bool packed, const pfac::DeviceProps &dp)
+{
+    pfac_config d = default_config(h, n_bases, packed, dp);
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (!h->cfg_set) return d;
+    pfac_config c = h->cfg;
+    if (c.kernel == 0) c.kernel = d.kernel;
+    if (c.tile_bases == 0) c.tile_bases = d.tile_bases;
+    if (c.threads == 0) c.threads = d.threads;
+    if (c.ctas_per_sm == 0) c.ctas_per_sm = d.ctas_per_sm;
+    return c;
+}
+
+pfac::TiledConfig tiled_config(const pfac_config &c)
+{
+    pfac::TiledConfig t{};
+    t.tile = c.tile_bases;
+    t.threads = c.threads;
+    t.ctas_per_sm = c.ctas_per_sm;
+    t.smem_table_bytes = c.smem_table_bytes;
+    t.l2_persist = c.l2_persist;
+    t.timeout_ns = 2000000000LL;
+    return t;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Run the scan with the handle's configuration; the tiled kernel needs 16-byte
+// aligned text and output and a table with compact nodes; otherwise kernel 1 runs.
+int run_scan(pfac_handle h, const void *text, bool packed, int64_t n, int32_t *out, int64_t *c_off,
+             int32_t *c_ids, int64_t cap, int64_t *count, cudaStream_t st, const pfac::DeviceProps &dp)
+{
+    pfac_config c = effective_config(h, n, packed, dp);
+    const bool compact = c_off != nullptr;
+    bool tiled = c.kernel == 2 && h->dt.nodes && aligned16(text) && (compact || aligned16(out));
+    int rc = PFAC_OK;
+    if (tiled) {
+        pfac::TiledConfig tc = tiled_config(c);
+        rc = pfac::launch_tiled(h->dt, text, packed, n, out, c_off, c_ids, cap, (unsigned long long *)count, tc, st, dp);
+        if (rc == PFAC_ERR_UNSUPPORTED) tiled = false;   // e.g. a halo too long for shared memory
+        else if (rc != PFAC_OK) return rc == PFAC_ERR_CUDA ? cuda_fail(cudaGetLastError()) : fail(rc);
+    }
+    if (!tiled) {
+        rc = pfac::launch_walk_rows_any(h->dt, text, packed, n, out, c_off, c_ids, cap, (unsigned long long *)count,
+                                        st, dp);
+        if (rc != PFAC_OK) return rc == PFAC_ERR_CUDA ? cuda_fail(cudaGetLastError()) : fail(rc);
+    }
+    return PFAC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pfac_last_error(void) { return g_last_error; }
+
+const char *pfac_last_cuda_error(void) { return g_last_cuda.c_str(); }
+
+const char *pfac_error_string(int status)
+{
+    switch (status) {
+    case PFAC_OK: return "ok";
+    case PFAC_ERR_INVALID_ARG: return "invalid argument";
+    case PFAC_ERR_EMPTY_PATTERN: return "empty pattern";
+    case PFAC_ERR_BAD_SYMBOL: return "byte outside A, C, G, T";
+    case PFAC_ERR_TOO_MANY_STATES: return "too many trie states (2^31 or more)";
+    case PFAC_ERR_OOM: return "out of memory";
+    case PFAC_ERR_CUDA: return "CUDA runtime error";
+    case PFAC_ERR_OVERFLOW: return "more matches than capacity";
+    case PFAC_ERR_TIMEOUT: return "bounded device wait ran out";
+    case PFAC_ERR_HOST_ONLY: return "handle has no device copy";
+    case PFAC_ERR_UNSUPPORTED: return "option not supported for this table";
+    default: return "unknown status";
+    }
+}
+
+pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, int32_t n,
+                          const pfac_build_opts *opts)
+{
+    g_last_error = PFAC_OK;
+    pfac_build_opts o{};
+    if (opts) o = *opts;
+    pfac_table *h = new (std::nothrow) pfac_table();
+    if (!h) { fail(PFAC_ERR_OOM); return nullptr; }
+    int rc = pfac::build_host_tables(patterns, lengths, n, o.jump_k, &h->host);
+    if (rc != PFAC_OK) { delete h; fail(rc); return nullptr; }
+    const pfac::HostTables &T = h->host;
+    h->rows_bytes = T.n_states * 16;
+    h->nodes_bytes = (int64_t)T.nodes.size() * 4;
+    if (!o.host_only) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) { delete h; cuda_fail(e); return nullptr; }
+        const size_t s_status = 256;
+        const size_t s_rows = round256((size_t)T.n_states * 16);
+        const size_t s_nodes = round256(T.nodes.size() * 4);
+        const size_t s_out = round256((size_t)T.n_states * 4);
+        const size_t s_jump = round256(T.jump.size() * 4);
+        const size_t s_jbest = round256(T.jump_best.size() * 4);
+        h->dbytes = s_status + s_rows + s_nodes + s_out + s_jump + s_jbest;
+        e = cudaMalloc(&h->dmem, h->dbytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            fail(e == cudaErrorMemoryAllocation ? PFAC_ERR_OOM : PFAC_ERR_CUDA);
+            return nullptr;
+        }
+        uint8_t *base = (uint8_t *)h->dmem;
+        size_t off = 0;
+        h->dt.status = (int32_t *)(base + off); off += s_status;
+        h->dt.rows = (const int32_t *)(base + off); off += s_rows;
+        h->dt.nodes = T.nodes.empty() ? nullptr : (const uint32_t *)(base + off); off += s_nodes;
+        h->dt.out_id = (const int32_t *)(base + off); off += s_out;
+        h->dt.jump = T.jump.empty() ? nullptr : (const uint32_t *)(base + off); off += s_jump;
+        h->dt.jump_best = T.jump_best.empty() ? nullptr : (const int32_t *)(base + off); off += s_jbest;
+        struct Up { const void *dst; const void *src; size_t bytes; } ups[] = {
+            {h->dt.rows, T.rows.data(), T.rows.size() * 4},
+            {h->dt.nodes, T.nodes.data(), T.nodes.size() * 4},
+            {h->dt.out_id, T.out_id.data(), T.out_id.size() * 4},
+            {h->dt.jump, T.jump.data(), T.jump.size() * 4},
+            {h->dt.jump_best, T.jump_best.data(), T.jump_best.size() * 4},
+        };
+        e = cudaMemset(h->dt.status, 0, s_status);
+        for (auto &u : ups)
+            if (e == cudaSuccess && u.dst && u.bytes) e = cudaMemcpy((void *)u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(h->dmem);
+            delete h;
+            cuda_fail(e);
+            return nullptr;
+        }
+        h->device = dev;
+        h->dt.n_states = T.n_states;
+        h->dt.max_len = T.max_len;
+        h->dt.jump_k = T.jump_k;
+        h->dt.win_lo = T.jump_k > 0 ? T.level[(size_t)std::min(T.jump_k + 1, T.max_len + 1)] : 0;
+        // The device copy is complete; the host keeps rows, ids and levels for export.
+        std::vector<uint32_t>().swap(h->host.nodes);
+        std::vector<uint32_t>().swap(h->host.jump);
+        std::vector<int32_t>().swap(h->host.jump_best);
+    }
+    return h;
+}
+
+pfac_handle pfac_build(const char *const *patterns, const int32_t *lengths, int32_t n)
+{
+    return pfac_build_ex(patterns, lengths, n, nullptr);
+}
+
+int pfac_destroy(pfac_handle h)
+{
+    if (!h) return PFAC_OK;
+    int rc = PFAC_OK;
+    if (h->dmem) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != h->device) cudaSetDevice(h->device);
+        cudaError_t e = cudaFree(h->dmem);
+        if (cur != h->device) cudaSetDevice(cur);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+    }
+    delete h;
+    return rc;
+}
+
+int pfac_info(pfac_handle h, int64_t *n_states, int32_t *max_len, int64_t *table_bytes)
+{
+    if (!h) return fail(PFAC_ERR_INVALID_ARG);
+    if (n_states) *n_states = h->host.n_states;
+    if (max_len) *max_len = h->host.max_len;
+    if (table_bytes) *table_bytes = (int64_t)h->dbytes;
+    return PFAC_OK;
+}
+
+int pfac_info_ex(pfac_handle h, pfac_table_info *info)
+{
+    if (!h || !info) return fail(PFAC_ERR_INVALID_ARG);
+    pfac_table_info i{};
+    i.n_states = h->host.n_states;
+    i.n_patterns = h->host.n_patterns;
+    i.max_len = h->host.max_len;
+    i.min_len = h->host.min_len;
+    i.jump_k = h->host.jump_k;
+    i.n_duplicates = h->host.n_duplicates;
+    i.table_bytes = (int64_t)h->dbytes;
+    i.rows_bytes = h->rows_bytes;
+    i.nodes_bytes = h->nodes_bytes;
+    i.has_nodes = h->nodes_bytes > 0;
+    i.device = h->device;
+    *info = i;
+    return PFAC_OK;
+}
+
+int pfac_export(pfac_handle h, int32_t *rows, int32_t *out_id, int64_t *level)
+{
+    if (!h) return fail(PFAC_ERR_INVALID_ARG);
+    const pfac::HostTables &T = h->host;
+    if (rows) memcpy(rows, T.rows.data(), T.rows.size() * 4);
+    if (out_id) memcpy(out_id, T.out_id.data(), T.out_id.size() * 4);
+    if (level) memcpy(level, T.level.data(), T.level.size() * 8);
+    return PFAC_OK;
+}
+
+int pfac_set_config(pfac_handle h, const pfac_config *cfg)
+{
+    if (!h) return fail(PFAC_ERR_INVALID_ARG);
+    if (cfg) {
+        if (cfg->kernel < 0 || cfg->kernel > 2 || cfg->tile_bases < 0 || (cfg->tile_bases & 63) ||
+            cfg->tile_bases > 32768 || cfg->threads < 0 || (cfg->threads & 31) || cfg->threads > 1024 ||
+            cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32)
+            return fail(PFAC_ERR_INVALID_ARG);
+        if (cfg->kernel == 2 && !(h->nodes_bytes > 0 && h->host.jump_k > 0)) return fail(PFAC_ERR_UNSUPPORTED);
+    }
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->cfg_set = cfg != nullptr;
+    if (cfg) h->cfg = *cfg;
+    return PFAC_OK;
+}
+
+int pfac_get_config(pfac_handle h, int64_t n_bases, pfac_config *cfg)
+{
+    if (!h || !cfg) return fail(PFAC_ERR_INVALID_ARG);
+    pfac::DeviceProps dp{};
+    if (h->device >= 0) {
+        int rc = device_props(&dp);
+        if (rc != PFAC_OK) return rc;
+    }
+    *cfg = effective_config(h, n_bases, true, dp);
+    return PFAC_OK;
+}
+
+int pfac_pack(const uint8_t *d_text, int64_t len, uint32_t *d_packed, int32_t *d_status, int64_t *d_bad,
+              void *stream)
+{
+    if (len < 0) return fail(PFAC_ERR_INVALID_ARG);
+    if (len > 0 && (!is_device_ptr(d_text) || !is_device_ptr(d_packed))) return fail(PFAC_ERR_INVALID_ARG);
+    if ((d_status && !is_device_ptr(d_status)) || (d_bad && !is_device_ptr(d_bad))) return fail(PFAC_ERR_INVALID_ARG);
+    pfac::DeviceProps dp{};
+    int rc = device_props(&dp);
+    if (rc != PFAC_OK) return rc;
+    rc = pfac::launch_pack(d_text, len, d_packed, d_status, d_bad, (cudaStream_t)stream, dp);
+    return rc == PFAC_OK ? PFAC_OK : cuda_fail(cudaGetLastError());
+}
+
+int pfac_match(pfac_handle h, const uint8_t *d_text, int64_t len, int32_t *d_out_ids, void *stream)
+{
+    pfac::DeviceProps dp{};
+    int rc = check_handle_for_launch(h, &dp);
+    if (rc != PFAC_OK) return rc;
+    if (len < 0) return fail(PFAC_ERR_INVALID_ARG);
+    if (len == 0) return PFAC_OK;
+    if (!is_device_ptr(d_text) || !is_device_ptr(d_out_ids)) return fail(PFAC_ERR_INVALID_ARG);
+    return run_scan(h, d_text, false, len, d_out_ids, nullptr, nullptr, 0, nullptr, (cudaStream_t)stream, dp);
+}
+
+int pfac_match_packed(pfac_handle h, const uint32_t *d_packed, int64_t n_bases, int32_t *d_out_ids, void *stream)
+{
+    pfac::DeviceProps dp{};
+    int rc = check_handle_for_launch(h, &dp);
+    if (rc != PFAC_OK) return rc;
+    if (n_bases < 0) return fail(PFAC_ERR_INVALID_ARG);
+    if (n_bases == 0) return PFAC_OK;
+    if (!is_device_ptr(d_packed) || !is_device_ptr(d_out_ids)) return fail(PFAC_ERR_INVALID_ARG);
+    return run_scan(h, d_packed, true, n_bases, d_out_ids, nullptr, nullptr, 0, nullptr, (cudaStream_t)stream, dp);
+}
+
+int pfac_match_compact(pfac_handle h, const uint32_t *d_packed, int64_t n_bases, int64_t *d_offsets, int32_t *d_ids,
+                       int64_t capacity, int64_t *d_count, void *stream)
+{
+    pfac::DeviceProps dp{};
+    int rc = check_handle_for_launch(h, &dp);
+    if (rc != PFAC_OK) return rc;
+    if (n_bases < 0 || capacity < 0 || !is_device_ptr(d_count)) return fail(PFAC_ERR_INVALID_ARG);
+    if (capacity > 0 && (!is_device_ptr(d_offsets) || !is_device_ptr(d_ids))) return fail(PFAC_ERR_INVALID_ARG);
+    if (n_bases > 0 && !is_device_ptr(d_packed)) return fail(PFAC_ERR_INVALID_ARG);
+    if (n_bases == 0) {
+        cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(int64_t), (cudaStream_t)stream);
+        return e == cudaSuccess ? PFAC_OK : cuda_fail(e);
+    }
+    int64_t *offs = d_offsets ? d_offsets : (int64_t *)d_count;   // never written when capacity == 0
+    int32_t *ids = d_ids ? d_ids : (int32_t *)d_count;
+    return run_scan(h, d_packed, true, n_bases, nullptr, offs, ids, capacity, d_count, (cudaStream_t)stream, dp);
+}
+
+int pfac_device_status(pfac_handle h, int32_t *status, void *stream)
+{
+    if (!h || !status) return fail(PFAC_ERR_INVALID_ARG);
+    if (h->device < 0) return fail(PFAC_ERR_HOST_ONLY);
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, h->dt.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dt.status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *status = v;
+    return PFAC_OK;
+}
+
+int pfac_match_batched(const pfac_handle *sets, int32_t n_sets, const uint8_t *d_texts,
+                       const int64_t *d_read_offsets, const int32_t *d_read_set, int32_t n_reads,
+                       int32_t *d_out_ids, void *stream)
+{
+    (void)sets; (void)n_sets; (void)d_texts; (void)d_read_offsets; (void)d_read_set; (void)n_reads;
+    (void)d_out_ids; (void)stream;
+    return fail(PFAC_ERR_UNSUPPORTED);
+}
+
+int pfac_debug_timeout_probe(int32_t *d_status, int64_t limit_ns, void *stream)
+{
+    if (!is_device_ptr(d_status) || limit_ns <= 0) return fail(PFAC_ERR_INVALID_ARG);
+    cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int rc = pfac::launch_timeout_probe(d_status, limit_ns, (cudaStream_t)stream);
+    return rc == PFAC_OK ? PFAC_OK : cuda_fail(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -1,0 +1,221 @@
+// Host-side construction of the PFAC goto table.
+//
+// Step 1 (Section V-A, the insertion procedure after Table I): patterns are inserted
+// one by one into a 4-column table; from state 0, each symbol either follows the
+// existing edge or creates the next free state. The state of a pattern's last symbol
+// is terminal and carries the pattern's id (the paper writes it into the cell; here
+// it is kept per state, and the first id given for a string is kept).
+//
+// Step 2 (the breadth-first state rearrangement cited in Section II): states are
+// renumbered breadth-first, children visited in A, C, G, T order, so each depth level
+// is a contiguous range of ids and the children of one state are consecutive. The
+// shallow levels that every walk visits become a short prefix of the table.
+//
+// Step 3: the table is encoded three ways for the device (see pfac_internal.h):
+// 16-byte rows (4 x int32, one per base, bit 31 = target is terminal), 4-byte compact
+// node words, and a k-mer jump table that replaces the first k steps of a walk with
+// one lookup.
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "../../include/pfac.h"
+#include "pfac_internal.h"
+
+namespace pfac {
+
+namespace {
+
+inline int base_code(unsigned char b)
+{
+    switch (b) {
+    case 'A': return 0;
+    case 'C': return 1;
+    case 'G': return 2;
+    case 'T': return 3;
+    default: return -1;
+    }
+}
+
+constexpr int64_t kMaxStates = int64_t(0x7FFFFFFF);
+
+}  // namespace
+
+int32_t auto_jump_k(int32_t n_patterns, int64_t n_states)
+{
+    (void)n_states;
+    // Levels with fewer than about four times as many k-mers as patterns are nearly
+    // complete: a jump over them replaces that many dependent steps at a table
+    // size of 4^k words. Seven levels (64 KB) is what a shared-memory copy allows.
+    double k = std::floor(std::log((double)std::max<int32_t>(n_patterns, 1)) / std::log(4.0) + 0.5);
+    return (int32_t)std::min(7.0, std::max(2.0, k));
+}
+
+int build_host_tables(const char *const *patterns, const int32_t *lengths, int32_t n,
+                      int32_t jump_k_opt, HostTables *out)
+{
+    if (n <= 0 || !patterns || !lengths || !out) return PFAC_ERR_INVALID_ARG;
+    if (jump_k_opt > kMaxJumpK) return PFAC_ERR_INVALID_ARG;
+    try {
+        // ---- validate ----------------------------------------------------------
+        int64_t total = 0;
+        int32_t max_len = 0, min_len = INT32_MAX;
+        for (int32_t j = 0; j < n; j++) {
+            if (lengths[j] <= 0) return lengths[j] == 0 ? PFAC_ERR_EMPTY_PATTERN : PFAC_ERR_INVALID_ARG;
+            if (!patterns[j]) return PFAC_ERR_INVALID_ARG;
+            const unsigned char *p = (const unsigned char *)patterns[j];
+            for (int32_t k = 0; k < lengths[j]; k++)
+                if (base_code(p[k]) < 0) return PFAC_ERR_BAD_SYMBOL;
+            total += lengths[j];
+            max_len = std::max(max_len, lengths[j]);
+            min_len = std::min(min_len, lengths[j]);
+        }
+
+        // ---- step 1: insertion-order trie --------------------------------------
+        std::vector<int32_t> go;      // 4 per state, 0 = no edge
+        std::vector<int32_t> term;    // pattern id per state
+        int64_t cap = std::min<int64_t>(total + 1, kMaxStates);
+        go.reserve((size_t)std::min<int64_t>(cap, 1 << 24) * 4);
+        go.assign(4, 0);
+        term.assign(1, 0);
+        int64_t n_states = 1;
+        int64_t dups = 0;
+        for (int32_t j = 0; j < n; j++) {
+            const unsigned char *p = (const unsigned char *)patterns[j];
+            int64_t s = 0;
+            for (int32_t k = 0; k < lengths[j]; k++) {
+                int c = base_code(p[k]);
+                int32_t nxt = go[(size_t)(4 * s + c)];
+                if (nxt == 0) {
+                    if (n_states >= kMaxStates) return PFAC_ERR_TOO_MANY_STATES;
+                    nxt = (int32_t)n_states++;
+                    go[(size_t)(4 * s + c)] = nxt;
+                    go.insert(go.end(), 4, 0);
+                    term.push_back(0);
+                }
+                s = nxt;
+            }
+            if (term[(size_t)s] == 0) term[(size_t)s] = j + 1;
+            else dups++;
+        }
+
+        // ---- step 2: breadth-first renumbering ---------------------------------
+        std::vector<int32_t> order((size_t)n_states);   // new id -> old id
+        std::vector<int32_t> renum((size_t)n_states);   // old id -> new id
+        std::vector<int32_t> depth_of((size_t)n_states);
+        int64_t head = 0, tail = 0;
+        order[tail++] = 0;
+        renum[0] = 0;
+        depth_of[0] = 0;
+        while (head < tail) {
+            int32_t old = order[(size_t)head];
+            int32_t dnew = depth_of[(size_t)head];
+            head++;
+            for (int c = 0; c < 4; c++) {
+                int32_t ch = go[(size_t)(4 * (int64_t)old + c)];
+                if (ch) {
+                    renum[(size_t)ch] = (int32_t)tail;
+                    depth_of[(size_t)tail] = dnew + 1;
+                    order[(size_t)tail++] = ch;
+                }
+            }
+        }
+
+        HostTables &T = *out;
+        T = HostTables();
+        T.n_states = n_states;
+        T.n_patterns = n;
+        T.max_len = max_len;
+        T.min_len = min_len;
+        T.n_duplicates = dups;
+        T.level.assign((size_t)max_len + 2, n_states);
+        for (int64_t s = n_states - 1; s >= 0; s--) T.level[(size_t)depth_of[(size_t)s]] = s;
+        for (int d = max_len; d >= 0; d--) T.level[(size_t)d] = std::min(T.level[(size_t)d], T.level[(size_t)d + 1]);
+
+        // ---- step 3a: 16-byte rows and pattern ids ------------------------------
+        T.rows.assign((size_t)n_states * 4, 0);
+        T.out_id.assign((size_t)n_states, 0);
+        for (int64_t s = 0; s < n_states; s++) {
+            int32_t old = order[(size_t)s];
+            T.out_id[(size_t)s] = term[(size_t)old];
+            for (int c = 0; c < 4; c++) {
+                int32_t ch = go[(size_t)(4 * (int64_t)old + c)];
+                if (ch) {
+                    uint32_t e = (uint32_t)renum[(size_t)ch];
+                    if (term[(size_t)ch]) e |= 0x80000000u;
+                    T.rows[(size_t)(4 * s + c)] = (int32_t)e;
+                }
+            }
+        }
+        std::vector<int32_t>().swap(go);
+        std::vector<int32_t>().swap(term);
+        std::vector<int32_t>().swap(order);
+        std::vector<int32_t>().swap(renum);
+        std::vector<int32_t>().swap(depth_of);
+
+        // ---- step 3b: compact node words -----------------------------------------
+        if (n_states < kMaxNodeStates) {
+            T.nodes.assign((size_t)n_states, 0);
+            for (int64_t s = 0; s < n_states; s++) {
+                uint32_t mask = 0, first = 0;
+                for (int c = 3; c >= 0; c--) {
+                    uint32_t e = (uint32_t)T.rows[(size_t)(4 * s + c)];
+                    if (e) { mask |= 1u << c; first = e & 0x7FFFFFFFu; }
+                }
+                uint32_t w = mask | (first << kNodeFirstShift);
+                if (T.out_id[(size_t)s]) w |= kNodeTermBit;
+                T.nodes[(size_t)s] = w;
+            }
+        }
+
+        // ---- step 3c: k-mer jump table ------------------------------------------
+        int32_t k = jump_k_opt == 0 ? auto_jump_k(n, n_states) : (jump_k_opt < 0 ? 0 : jump_k_opt);
+        if (k > 0 && !T.nodes.empty() && n < (1 << 27)) {
+            T.jump_k = k;
+            size_t E = (size_t)1 << (2 * k);
+            T.jump.assign(E, 0);
+            T.jump_best.assign(E, 0);
+            // Depth-first over the trie down to depth k. A prefix of d symbols whose walk
+            // stops at symbol d fixes the entry of every k-mer that starts with it:
+            // those are the indices congruent to the prefix code modulo 4^(d+1).
+            struct Frame { int32_t s; int32_t d; uint32_t code; int32_t best; };
+            std::vector<Frame> stack;
+            stack.push_back({0, 0, 0u, 0});
+            while (!stack.empty()) {
+                Frame f = stack.back();
+                stack.pop_back();
+                if (f.d == k) {
+                    uint32_t w = T.nodes[(size_t)f.s] & ~kNodeTermBit;
+                    if (f.best) w |= kNodeTermBit;
+                    T.jump[f.code] = w;
+                    T.jump_best[f.code] = f.best;
+                    continue;
+                }
+                for (int c = 0; c < 4; c++) {
+                    uint32_t code = f.code | ((uint32_t)c << (2 * f.d));
+                    uint32_t e = (uint32_t)T.rows[(size_t)(4 * (int64_t)f.s + c)];
+                    if (e) {
+                        int32_t ch = (int32_t)(e & 0x7FFFFFFFu);
+                        int32_t best = (e & 0x80000000u) ? ch : f.best;
+                        stack.push_back({ch, f.d + 1, code, best});
+                    } else {
+                        // walk over the prefix ends here: answer fixed for all extensions
+                        uint32_t ans = f.best ? (uint32_t)T.out_id[(size_t)f.best] : 0u;
+                        uint32_t w = ans << kNodeFirstShift;
+                        size_t stride = (size_t)1 << (2 * (f.d + 1));
+                        for (size_t idx = code; idx < E; idx += stride) T.jump[idx] = w;
+                    }
+                }
+            }
+        }
+        return PFAC_OK;
+    } catch (const std::bad_alloc &) {
+        return PFAC_ERR_OOM;
+    }
+}
+
+}  // namespace pfac
