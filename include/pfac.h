@@ -127,17 +127,21 @@ int pfac_export(pfac_handle h, int32_t *rows, int32_t *out_id, int64_t *level);
  * Launch configuration (what the autotuner chooses). All fields 0 = automatic.
  * ------------------------------------------------------------------------- */
 typedef struct {
-    int32_t kernel;          /* 0 auto, 1 = per-offset walk over rows in global memory
-                                (one thread per text offset, the paper's layout),
-                                2 = tiled: text staged by TMA, table window in shared
-                                memory, jump table, compact nodes */
-    int32_t tile_bases;      /* bases per tile (kernel 2), multiple of 64 */
-    int32_t threads;         /* threads per CTA */
-    int32_t ctas_per_sm;     /* resident CTAs per SM for the persistent grid */
-    int32_t smem_table_bytes;/* bytes of shared memory for the table window (kernel 2);
-                                -1 = none */
-    int32_t l2_persist;      /* 1 = pin the next part of the table in L2 with an access
-                                policy window, -1 = never */
+    int32_t kernel;          /* 0 auto, 1 = per-offset walk over 16-byte rows in global
+                                memory (one thread per text offset, the paper's layout),
+                                2 = pipelined: text staged by TMA into a shared-memory
+                                ring, jump table and compact nodes in shared memory */
+    int32_t threads;         /* kernel 2: threads per CTA, 64..1024, multiple of 32: one
+                                producer warp plus consumer warps; a tile is 512 bases
+                                per consumer warp */
+    int32_t ctas_per_sm;     /* kernel 2: resident CTAs per SM of the persistent grid */
+    int32_t stages;          /* kernel 2: text stages in the ring, 2..8 */
+    int32_t step_cap;        /* kernel 2: a walk still going this many steps past depth
+                                jump_k + 2 is finished by a separate tail kernel */
+    int32_t smem_table_bytes;/* kernel 2: shared memory for the window of compact nodes
+                                below the jump depth; -1 = none, 0 = all that fits */
+    int32_t l2_persist;      /* 1 = pin the nodes after the shared-memory window in L2
+                                with an access-policy window, -1 = never */
 } pfac_config;
 
 /* Set (cfg != NULL) or reset (cfg == NULL) the launch configuration of a handle.

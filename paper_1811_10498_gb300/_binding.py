@@ -45,7 +45,7 @@ class pfac_table_info(C.Structure):
 
 
 class pfac_config(C.Structure):
-    _fields_ = [("kernel", I32), ("tile_bases", I32), ("threads", I32), ("ctas_per_sm", I32),
+    _fields_ = [("kernel", I32), ("threads", I32), ("ctas_per_sm", I32), ("stages", I32), ("step_cap", I32),
                 ("smem_table_bytes", I32), ("l2_persist", I32)]
 
 

@@ -1,6 +1,7 @@
 // C ABI of the PFAC scan (include/pfac.h): table handles, upload, argument checks,
 // launch configuration and dispatch to the kernels in pfac_kernels.cu.
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -96,12 +97,12 @@ pfac_config default_config(const pfac_table *h, int64_t n_bases, bool packed, co
     (void)dp;
     pfac_config c{};
     c.kernel = (h->dt.nodes && h->dt.jump) ? 2 : 1;
-    c.tile_bases = 4096;
     c.threads = 1024;
     c.ctas_per_sm = 1;
+    c.stages = packed ? 4 : 2;
+    c.step_cap = 8;
     c.smem_table_bytes = 0;
     c.l2_persist = 0;
-    (void)packed;
     return c;
 }
 
@@ -112,22 +113,73 @@ pfac_config effective_config(pfac_table *h, int64_t n_bases, bool packed, const 
     if (!h->cfg_set) return d;
     pfac_config c = h->cfg;
     if (c.kernel == 0) c.kernel = d.kernel;
-    if (c.tile_bases == 0) c.tile_bases = d.tile_bases;
     if (c.threads == 0) c.threads = d.threads;
     if (c.ctas_per_sm == 0) c.ctas_per_sm = d.ctas_per_sm;
+    if (c.stages == 0) c.stages = d.stages;
+    if (c.step_cap == 0) c.step_cap = d.step_cap;
     return c;
 }
 
 pfac::TiledConfig tiled_config(const pfac_config &c)
 {
     pfac::TiledConfig t{};
-    t.tile = c.tile_bases;
     t.threads = c.threads;
     t.ctas_per_sm = c.ctas_per_sm;
+    t.stages = c.stages;
+    t.step_cap = c.step_cap;
     t.smem_table_bytes = c.smem_table_bytes;
     t.l2_persist = c.l2_persist;
     t.timeout_ns = 2000000000LL;
     return t;
+}
+
+// Deferred-walk scratch, one buffer per (device, stream): launches on one stream are
+// ordered, launches on different streams never share a buffer. Allocated on first use
+// and grown when a longer text needs more room.
+struct Scratch {
+    void *mem = nullptr;
+    int64_t cap = 0;
+};
+std::mutex g_scratch_mu;
+std::map<std::pair<int, cudaStream_t>, Scratch> g_scratch;
+
+// Items of deferred-walk scratch for a text of n bases. PFAC_DEFER_CAP overrides it
+// (tests use a tiny list to exercise walks that find the list full).
+int64_t defer_capacity(int64_t n)
+{
+    if (const char *env = getenv("PFAC_DEFER_CAP")) {
+        long long v = atoll(env);
+        if (v >= 1) return v;
+    }
+    return std::min<int64_t>(std::max<int64_t>(n / 256, 65536), 1LL << 24);
+}
+
+int get_scratch(int dev, cudaStream_t st, int64_t n, pfac::DeferScratch *out)
+{
+    const int64_t want = defer_capacity(n);
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    Scratch &sc = g_scratch[{dev, st}];
+    if (sc.cap < want) {
+        if (sc.mem) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess) e = cudaFree(sc.mem);
+            if (e != cudaSuccess) return cuda_fail(e);
+            sc.mem = nullptr;
+            sc.cap = 0;
+        }
+        void *m = nullptr;
+        cudaError_t e = cudaMalloc(&m, 256 + (size_t)want * pfac::defer_item_bytes());
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? PFAC_ERR_OOM : PFAC_ERR_CUDA);
+        }
+        sc.mem = m;
+        sc.cap = want;
+    }
+    out->count = (unsigned long long *)sc.mem;
+    out->items = (uint8_t *)sc.mem + 256;
+    out->cap = sc.cap;
+    return PFAC_OK;
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
@@ -143,7 +195,11 @@ int run_scan(pfac_handle h, const void *text, bool packed, int64_t n, int32_t *o
     int rc = PFAC_OK;
     if (tiled) {
         pfac::TiledConfig tc = tiled_config(c);
-        rc = pfac::launch_tiled(h->dt, text, packed, n, out, c_off, c_ids, cap, (unsigned long long *)count, tc, st, dp);
+        pfac::DeferScratch scratch{};
+        rc = get_scratch(dp.device, st, n, &scratch);
+        if (rc != PFAC_OK) return rc;
+        rc = pfac::launch_tiled(h->dt, text, packed, n, out, c_off, c_ids, cap, (unsigned long long *)count, tc,
+                                scratch, st, dp);
         if (rc == PFAC_ERR_UNSUPPORTED) tiled = false;   // e.g. a halo too long for shared memory
         else if (rc != PFAC_OK) return rc == PFAC_ERR_CUDA ? cuda_fail(cudaGetLastError()) : fail(rc);
     }
@@ -202,9 +258,9 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         const size_t s_rows = round256((size_t)T.n_states * 16);
         const size_t s_nodes = round256(T.nodes.size() * 4);
         const size_t s_out = round256((size_t)T.n_states * 4);
-        const size_t s_jump = round256(T.jump.size() * 4);
-        const size_t s_jbest = round256(T.jump_best.size() * 4);
-        h->dbytes = s_status + s_rows + s_nodes + s_out + s_jump + s_jbest;
+        const size_t jump_bytes = T.jump16.size() * 2 + T.jump32.size() * 4;
+        const size_t s_jump = round256(jump_bytes);
+        h->dbytes = s_status + s_rows + s_nodes + s_out + s_jump;
         e = cudaMalloc(&h->dmem, h->dbytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -218,14 +274,13 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         h->dt.rows = (const int32_t *)(base + off); off += s_rows;
         h->dt.nodes = T.nodes.empty() ? nullptr : (const uint32_t *)(base + off); off += s_nodes;
         h->dt.out_id = (const int32_t *)(base + off); off += s_out;
-        h->dt.jump = T.jump.empty() ? nullptr : (const uint32_t *)(base + off); off += s_jump;
-        h->dt.jump_best = T.jump_best.empty() ? nullptr : (const int32_t *)(base + off); off += s_jbest;
+        h->dt.jump = jump_bytes ? (const void *)(base + off) : nullptr; off += s_jump;
+        const void *jump_src = T.jump_wide ? (const void *)T.jump32.data() : (const void *)T.jump16.data();
         struct Up { const void *dst; const void *src; size_t bytes; } ups[] = {
             {h->dt.rows, T.rows.data(), T.rows.size() * 4},
             {h->dt.nodes, T.nodes.data(), T.nodes.size() * 4},
             {h->dt.out_id, T.out_id.data(), T.out_id.size() * 4},
-            {h->dt.jump, T.jump.data(), T.jump.size() * 4},
-            {h->dt.jump_best, T.jump_best.data(), T.jump_best.size() * 4},
+            {h->dt.jump, jump_src, jump_bytes},
         };
         e = cudaMemset(h->dt.status, 0, s_status);
         for (auto &u : ups)
@@ -240,11 +295,13 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         h->dt.n_states = T.n_states;
         h->dt.max_len = T.max_len;
         h->dt.jump_k = T.jump_k;
-        h->dt.win_lo = T.jump_k > 0 ? T.level[(size_t)std::min(T.jump_k + 1, T.max_len + 1)] : 0;
+        h->dt.jump_wide = T.jump_wide;
+        h->dt.level_k = T.jump_k > 0 ? T.level[(size_t)T.jump_k] : 0;
+        h->dt.level_k1 = T.jump_k > 0 ? T.level[(size_t)T.jump_k + 1] : 0;
         // The device copy is complete; the host keeps rows, ids and levels for export.
         std::vector<uint32_t>().swap(h->host.nodes);
-        std::vector<uint32_t>().swap(h->host.jump);
-        std::vector<int32_t>().swap(h->host.jump_best);
+        std::vector<uint16_t>().swap(h->host.jump16);
+        std::vector<uint32_t>().swap(h->host.jump32);
     }
     return h;
 }
@@ -312,9 +369,9 @@ int pfac_set_config(pfac_handle h, const pfac_config *cfg)
 {
     if (!h) return fail(PFAC_ERR_INVALID_ARG);
     if (cfg) {
-        if (cfg->kernel < 0 || cfg->kernel > 2 || cfg->tile_bases < 0 || (cfg->tile_bases & 63) ||
-            cfg->tile_bases > 32768 || cfg->threads < 0 || (cfg->threads & 31) || cfg->threads > 1024 ||
-            cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32)
+        if (cfg->kernel < 0 || cfg->kernel > 2 || cfg->threads < 0 || (cfg->threads & 31) || cfg->threads > 1024 ||
+            (cfg->threads > 0 && cfg->threads < 64) || cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32 ||
+            cfg->stages < 0 || cfg->stages == 1 || cfg->stages > 8 || cfg->step_cap < 0 || cfg->step_cap > 24)
             return fail(PFAC_ERR_INVALID_ARG);
         if (cfg->kernel == 2 && !(h->nodes_bytes > 0 && h->host.jump_k > 0)) return fail(PFAC_ERR_UNSUPPORTED);
     }

@@ -19,13 +19,24 @@ constexpr uint32_t kNodeTermBit = 0x10u;
 constexpr int kNodeFirstShift = 5;
 constexpr int64_t kMaxNodeStates = int64_t(1) << 27;
 
-// Jump table entry for the k-mer w (base j of w in bits 2j..2j+1):
-//   (e & 0x1F) == 0 : the walk over w ends before depth k; e >> 5 is the final
-//                     answer (id of the longest pattern on the way, 0 if none).
-//   otherwise       : e is the node word of the state reached at depth k, with bit 4
-//                     meaning "a pattern ends within the first k bases": the deepest
-//                     such state is jump_best[w].
+// Jump table of order k: one entry per k-mer w (base j of w in bits 2j..2j+1), the
+// index of the state the first k bases lead to inside the "level-k window", an array
+// of node words that starts with two sentinels and continues with every state of
+// depth k, in breadth-first order:
+//   0             the walk over w ends before depth k and no pattern ends on the way
+//                 (answer 0); window slot 0 is a node with no edges;
+//   1             special: a pattern ends within the first k bases (the answer, or a
+//                 prefix of it, comes from the prefix), so the walk is redone from the
+//                 root; window slot 1 is a node with all four edges, so the next step
+//                 always "continues" and sends the offset to that slower path;
+//   2 + i         the i-th state of depth k (breadth-first id level[k] + i); no pattern
+//                 ends within the first k bases.
+// Entries are 16-bit when depth k has at most 65533 states, else 32-bit.
 constexpr int kMaxJumpK = 12;
+constexpr uint32_t kJumpDead = 0;
+constexpr uint32_t kJumpSpecial = 1;
+constexpr uint32_t kJumpFirst = 2;
+constexpr int64_t kJump16MaxLevel = 65533;
 
 struct HostTables {
     int64_t n_states = 0;
@@ -38,16 +49,18 @@ struct HostTables {
     std::vector<uint32_t> nodes;     // n_states compact node words (empty if too many states)
     std::vector<int64_t> level;      // max_len + 2: states of depth d in [level[d], level[d+1])
     int32_t jump_k = 0;              // 0 = no jump table
-    std::vector<uint32_t> jump;      // 4^k entries
-    std::vector<int32_t> jump_best;  // 4^k: deepest terminal state within the k-mer (or 0)
+    int32_t jump_wide = 0;           // 1: 32-bit entries (jump32), 0: 16-bit (jump16)
+    std::vector<uint16_t> jump16;    // 4^k entries
+    std::vector<uint32_t> jump32;    // 4^k entries
 };
 
 // Status codes match pfac.h.
 int build_host_tables(const char *const *patterns, const int32_t *lengths, int32_t n,
                       int32_t jump_k_opt, HostTables *out);
 
-// Order of the jump table chosen when the caller leaves it to the library.
-int32_t auto_jump_k(int32_t n_patterns, int64_t n_states);
+// Order of the jump table chosen when the caller leaves it to the library, from the
+// number of states per depth level.
+int32_t auto_jump_k(const std::vector<int64_t> &level, int32_t max_len);
 
 }  // namespace pfac
 
@@ -62,28 +75,40 @@ struct DeviceTable {
     const int32_t *rows;       // 4 * n_states
     const uint32_t *nodes;     // n_states compact node words, or nullptr
     const int32_t *out_id;     // n_states
-    const uint32_t *jump;      // 4^jump_k, or nullptr
-    const int32_t *jump_best;  // 4^jump_k, or nullptr
+    const void *jump;          // 4^jump_k entries (uint16 or uint32), or nullptr
     int64_t n_states;
     int32_t max_len;
     int32_t jump_k;            // 0 = no jump table
-    int64_t win_lo;            // first state of depth jump_k + 1 (start of the smem window)
+    int32_t jump_wide;         // 32-bit jump entries
+    int64_t level_k;           // first state of depth jump_k (window slot kJumpFirst)
+    int64_t level_k1;          // first state of depth jump_k + 1
     int32_t *status;           // device status word (PFAC_OK or the first error)
 };
 
 struct TiledConfig {
-    int32_t tile;              // bases per tile, multiple of 64
-    int32_t threads;           // threads per CTA (multiple of 32)
+    int32_t threads;           // threads per CTA: one producer warp + consumer warps
     int32_t ctas_per_sm;
-    int32_t smem_table_bytes;  // shared-memory budget for the node window (< 0: none)
+    int32_t stages;            // text stages in the shared-memory ring (0 = default)
+    int32_t step_cap;          // steps past the jump depth before a walk is deferred (0 = default)
+    int32_t smem_table_bytes;  // shared-memory budget for the node window (< 0: none, 0: all)
     int32_t l2_persist;        // > 0: access-policy window over the nodes after the smem window
     int64_t timeout_ns;        // limit of every bounded wait
 };
+
+// Global scratch for walks deferred to the tail kernel.
+struct DeferScratch {
+    void *items;                 // cap items of defer_item_bytes() each
+    int64_t cap;
+    unsigned long long *count;   // reset by every launch
+};
+
+size_t defer_item_bytes();
 
 struct DeviceProps {
     int device;
     int num_sms;
     int smem_optin;            // max dynamic shared memory per block
+    int smem_per_sm;
     int l2_bytes;
     int persist_l2_max;
 };
@@ -104,7 +129,8 @@ int launch_walk_rows_any(const DeviceTable &t, const void *text, bool packed, in
 // Dense output when c_off == nullptr, otherwise the compacted match list.
 int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n, int32_t *out,
                  int64_t *c_off, int32_t *c_ids, int64_t cap, unsigned long long *count,
-                 const TiledConfig &cfg, cudaStream_t st, const DeviceProps &dp);
+                 const TiledConfig &cfg, const DeferScratch &scratch, cudaStream_t st,
+                 const DeviceProps &dp);
 
 // Shared memory the tiled kernel needs for a configuration (bytes), and the window
 // of nodes it would hold.

@@ -282,371 +282,513 @@ int launch_walk_rows(const DeviceTable &t, const void *text, bool packed, int64_
 }
 
 // ---------------------------------------------------------------------------
-// Kernel 2: tiled, TMA-staged, jump table + compact nodes.
+// Kernel 2: warp-specialised pipeline.
+//
+//   * one producer warp stages the text of each tile (512 bases per consumer warp)
+//     into an S-stage shared-memory ring with TMA bulk copies; full/empty mbarriers
+//     hand stages to the consumer warps and back, with bounded waits;
+//   * each consumer lane owns 16 consecutive offsets and reads one 48-base window
+//     (three packed words) from the stage. A fully unrolled, branch-free block does
+//     for every offset: one jump-table lookup (first k bases) and the next two steps
+//     through compact node words (the node of depth k comes with the jump entry, the
+//     node of depth k+1 from the shared-memory window). Results go out as four
+//     128-bit stores;
+//   * the few walks still going at depth k+2 (or that need a pattern id ending inside
+//     the jump prefix, or sit near the text end) continue in a per-lane loop, from
+//     the same register window, up to depth k+2+cap;
+//   * walks longer than that (true hits along a long pattern) are appended to a
+//     deferred list in global scratch memory and finished by a tail kernel, so no
+//     latency-bound chain ever holds a pipeline stage.
 // ---------------------------------------------------------------------------
 
-struct TiledParams {
+struct DeferItem {
+    long long gp;      // text offset of the walk
+    uint32_t s;        // state reached
+    uint32_t best;     // deepest terminal state passed (0 = none)
+    int32_t q;         // bases consumed
+    int32_t pad;
+};
+
+struct ScanParams {
     DeviceTable t;
     const void *text;
-    int64_t n;              // bases
-    int64_t n_units;        // packed: words, ASCII: bytes (what the text buffer holds)
+    int64_t n;                   // bases
+    int64_t n_units;             // packed words or ASCII bytes in the text buffer
     int32_t *out;
     int64_t *c_off;
     int32_t *c_ids;
     int64_t cap;
     unsigned long long *count;
+    DeferItem *defer;
+    int64_t defer_cap;
+    unsigned long long *defer_count;
     int64_t n_tiles;
-    int32_t tile;           // bases per tile, multiple of 64
-    int32_t jump_smem;      // jump table copied into shared memory
-    uint32_t win_lo;        // node window [win_lo, win_lo + win_len) in shared memory
-    uint32_t win_len;
-    int32_t buf_units;      // packed words (or ASCII bytes) per text buffer
-    int32_t conv_words;     // ASCII: packed words converted per tile
-    uint32_t off_jump, off_win, off_text0, off_text1, off_conv, off_inv, off_out, off_queue;
+    int32_t tile;                // bases per tile = 512 * consumers
+    int32_t consumers;           // consumer warps (the producer is warp `consumers`)
+    int32_t stages;
+    int32_t stage_units;         // packed words or ASCII bytes per stage
+    int32_t qmax;                // a walk still going after qmax bases is deferred
+    int32_t jump_smem;           // jump table copied into shared memory
+    uint32_t win_len;            // window slots in shared memory (two sentinels + states)
+    uint32_t off_jump, off_win, off_stage, stage_bytes;
     int64_t timeout_ns;
 };
 
-struct TiledLayout {
-    uint32_t off_jump, off_win, off_text0, off_text1, off_conv, off_inv, off_out, off_queue, total;
-    int32_t buf_units, conv_words;
+// Node word of state s at depth >= jump_k: window slot s - level_k + 2 when the
+// window holds it, else global memory (L2 / HBM). States above depth jump_k (root
+// walks) always come from global memory.
+__device__ __forceinline__ uint32_t node_at(uint32_t s, const uint32_t *sw, uint32_t level_k, uint32_t win_states,
+                                            const uint32_t *__restrict__ nodes)
+{
+    const uint32_t rel = s - level_k;    // wraps for states above depth jump_k
+    return rel < win_states ? sw[rel + kJumpFirst] : __ldg(nodes + s);
+}
+
+constexpr int kMaxStages = 8;
+constexpr uint32_t kBarBytes = 256;   // full[8], empty[8], abort flag
+
+// Wait for an mbarrier phase, giving up after limit_ns or when another warp of the
+// CTA has raised the abort flag. Returns false if it gave up.
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, int64_t limit_ns,
+                                              volatile uint32_t *abort_flag)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if ((int64_t)(global_timer_ns() - t0) > limit_ns) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void st_global_v4_hint(int32_t *p, int4 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+}
+
+// Continue a walk in global memory (text and nodes), for deferred walks and for
+// walks that could not be deferred. Returns the pattern id (0 if none).
+template <bool PACKED>
+__device__ int32_t walk_global(const DeviceTable &T, const void *__restrict__ text, int64_t n, int64_t gp,
+                               uint32_t s, int q, uint32_t best)
+{
+    const uint32_t *__restrict__ nodes = T.nodes;
+    uint32_t nd = __ldg(nodes + s);
+    const int64_t lim = min(n - gp, (int64_t)T.max_len);
+    while (q < lim) {
+        const int64_t pos = gp + q;
+        int c;
+        if (PACKED) {
+            c = (int)((__ldg((const uint32_t *)text + (pos >> 4)) >> ((pos & 15) * 2)) & 3u);
+        } else {
+            c = base_code_or_neg(__ldg((const uint8_t *)text + pos));
+            if (c < 0) break;
+        }
+        if (!((nd >> c) & 1u)) break;
+        s = (nd >> kNodeFirstShift) + __popc(nd & ((1u << c) - 1u));
+        nd = __ldg(nodes + s);
+        if (nd & kNodeTermBit) best = s;
+        q++;
+    }
+    return best ? __ldg(T.out_id + best) : 0;
+}
+
+// Record a non-zero result: dense output (the slot already holds 0) or the match list.
+template <bool COMPACT>
+__device__ __forceinline__ void emit_match(const ScanParams &P, int64_t gp, int32_t v)
+{
+    if (!v) return;
+    if (COMPACT) {
+        const unsigned long long k = atomicAdd(P.count, 1ull);
+        if ((int64_t)k < P.cap) {
+            P.c_off[k] = gp;
+            P.c_ids[k] = v;
+        }
+    } else {
+        P.out[gp] = v;
+    }
+}
+
+// Mask of positions j (bit j) such that bits j .. j+w-1 of `bad` are all clear.
+__device__ __forceinline__ uint32_t clear_runs(uint64_t bad, int w)
+{
+    uint64_t t = bad;
+    int have = 1;
+    while (have * 2 <= w) {
+        t |= t >> have;
+        have *= 2;
+    }
+    if (have < w) t |= t >> (w - have);
+    return (uint32_t)(~t) & 0xFFFFu;
+}
+
+template <typename JW>
+__device__ __forceinline__ uint32_t jump_entry(const ScanParams &P, const JW *sj, uint32_t kmer)
+{
+    return P.jump_smem ? (uint32_t)sj[kmer] : (uint32_t)__ldg(reinterpret_cast<const JW *>(P.t.jump) + kmer);
+}
+
+// Node word of window slot v (a jump entry). FULL: the window holds every state of
+// depth jump_k, so every slot a jump entry names is in shared memory.
+template <bool FULL>
+__device__ __forceinline__ uint32_t node_of_slot(uint32_t v, const uint32_t *sw, uint32_t win_slots, uint32_t level_k,
+                                                 const uint32_t *__restrict__ nodes)
+{
+    if (FULL) return sw[v];
+    return v < win_slots ? sw[v] : __ldg(nodes + (level_k + v - kJumpFirst));
+}
+
+template <bool PACKED, bool COMPACT, typename JW, bool FULL>
+__global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = reinterpret_cast<uint64_t *>(smem + 64);
+    volatile uint32_t *abort_flag = reinterpret_cast<volatile uint32_t *>(smem + 128);
+    const JW *sj = reinterpret_cast<const JW *>(smem + P.off_jump);
+    const uint32_t *sw = reinterpret_cast<const uint32_t *>(smem + P.off_win);
+    uint8_t *stage0 = smem + P.off_stage;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const DeviceTable &T = P.t;
+    const int K = T.jump_k;
+    const uint32_t kmask = (uint32_t)((1ull << (2 * K)) - 1ull);
+    const int S = P.stages;
+    const int64_t n = P.n;
+    const uint32_t level_k = (uint32_t)T.level_k;
+    const uint32_t win_slots = P.win_len;                 // sentinels included
+    const uint32_t win_states = P.win_len - kJumpFirst;   // states of depth >= jump_k held
+
+    if (tid == 0) {
+        for (int i = 0; i < S; i++) {
+            mbar_init(smem_addr(&full[i]), 1);
+            mbar_init(smem_addr(&empty[i]), (uint32_t)P.consumers);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    {
+        // jump table and node window, resident for the whole persistent kernel
+        if (P.jump_smem) {
+            const int64_t bytes = (int64_t)sizeof(JW) << (2 * K);
+            uint8_t *dst = smem + P.off_jump;
+            const uint8_t *src = (const uint8_t *)T.jump;
+            for (int64_t i = 16 * (int64_t)tid; i + 16 <= bytes; i += 16 * (int64_t)blockDim.x)
+                *reinterpret_cast<uint4 *>(dst + i) = __ldg(reinterpret_cast<const uint4 *>(src + i));
+            for (int64_t i = (bytes & ~(int64_t)15) + tid; i < bytes; i += blockDim.x) dst[i] = src[i];
+        }
+        uint32_t *ww = reinterpret_cast<uint32_t *>(smem + P.off_win);
+        if (tid == 0) {
+            ww[kJumpDead] = 0u;              // no edges: the walk ends
+            ww[kJumpSpecial] = kNodeMaskBits; // every edge: go to the full walk
+        }
+        for (uint32_t i = tid; i < win_states; i += blockDim.x) ww[kJumpFirst + i] = __ldg(T.nodes + level_k + i);
+    }
+    __syncthreads();
+
+    const int unit = PACKED ? 4 : 1;
+    const int64_t tile_units = PACKED ? (P.tile >> 4) : P.tile;
+
+    if (warp == P.consumers) {
+        // ---------------- producer warp ----------------
+        if (lane == 0) {
+            int k = 0;
+            for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, k++) {
+                const int st = k % S;
+                if (k >= S && !wait_or_abort(smem_addr(&empty[st]), (uint32_t)(((k / S) - 1) & 1), P.timeout_ns,
+                                             abort_flag))
+                    break;
+                const int64_t u0 = t * tile_units;
+                const int64_t cnt = min((int64_t)P.stage_units, P.n_units - u0);
+                const uint32_t bytes = (uint32_t)((cnt * unit) & ~(int64_t)15);
+                uint8_t *dst = stage0 + (size_t)st * P.stage_bytes;
+                // the ragged (< 16-byte) tail by plain loads, published by the arrive below
+                for (int64_t b = bytes; b < cnt * unit; b++) dst[b] = __ldg((const uint8_t *)P.text + u0 * unit + b);
+                mbar_arrive_expect_tx(smem_addr(&full[st]), bytes);
+                if (bytes) bulk_load(smem_addr(dst), (const uint8_t *)P.text + u0 * unit, bytes, smem_addr(&full[st]));
+            }
+            // Let every copy this CTA issued land before the CTA can exit (bounded).
+            for (int i = 0; i < S && i < k; i++) {
+                const int kk = k - 1 - i;
+                mbar_wait_bounded(smem_addr(&full[kk % S]), (uint32_t)((kk / S) & 1), P.timeout_ns);
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumer warps ----------------
+    const uint64_t pol = policy_evict_first();
+    int k = 0;
+    for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, k++) {
+        const int st = k % S;
+        if (!wait_or_abort(smem_addr(&full[st]), (uint32_t)((k / S) & 1), P.timeout_ns, abort_flag)) {
+            if (lane == 0) record_error(T.status, PFAC_ERR_TIMEOUT);
+            return;
+        }
+        const uint8_t *stage = stage0 + (size_t)st * P.stage_bytes;
+        const int p_rel = warp * 512 + lane * 16;
+        const int64_t gp0 = t * (int64_t)P.tile + p_rel;
+        // 48-base window: packed words and a mask of bases that cannot be read (past
+        // the text end, or ASCII bytes outside ACGT).
+        uint32_t x0 = 0, x1 = 0, x2 = 0;
+        const int64_t rem = n - gp0;
+        uint64_t bad = rem < 48 ? (rem > 0 ? (~0ull << rem) : ~0ull) : 0ull;
+        if (rem > 0) {
+            if (PACKED) {
+                const uint32_t *w = reinterpret_cast<const uint32_t *>(stage) + (p_rel >> 4);
+                x0 = w[0];
+                x1 = w[1];
+                x2 = w[2];
+            } else {
+                const uint4 *r = reinterpret_cast<const uint4 *>(stage + p_rel);
+                uint32_t b0, b1, b2;
+                x0 = pack16(r[0], &b0);
+                x1 = pack16(r[1], &b1);
+                x2 = pack16(r[2], &b2);
+                bad |= (uint64_t)b0 | ((uint64_t)b1 << 16) | ((uint64_t)b2 << 32);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&empty[st]));   // this warp is done with the stage
+        bad &= 0xFFFFFFFFFFFFull;
+        const uint32_t valid = rem >= 16 ? 0xFFFFu : (rem > 0 ? ((1u << rem) - 1u) : 0u);
+        const uint32_t fast = clear_runs(bad, K + 1) & valid;   // jump + one step readable
+
+        // Every offset: jump over the first K bases, then one step through the node
+        // the jump lands on. The walk goes on only where that step exists (or the
+        // entry is the special one, whose sentinel node has every edge).
+        uint32_t pend = 0;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const uint32_t win = __funnelshift_r(x0, x1, 2 * j);     // bases j .. j+15
+            const uint32_t v = jump_entry<JW>(P, sj, win & kmask);
+            const uint32_t nd = node_of_slot<FULL>(v, sw, win_slots, level_k, T.nodes);
+            const uint32_t c = (win >> (2 * K)) & 3u;
+            pend |= ((nd >> c) & 1u) << j;
+        }
+        pend &= fast;
+        pend |= valid & ~fast;     // these walk from the root
+
+        if (!COMPACT && valid) {
+            if (valid == 0xFFFFu) {
+                int32_t *o = P.out + gp0;
+                const int4 z = make_int4(0, 0, 0, 0);
+                st_global_v4_hint(o + 0, z, pol);
+                st_global_v4_hint(o + 4, z, pol);
+                st_global_v4_hint(o + 8, z, pol);
+                st_global_v4_hint(o + 12, z, pol);
+            } else {
+                for (int j = 0; j < 16; j++)
+                    if ((valid >> j) & 1u) P.out[gp0 + j] = 0;
+            }
+        }
+
+        // -------- walks that go on --------
+        // Spread them over the warp: item r of the warp (in lane order, then offset
+        // order) goes to lane r mod 32 in round r / 32. The owner's window comes by
+        // shuffle.
+        const uint32_t cnt = __popc(pend);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        const uint32_t excl = incl - cnt;
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+            const uint32_t r = r0 + lane;
+            // owner = the last lane whose first item is <= r
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint32_t e = __shfl_sync(0xFFFFFFFFu, excl, owner + step);
+                if (e <= r) owner += step;
+            }
+            const uint32_t om = __shfl_sync(0xFFFFFFFFu, pend, owner);
+            const uint32_t oe = __shfl_sync(0xFFFFFFFFu, excl, owner);
+            const uint32_t ofast = __shfl_sync(0xFFFFFFFFu, fast, owner);
+            const uint32_t ox0 = __shfl_sync(0xFFFFFFFFu, x0, owner);
+            const uint32_t ox1 = __shfl_sync(0xFFFFFFFFu, x1, owner);
+            const uint32_t ox2 = __shfl_sync(0xFFFFFFFFu, x2, owner);
+            const uint32_t obad_lo = __shfl_sync(0xFFFFFFFFu, (uint32_t)bad, owner);
+            const uint32_t obad_hi = __shfl_sync(0xFFFFFFFFu, (uint32_t)(bad >> 32), owner);
+            if (r >= total) continue;
+            // the (r - oe)-th set bit of the owner's mask (r - oe < popcount by construction)
+            uint32_t m = om;
+            for (uint32_t i = r - oe; i > 0; i--) m &= m - 1u;
+            const int j = (__ffs(m) - 1) & 15;
+            const int64_t gp = t * (int64_t)P.tile + warp * 512 + owner * 16 + j;
+            const uint64_t lo64 = ((uint64_t)ox1 << 32) | ox0;
+            uint64_t rest = j ? ((lo64 >> (2 * j)) | ((uint64_t)ox2 << (64 - 2 * j))) : lo64;   // bases j..j+31
+            const uint64_t badj = (((uint64_t)obad_hi << 32) | obad_lo) >> j;
+            const int wlim = badj ? __ffsll((long long)badj) - 1 : 48 - j;
+            const int lim = min(wlim, T.max_len);
+            uint32_t s = 0, nd, best = 0;
+            int q = 0;
+            const uint32_t v = ((ofast >> j) & 1u) ? jump_entry<JW>(P, sj, (uint32_t)rest & kmask) : kJumpSpecial;
+            if (v != kJumpSpecial) {
+                s = level_k + v - kJumpFirst;
+                nd = node_of_slot<FULL>(v, sw, win_slots, level_k, T.nodes);
+                rest >>= 2 * K;
+                q = K;
+            } else {
+                nd = __ldg(T.nodes);     // the root
+            }
+            bool deferred = false;
+            while (q < lim) {
+                const uint32_t c = (uint32_t)rest & 3u;
+                rest >>= 2;
+                if (!((nd >> c) & 1u)) break;
+                s = (nd >> kNodeFirstShift) + __popc(nd & ((1u << c) - 1u));
+                nd = node_at(s, sw, level_k, win_states, T.nodes);
+                q++;
+                if (nd & kNodeTermBit) best = s;
+                if (q >= P.qmax && q < lim && (nd & kNodeMaskBits)) {
+                    // long walk: finish it in the tail kernel (or here if the list is full)
+                    const unsigned long long di = atomicAdd(P.defer_count, 1ull);
+                    if ((int64_t)di < P.defer_cap) {
+                        DeferItem it;
+                        it.gp = gp;
+                        it.s = s;
+                        it.best = best;
+                        it.q = q;
+                        it.pad = 0;
+                        P.defer[di] = it;
+                    } else {
+                        emit_match<COMPACT>(P, gp, walk_global<PACKED>(T, P.text, n, gp, s, q, best));
+                    }
+                    deferred = true;
+                    break;
+                }
+            }
+            // A walk that stops here met a missing edge, an unreadable base or the
+            // deepest level: qmax <= 32 < 48 - j, so the window never runs out first.
+            if (!deferred && best) emit_match<COMPACT>(P, gp, __ldg(T.out_id + best));
+        }
+    }
+}
+
+// Deferred walks: one thread per item.
+template <bool PACKED, bool COMPACT>
+__global__ void __launch_bounds__(256) tail_kernel(const ScanParams P)
+{
+    const unsigned long long cnt = *P.defer_count;
+    const int64_t m = min((int64_t)cnt, P.defer_cap);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const DeferItem it = P.defer[i];
+        emit_match<COMPACT>(P, it.gp, walk_global<PACKED>(P.t, P.text, P.n, it.gp, it.s, it.q, it.best));
+    }
+}
+
+struct ScanLayout {
+    uint32_t off_jump, off_win, off_stage, stage_bytes, total;
+    int32_t stage_units;
 };
 
-static inline uint32_t align16(uint64_t x) { return (uint32_t)((x + 15) & ~(uint64_t)15); }
+static inline uint32_t align128(uint64_t x) { return (uint32_t)((x + 127) & ~(uint64_t)127); }
 
-// Shared memory without the node window. Layout: [mbarriers, queue count][jump]
-// [window][text 0][text 1][converted text][invalid mask][staged results][queue].
-static TiledLayout tiled_layout(int32_t tile, int32_t max_len, int32_t jump_k, bool jump_smem, bool packed,
-                                uint32_t win_len)
+static ScanLayout scan_layout(int consumers, int stages, int64_t jump_smem_bytes, bool packed, uint32_t win_slots)
 {
-    TiledLayout L{};
-    // packed words a tile's walks can touch: tile, halo of max_len bases, one word of
-    // look-ahead for the 16-base register window.
-    const int32_t words = tile / 16 + (max_len + 31) / 16 + 1;
-    uint64_t off = 32;
+    ScanLayout L{};
+    const int64_t tile = 512LL * consumers;
+    uint64_t off = kBarBytes;
     L.off_jump = (uint32_t)off;
-    if (jump_smem) off += align16((uint64_t)4 << (2 * jump_k));
+    off += align128((uint64_t)jump_smem_bytes);
     L.off_win = (uint32_t)off;
-    off += align16((uint64_t)win_len * 4);
-    if (packed) {
-        L.buf_units = words;
-        L.conv_words = 0;
-        L.off_text0 = (uint32_t)off; off += align16((uint64_t)words * 4);
-        L.off_text1 = (uint32_t)off; off += align16((uint64_t)words * 4);
-        L.off_conv = L.off_inv = 0;
-    } else {
-        L.buf_units = words * 16;   // bytes
-        L.conv_words = words;
-        L.off_text0 = (uint32_t)off; off += align16((uint64_t)words * 16);
-        L.off_text1 = (uint32_t)off; off += align16((uint64_t)words * 16);
-        L.off_conv = (uint32_t)off; off += align16((uint64_t)words * 4);
-        // one bit per base: (words + 1) / 2 words, plus two sentinel words (four
-        // 16-bit halves set to "invalid" past the converted bases)
-        L.off_inv = (uint32_t)off; off += align16((((uint64_t)words + 1) / 2 + 2) * 4);
-    }
-    L.off_out = (uint32_t)off; off += align16((uint64_t)tile * 4);
-    L.off_queue = (uint32_t)off; off += align16((uint64_t)tile * 8);
+    off += align128((uint64_t)win_slots * 4);
+    // a lane reads 48 bases from its first offset: 2 words (32 bytes) past the tile
+    L.stage_units = packed ? (int32_t)(tile / 16 + 4) : (int32_t)(tile + 48);
+    L.stage_bytes = align128((uint64_t)L.stage_units * (packed ? 4 : 1));
+    L.off_stage = (uint32_t)off;
+    off += (uint64_t)L.stage_bytes * stages;
     L.total = (uint32_t)off;
     return L;
 }
 
-// Consecutive valid bases from p (at most maxrun), from the invalid-byte mask.
-__device__ __forceinline__ int valid_run(const uint32_t *inv, int p, int maxrun)
-{
-    int w = p >> 5;
-    uint32_t bits = inv[w] >> (p & 31);
-    int run = 32 - (p & 31);
-    if (bits) return min(__ffs(bits) - 1, maxrun);
-    while (run < maxrun) {
-        bits = inv[++w];
-        if (bits) return min(run + __ffs(bits) - 1, maxrun);
-        run += 32;
-    }
-    return maxrun;
-}
+static int consumers_of(const TiledConfig &cfg) { return cfg.threads / 32 - 1; }
+static int stages_of(const TiledConfig &cfg, bool packed) { return cfg.stages > 0 ? cfg.stages : (packed ? 4 : 2); }
 
-__device__ __forceinline__ uint32_t window16(const uint32_t *tw, int pos)
-{
-    return __funnelshift_r(tw[pos >> 4], tw[(pos >> 4) + 1], (pos & 15) * 2);
-}
-
-__device__ __forceinline__ uint32_t node_at(uint32_t s, const uint32_t *sw, uint32_t win_lo, uint32_t win_len,
-                                            const uint32_t *__restrict__ nodes)
-{
-    const uint32_t rel = s - win_lo;
-    return rel < win_len ? sw[rel] : __ldg(nodes + s);
-}
-
-template <bool PACKED, bool COMPACT>
-__global__ void __launch_bounds__(1024, 1) tiled_kernel(const TiledParams P)
-{
-    extern __shared__ __align__(128) uint8_t smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-    uint32_t *qcount = reinterpret_cast<uint32_t *>(smem + 16);
-    uint32_t *sj = reinterpret_cast<uint32_t *>(smem + P.off_jump);
-    uint32_t *sw = reinterpret_cast<uint32_t *>(smem + P.off_win);
-    int32_t *out_s = reinterpret_cast<int32_t *>(smem + P.off_out);
-    uint2 *queue = reinterpret_cast<uint2 *>(smem + P.off_queue);
-    uint32_t *conv = reinterpret_cast<uint32_t *>(smem + P.off_conv);
-    uint32_t *inv = reinterpret_cast<uint32_t *>(smem + P.off_inv);
-
-    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
-    const DeviceTable &T = P.t;
-    const int K = T.jump_k;
-    const uint32_t kmask = (K >= 16) ? 0xFFFFFFFFu : ((1u << (2 * K)) - 1u);
-    const int max_len = T.max_len;
-    const int64_t n = P.n;
-    const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
-    const uint32_t text_off[2] = {P.off_text0, P.off_text1};
-
-    if (tid == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
-        fence_mbar_init();
-    }
-    // Table parts kept in shared memory for the whole (persistent) kernel.
-    if (P.jump_smem) {
-        const int64_t E = (int64_t)1 << (2 * K);
-        for (int64_t i = tid; i < E; i += nthr) sj[i] = __ldg(T.jump + i);
-    }
-    for (uint32_t i = tid; i < P.win_len; i += nthr) sw[i] = __ldg(T.nodes + P.win_lo + i);
-    __syncthreads();
-
-    const int unit_bytes = PACKED ? 4 : 1;
-    const int64_t tile_units = PACKED ? (P.tile >> 4) : P.tile;  // units per tile step
-    uint64_t policy = 0;
-    if (tid == 0) policy = policy_evict_first();
-
-    // Issue the staging copy of tile `tt` into buffer `b`; returns the units that the
-    // threads must still load by hand (the ragged < 16-byte tail).
-    auto issue = [&](int64_t tt, int b) {
-        const int64_t u0 = tt * tile_units;
-        const int64_t cnt = min((int64_t)P.buf_units, P.n_units - u0);
-        const uint32_t bytes = (uint32_t)((cnt * unit_bytes) & ~(int64_t)15);
-        const uint32_t bar = b ? bar1 : bar0;
-        fence_proxy_async();
-        mbar_arrive_expect_tx(bar, bytes);
-        if (bytes) bulk_load(smem_addr(smem + text_off[b]), (const uint8_t *)P.text + u0 * unit_bytes, bytes, bar);
-    };
-
-    int64_t t = blockIdx.x;
-    if (tid == 0 && t < P.n_tiles) issue(t, 0);
-
-    for (int it = 0; t < P.n_tiles; t += gridDim.x, it++) {
-        const int b = it & 1;
-        const uint32_t parity = (uint32_t)((it >> 1) & 1);
-        const int64_t b0 = t * (int64_t)P.tile;
-        const int tile_len = (int)min((int64_t)P.tile, n - b0);
-        const int64_t tn = t + gridDim.x;
-        if (tid == 0 && tn < P.n_tiles) issue(tn, b ^ 1);
-
-        const bool ok = mbar_wait_bounded(b ? bar1 : bar0, parity, P.timeout_ns);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                record_error(T.status, PFAC_ERR_TIMEOUT);
-                // Let this CTA's own copies finish (again with a limit) before leaving.
-                mbar_wait_bounded(b ? bar1 : bar0, parity, P.timeout_ns);
-                if (tn < P.n_tiles) mbar_wait_bounded(b ? bar0 : bar1, (uint32_t)(((it + 1) >> 1) & 1), P.timeout_ns);
-                bulk_wait_all();
-            }
-            return;
-        }
-        // Ragged tail of the staged text (the bulk copy moves whole 16-byte chunks).
-        {
-            const int64_t u0 = t * tile_units;
-            const int64_t cnt = min((int64_t)P.buf_units, P.n_units - u0);
-            const int64_t bulk_units = ((cnt * unit_bytes) & ~(int64_t)15) / unit_bytes;
-            uint8_t *buf = smem + text_off[b];
-            if (PACKED) {
-                if (tid < cnt - bulk_units)
-                    reinterpret_cast<uint32_t *>(buf)[bulk_units + tid] =
-                        __ldg((const uint32_t *)P.text + u0 + bulk_units + tid);
-            } else {
-                if (tid < cnt - bulk_units) buf[bulk_units + tid] = __ldg((const uint8_t *)P.text + u0 + bulk_units + tid);
-            }
-            if (!PACKED) {
-                __syncthreads();
-                // ASCII -> packed words + invalid mask; bytes past the loaded ones are invalid.
-                const uint4 *raw = reinterpret_cast<const uint4 *>(buf);
-                uint16_t *inv16 = reinterpret_cast<uint16_t *>(inv);
-                for (int w = tid; w < P.conv_words; w += nthr) {
-                    uint32_t badm;
-                    const uint32_t word = pack16(raw[w], &badm);
-                    const int64_t have = cnt - (int64_t)w * 16;
-                    if (have < 16) badm |= have <= 0 ? 0xFFFFu : (0xFFFFu << have) & 0xFFFFu;
-                    conv[w] = word;
-                    inv16[w] = (uint16_t)badm;
-                }
-                if (tid < 4) inv16[P.conv_words + tid] = 0xFFFFu;
-            }
-        }
-        if (tid == 0) {
-            if (!COMPACT) bulk_wait_read_all();   // previous tile's result store has read out_s
-            *qcount = 0;
-        }
-        __syncthreads();
-
-        const uint32_t *tw = PACKED ? reinterpret_cast<const uint32_t *>(smem + text_off[b]) : conv;
-
-        // ---- phase 1: jump lookup + one step for every offset -------------------
-        for (int r0 = 0; r0 < tile_len; r0 += nthr) {
-            const int p = r0 + tid;
-            bool pend = false;
-            uint32_t item_s = 0, item_f = 0;
-            if (p < tile_len) {
-                const int64_t gp = b0 + p;
-                const int maxrun = (int)min(n - gp, (int64_t)max_len);
-                const int lim = PACKED ? maxrun : valid_run(inv, p, maxrun);
-                int32_t res = 0;
-                if (K > 0 && lim >= K) {
-                    const uint32_t win = window16(tw, p);
-                    const uint32_t kmer = win & kmask;
-                    const uint32_t e = P.jump_smem ? sj[kmer] : __ldg(T.jump + kmer);
-                    if ((e & 0x1Fu) == 0) {
-                        res = (int32_t)(e >> kNodeFirstShift);
-                    } else {
-                        const bool pf = (e & kNodeTermBit) != 0;
-                        if (lim > K) {
-                            const uint32_t c = (win >> (2 * K)) & 3u;
-                            if ((e >> c) & 1u) {
-                                pend = true;
-                                item_s = (e >> kNodeFirstShift) + __popc(e & ((1u << c) - 1u));
-                                item_f = pf;
-                            }
-                        }
-                        if (!pend && pf) {
-                            const int32_t bs = __ldg(T.jump_best + kmer);
-                            res = bs ? __ldg(T.out_id + bs) : 0;
-                        }
-                    }
-                } else if (lim > 0) {
-                    pend = true;      // too close to the end (or no jump table): walk from the root
-                }
-                if (!pend) out_s[p] = res;
-            }
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, pend);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                uint32_t base = 0;
-                if (lane == leader) base = atomicAdd(qcount, (uint32_t)__popc(m));
-                base = __shfl_sync(0xFFFFFFFFu, base, leader);
-                if (pend) queue[base + __popc(m & ((1u << lane) - 1u))] = make_uint2(item_s, (uint32_t)p | (item_f << 31));
-            }
-        }
-        __syncthreads();
-
-        // ---- phase 2: walk the queued offsets ----------------------------------
-        const int nq = (int)*qcount;
-        for (int i = tid; i < nq; i += nthr) {
-            const uint2 item = queue[i];
-            const int p = (int)(item.y & 0x7FFFFFFFu);
-            uint32_t s = item.x;
-            const int64_t gp = b0 + p;
-            const int maxrun = (int)min(n - gp, (int64_t)max_len);
-            const int lim = PACKED ? maxrun : valid_run(inv, p, maxrun);
-            int q;
-            uint32_t best = 0, nd;
-            if (s == 0) {
-                q = 0;
-                nd = node_at(0, sw, P.win_lo, P.win_len, T.nodes);
-            } else {
-                q = K + 1;
-                if (item.y >> 31) best = (uint32_t)__ldg(T.jump_best + (window16(tw, p) & kmask));
-                nd = node_at(s, sw, P.win_lo, P.win_len, T.nodes);
-                if (nd & kNodeTermBit) best = s;
-            }
-            uint32_t win = 0;
-            int avail = 0;
-            while (q < lim) {
-                if (avail == 0) { win = window16(tw, p + q); avail = 16; }
-                const uint32_t c = win & 3u;
-                win >>= 2;
-                avail--;
-                if (!((nd >> c) & 1u)) break;
-                s = (nd >> kNodeFirstShift) + __popc(nd & ((1u << c) - 1u));
-                nd = node_at(s, sw, P.win_lo, P.win_len, T.nodes);
-                if (nd & kNodeTermBit) best = s;
-                q++;
-            }
-            out_s[p] = best ? __ldg(T.out_id + best) : 0;
-        }
-
-        // ---- results ------------------------------------------------------------
-        if (!COMPACT) {
-            fence_proxy_async();
-            __syncthreads();
-            const int bulk_n = tile_len & ~3;
-            if (tid == 0 && bulk_n) {
-                bulk_store(P.out + b0, smem_addr(out_s), (uint32_t)bulk_n * 4u, policy);
-                bulk_commit();
-            }
-            if (tid < tile_len - bulk_n) P.out[b0 + bulk_n + tid] = out_s[bulk_n + tid];
-        } else {
-            __syncthreads();
-            for (int r0 = (tid & ~31); r0 < tile_len; r0 += nthr) {
-                const int p = r0 + lane;
-                const int32_t v = p < tile_len ? out_s[p] : 0;
-                const unsigned m = __ballot_sync(0xFFFFFFFFu, v != 0);
-                if (m) {
-                    const int leader = __ffs(m) - 1;
-                    unsigned long long base = 0;
-                    if (lane == leader) base = atomicAdd(P.count, (unsigned long long)__popc(m));
-                    base = __shfl_sync(0xFFFFFFFFu, base, leader);
-                    if (v) {
-                        const int64_t k = (int64_t)base + __popc(m & ((1u << lane) - 1u));
-                        if (k < P.cap) { P.c_off[k] = b0 + p; P.c_ids[k] = v; }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-    if (tid == 0 && !COMPACT) bulk_wait_all();
-}
-
+// Shared memory per CTA: the jump table when it fits beside the stages, then as many
+// states of depth >= jump_k as the remaining budget holds.
 int64_t tiled_smem_bytes(const DeviceTable &t, const TiledConfig &cfg, bool packed, int32_t *win_len_out,
                          int32_t *jump_smem_out, const DeviceProps &dp)
 {
-    const bool jump_smem = t.jump_k > 0 && t.jump_k <= 7;
-    const TiledLayout base = tiled_layout(cfg.tile, t.max_len, t.jump_k, jump_smem, packed, 0);
-    int64_t room = (int64_t)dp.smem_optin - base.total;
-    if (room < 0) return -1;
-    int64_t win = 0;
-    if (t.nodes && cfg.smem_table_bytes >= 0) {
-        int64_t budget = cfg.smem_table_bytes > 0 ? std::min<int64_t>(cfg.smem_table_bytes, room) : room;
-        win = std::min<int64_t>(budget / 4, t.n_states - t.win_lo);
-        if (win < 0) win = 0;
+    const int C = consumers_of(cfg);
+    const int S = stages_of(cfg, packed);
+    const int64_t per_cta = (int64_t)dp.smem_per_sm / std::max(1, cfg.ctas_per_sm) - 1024;
+    const int64_t limit = std::min<int64_t>(dp.smem_optin, per_cta);
+    const int64_t jbytes = (t.jump_wide ? 4LL : 2LL) << (2 * t.jump_k);
+    const int64_t base = scan_layout(C, S, 0, packed, kJumpFirst).total;
+    const bool jump_smem = base + align128((uint64_t)jbytes) <= limit;
+    const int64_t fixed = scan_layout(C, S, jump_smem ? jbytes : 0, packed, kJumpFirst).total;
+    if (fixed > limit) return -1;
+    int64_t states = 0;
+    if (cfg.smem_table_bytes >= 0) {
+        const int64_t room = limit - fixed;
+        const int64_t budget = cfg.smem_table_bytes > 0 ? std::min<int64_t>(cfg.smem_table_bytes, room) : room;
+        states = std::max<int64_t>(0, std::min<int64_t>(budget / 4, t.n_states - t.level_k));
+        while (states > 0 && scan_layout(C, S, jump_smem ? jbytes : 0, packed, (uint32_t)(kJumpFirst + states)).total > limit)
+            states -= 32;
+        states = std::max<int64_t>(states, 0);
     }
-    if (win_len_out) *win_len_out = (int32_t)win;
+    if (win_len_out) *win_len_out = (int32_t)(kJumpFirst + states);
     if (jump_smem_out) *jump_smem_out = jump_smem;
-    return tiled_layout(cfg.tile, t.max_len, t.jump_k, jump_smem, packed, (uint32_t)win).total;
+    return scan_layout(C, S, jump_smem ? jbytes : 0, packed, (uint32_t)(kJumpFirst + states)).total;
 }
 
-template <bool PACKED, bool COMPACT>
-static int launch_tiled_t(const TiledParams &P, int grid, int threads, uint32_t smem, cudaStream_t st)
+template <bool PACKED, bool COMPACT, typename JW, bool FULL>
+static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t smem, int tail_grid, cudaStream_t st)
 {
-    auto kern = tiled_kernel<PACKED, COMPACT>;
+    auto kern = scan_kernel<PACKED, COMPACT, JW, FULL>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return PFAC_ERR_CUDA;
     kern<<<grid, threads, smem, st>>>(P);
+    if (cudaGetLastError() != cudaSuccess) return PFAC_ERR_CUDA;
+    tail_kernel<PACKED, COMPACT><<<tail_grid, 256, 0, st>>>(P);
     return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
 }
 
+// 16-bit entries with every depth-k state in shared memory is the fast case; other
+// tables take the general kernel (32-bit entries, window lookups that may miss).
+template <bool PACKED, bool COMPACT>
+static int launch_scan_w(const ScanParams &P, bool wide, bool full, int grid, int threads, uint32_t smem,
+                         int tail_grid, cudaStream_t st)
+{
+    if (!wide && full) return launch_scan_t<PACKED, COMPACT, uint16_t, true>(P, grid, threads, smem, tail_grid, st);
+    return wide ? launch_scan_t<PACKED, COMPACT, uint32_t, false>(P, grid, threads, smem, tail_grid, st)
+                : launch_scan_t<PACKED, COMPACT, uint16_t, false>(P, grid, threads, smem, tail_grid, st);
+}
+
 int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n, int32_t *out, int64_t *c_off,
-                 int32_t *c_ids, int64_t cap, unsigned long long *count, const TiledConfig &cfg, cudaStream_t st,
-                 const DeviceProps &dp)
+                 int32_t *c_ids, int64_t cap, unsigned long long *count, const TiledConfig &cfg,
+                 const DeferScratch &scratch, cudaStream_t st, const DeviceProps &dp)
 {
     const bool compact = c_off != nullptr;
     if (compact && cudaMemsetAsync(count, 0, sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     if (n == 0) return PFAC_OK;
-    if (!t.nodes || cfg.tile <= 0 || (cfg.tile & 63) || cfg.threads <= 0 || (cfg.threads & 31) ||
-        cfg.threads > 1024 || cfg.tile > 32768)
+    const int C = consumers_of(cfg);
+    const int S = stages_of(cfg, packed);
+    if (!t.nodes || !t.jump || t.jump_k < 1 || t.jump_k > kMaxJumpK || C < 1 || (cfg.threads & 31) ||
+        cfg.threads > 1024 || S < 2 || S > kMaxStages || !scratch.items || !scratch.count)
         return PFAC_ERR_INVALID_ARG;
     int32_t win_len = 0, jump_smem = 0;
     const int64_t smem = tiled_smem_bytes(t, cfg, packed, &win_len, &jump_smem, dp);
     if (smem < 0 || smem > dp.smem_optin) return PFAC_ERR_UNSUPPORTED;
-    const bool jsm = jump_smem != 0;
-    const TiledLayout L = tiled_layout(cfg.tile, t.max_len, t.jump_k, jsm, packed, (uint32_t)win_len);
-    TiledParams P{};
+    const int64_t jbytes = (t.jump_wide ? 4LL : 2LL) << (2 * t.jump_k);
+    const ScanLayout L = scan_layout(C, S, jump_smem ? jbytes : 0, packed, (uint32_t)win_len);
+    if (cudaMemsetAsync(scratch.count, 0, sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
+    ScanParams P{};
     P.t = t;
     P.text = text;
     P.n = n;
@@ -656,31 +798,37 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     P.c_ids = c_ids;
     P.cap = cap;
     P.count = count;
-    P.tile = cfg.tile;
-    P.n_tiles = (n + cfg.tile - 1) / cfg.tile;
-    P.jump_smem = jsm;
-    P.win_lo = (uint32_t)t.win_lo;
+    P.defer = (DeferItem *)scratch.items;
+    P.defer_cap = scratch.cap;
+    P.defer_count = scratch.count;
+    P.tile = 512 * C;
+    P.n_tiles = (n + P.tile - 1) / P.tile;
+    P.consumers = C;
+    P.stages = S;
+    P.stage_units = L.stage_units;
+    // deferred once this many bases are consumed (the register window holds 32)
+    P.qmax = std::min(32, t.jump_k + 1 + (cfg.step_cap > 0 ? cfg.step_cap : 8));
+    P.jump_smem = jump_smem;
     P.win_len = (uint32_t)win_len;
-    P.buf_units = L.buf_units;
-    P.conv_words = L.conv_words;
     P.off_jump = L.off_jump;
     P.off_win = L.off_win;
-    P.off_text0 = L.off_text0;
-    P.off_text1 = L.off_text1;
-    P.off_conv = L.off_conv;
-    P.off_inv = L.off_inv;
-    P.off_out = L.off_out;
-    P.off_queue = L.off_queue;
+    P.off_stage = L.off_stage;
+    P.stage_bytes = L.stage_bytes;
     P.timeout_ns = cfg.timeout_ns > 0 ? cfg.timeout_ns : 2000000000LL;
     const int64_t grid64 = std::min<int64_t>(P.n_tiles, (int64_t)dp.num_sms * std::max(1, cfg.ctas_per_sm));
     const int grid = (int)std::max<int64_t>(1, grid64);
-    if (packed) {
-        return compact ? launch_tiled_t<true, true>(P, grid, cfg.threads, L.total, st)
-                       : launch_tiled_t<true, false>(P, grid, cfg.threads, L.total, st);
-    }
-    return compact ? launch_tiled_t<false, true>(P, grid, cfg.threads, L.total, st)
-                   : launch_tiled_t<false, false>(P, grid, cfg.threads, L.total, st);
+    const int tail_grid = dp.num_sms * 4;
+    const bool wide = t.jump_wide != 0;
+    // every state of depth jump_k in the window (slots up to kJumpFirst + that count)
+    const bool full = (int64_t)win_len >= kJumpFirst + t.level_k1 - t.level_k;
+    if (packed)
+        return compact ? launch_scan_w<true, true>(P, wide, full, grid, cfg.threads, L.total, tail_grid, st)
+                       : launch_scan_w<true, false>(P, wide, full, grid, cfg.threads, L.total, tail_grid, st);
+    return compact ? launch_scan_w<false, true>(P, wide, full, grid, cfg.threads, L.total, tail_grid, st)
+                   : launch_scan_w<false, false>(P, wide, full, grid, cfg.threads, L.total, tail_grid, st);
 }
+
+size_t defer_item_bytes() { return sizeof(DeferItem); }
 
 // ---------------------------------------------------------------------------
 // Timeout probe (exercises the bounded wait without any fault or hang).
@@ -713,6 +861,7 @@ int get_device_props(DeviceProps *p)
     p->device = dev;
     if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->l2_bytes, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->persist_l2_max, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess)
         return PFAC_ERR_CUDA;

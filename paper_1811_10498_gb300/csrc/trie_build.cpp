@@ -45,14 +45,20 @@ constexpr int64_t kMaxStates = int64_t(0x7FFFFFFF);
 
 }  // namespace
 
-int32_t auto_jump_k(int32_t n_patterns, int64_t n_states)
+int32_t auto_jump_k(const std::vector<int64_t> &level, int32_t max_len)
 {
-    (void)n_states;
-    // Levels with fewer than about four times as many k-mers as patterns are nearly
-    // complete: a jump over them replaces that many dependent steps at a table
-    // size of 4^k words. Seven levels (64 KB) is what a shared-memory copy allows.
-    double k = std::floor(std::log((double)std::max<int32_t>(n_patterns, 1)) / std::log(4.0) + 0.5);
-    return (int32_t)std::min(7.0, std::max(2.0, k));
+    // The deepest order whose table (2 bytes per k-mer) and depth-k states (4 bytes
+    // each) fit in about 200 KB of shared memory with 16-bit entries: every level it
+    // covers is one dependent step fewer for every text offset.
+    int32_t best = 1;
+    for (int32_t k = 1; k <= 8 && k <= max_len; k++) {
+        const int64_t nk = level[(size_t)k + 1] - level[(size_t)k];
+        if (nk > kJump16MaxLevel) break;
+        const int64_t bytes = 2 * ((int64_t)1 << (2 * k)) + 4 * (nk + 2);
+        if (bytes > 200 * 1024) break;
+        best = k;
+    }
+    return best;
 }
 
 int build_host_tables(const char *const *patterns, const int32_t *lengths, int32_t n,
@@ -173,44 +179,44 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
         }
 
         // ---- step 3c: k-mer jump table ------------------------------------------
-        int32_t k = jump_k_opt == 0 ? auto_jump_k(n, n_states) : (jump_k_opt < 0 ? 0 : jump_k_opt);
-        if (k > 0 && !T.nodes.empty() && n < (1 << 27)) {
+        int32_t k = jump_k_opt == 0 ? auto_jump_k(T.level, max_len) : (jump_k_opt < 0 ? 0 : jump_k_opt);
+        if (k > max_len) k = max_len;
+        if (k > 0 && !T.nodes.empty()) {
             T.jump_k = k;
-            size_t E = (size_t)1 << (2 * k);
-            T.jump.assign(E, 0);
-            T.jump_best.assign(E, 0);
+            const int64_t lk = T.level[(size_t)k];
+            const int64_t nk = T.level[(size_t)k + 1] - lk;
+            T.jump_wide = nk > kJump16MaxLevel;
+            const size_t E = (size_t)1 << (2 * k);
+            std::vector<uint32_t> J(E, kJumpDead);
             // Depth-first over the trie down to depth k. A prefix of d symbols whose walk
-            // stops at symbol d fixes the entry of every k-mer that starts with it:
-            // those are the indices congruent to the prefix code modulo 4^(d+1).
-            struct Frame { int32_t s; int32_t d; uint32_t code; int32_t best; };
+            // stops at symbol d fixes the entry of every k-mer that starts with it: the
+            // indices congruent to the prefix code modulo 4^(d+1).
+            struct Frame { int32_t s; int32_t d; uint32_t code; bool term; };
             std::vector<Frame> stack;
-            stack.push_back({0, 0, 0u, 0});
+            stack.push_back({0, 0, 0u, false});
             while (!stack.empty()) {
                 Frame f = stack.back();
                 stack.pop_back();
                 if (f.d == k) {
-                    uint32_t w = T.nodes[(size_t)f.s] & ~kNodeTermBit;
-                    if (f.best) w |= kNodeTermBit;
-                    T.jump[f.code] = w;
-                    T.jump_best[f.code] = f.best;
+                    J[f.code] = f.term ? kJumpSpecial : (uint32_t)(kJumpFirst + (f.s - lk));
                     continue;
                 }
                 for (int c = 0; c < 4; c++) {
-                    uint32_t code = f.code | ((uint32_t)c << (2 * f.d));
-                    uint32_t e = (uint32_t)T.rows[(size_t)(4 * (int64_t)f.s + c)];
+                    const uint32_t code = f.code | ((uint32_t)c << (2 * f.d));
+                    const uint32_t e = (uint32_t)T.rows[(size_t)(4 * (int64_t)f.s + c)];
                     if (e) {
-                        int32_t ch = (int32_t)(e & 0x7FFFFFFFu);
-                        int32_t best = (e & 0x80000000u) ? ch : f.best;
-                        stack.push_back({ch, f.d + 1, code, best});
+                        stack.push_back({(int32_t)(e & 0x7FFFFFFFu), f.d + 1, code, f.term || (e & 0x80000000u)});
                     } else {
-                        // walk over the prefix ends here: answer fixed for all extensions
-                        uint32_t ans = f.best ? (uint32_t)T.out_id[(size_t)f.best] : 0u;
-                        uint32_t w = ans << kNodeFirstShift;
-                        size_t stride = (size_t)1 << (2 * (f.d + 1));
-                        for (size_t idx = code; idx < E; idx += stride) T.jump[idx] = w;
+                        // the walk over the prefix ends here: an answer from the prefix
+                        // needs the full walk, otherwise the answer is 0
+                        const uint32_t v = f.term ? kJumpSpecial : kJumpDead;
+                        const size_t stride = (size_t)1 << (2 * (f.d + 1));
+                        for (size_t idx = code; idx < E; idx += stride) J[idx] = v;
                     }
                 }
             }
+            if (T.jump_wide) T.jump32.swap(J);
+            else T.jump16.assign(J.begin(), J.end());
         }
         return PFAC_OK;
     } catch (const std::bad_alloc &) {

@@ -56,13 +56,15 @@ def genome_small():
 @pytest.mark.parametrize("cfg", [
     dict(kernel=1),
     dict(kernel=2),
-    dict(kernel=2, tile_bases=64, threads=32),
-    dict(kernel=2, tile_bases=1024, threads=256),
-    dict(kernel=2, tile_bases=8192, threads=1024),
-    dict(kernel=2, tile_bases=32768, threads=512),
+    dict(kernel=2, threads=64),
+    dict(kernel=2, threads=96, stages=2),
+    dict(kernel=2, threads=512, stages=8),
+    dict(kernel=2, threads=1024, stages=3),
     dict(kernel=2, smem_table_bytes=-1),
     dict(kernel=2, smem_table_bytes=4096),
     dict(kernel=2, ctas_per_sm=2, threads=512),
+    dict(kernel=2, step_cap=1),
+    dict(kernel=2, step_cap=24),
 ], ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
 def test_genome_configs(genome_small, cfg, packed):
     w, want = genome_small
@@ -70,6 +72,18 @@ def test_genome_configs(genome_small, cfg, packed):
     got = (gpu_match_packed if packed else gpu_match)(t, w.text, **cfg)
     assert np.array_equal(got, want), first_diff(got, want)
     assert (want != 0).sum() > 1000
+
+
+def test_deferred_list_overflow(genome_small, monkeypatch):
+    """A deferred-walk list of 7 items: the walks that find it full finish inline."""
+    import torch
+    w, want = genome_small
+    monkeypatch.setenv("PFAC_DEFER_CAP", "7")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        t = b.Table((w.blob, w.offsets))
+        got = gpu_match_packed(t, w.text, kernel=2, step_cap=1)
+    assert np.array_equal(got, want), first_diff(got, want)
 
 
 @pytest.mark.parametrize("jump_k", [-1, 1, 2, 3, 5, 7, 8, 10])
@@ -107,10 +121,10 @@ def test_adversarial(name, text, pats, kernel):
     t = b.Table(pats)
     a = np.frombuffer(text, dtype=np.uint8)
     want = ref(a, pats)
-    got = gpu_match(t, a, kernel=kernel, tile_bases=64, threads=32)
+    got = gpu_match(t, a, kernel=kernel, threads=64)
     assert np.array_equal(got, want), (name, first_diff(got, want))
     if all(c in b"ACGT" for c in text):
-        got = gpu_match_packed(t, a, kernel=kernel, tile_bases=64, threads=32)
+        got = gpu_match_packed(t, a, kernel=kernel, threads=64)
         assert np.array_equal(got, want), (name, first_diff(got, want))
 
 
@@ -119,27 +133,30 @@ def test_empty_text():
     assert gpu_match(t, np.zeros(0, dtype=np.uint8)).size == 0
 
 
-@pytest.mark.parametrize("tile", [64, 128, 4096])
-def test_matches_across_tile_edges(tile):
-    """Long patterns planted so they start just before, at and after tile edges and
-    end exactly at a tile edge, in the halo, and at the text end."""
+@pytest.mark.parametrize("threads", [64, 128, 1024])
+def test_matches_across_tile_edges(threads):
+    """Long patterns planted so they start just before, at and after tile edges (a tile
+    is 512 bases per consumer warp) and end exactly at a tile edge, at a 16-base lane
+    batch edge, at a 48-base window edge, and at the text end."""
+    tile = 512 * (threads // 32 - 1)
     rng = datagen.rng_for(99)
     n = tile * 6 + 37
     text = datagen.iid_text(n, rng)
     pats = []
     for edge in range(tile, n, tile):
-        for start in (edge - 40, edge - 1, edge, edge + 1):
+        for start in (edge - 40, edge - 17, edge - 1, edge, edge + 1, edge + 15, edge + 33):
             L = 40 if start + 40 <= n else n - start
             if 0 <= start and L > 0:
                 pats.append(text[start:start + L].tobytes())
         pats.append(text[edge - 25:edge].tobytes())          # ends exactly at the edge
+        pats.append(text[edge + 2:edge + 48].tobytes())      # ends at the 48-base window edge
     pats.append(text[n - 30:].tobytes())                     # ends at the text end
     want = ref(text, pats)
     t = b.Table(pats)
     for kernel in (1, 2):
-        got = gpu_match(t, text, kernel=kernel, tile_bases=tile, threads=64)
+        got = gpu_match(t, text, kernel=kernel, threads=threads)
         assert np.array_equal(got, want), (kernel, first_diff(got, want))
-        got = gpu_match_packed(t, text, kernel=kernel, tile_bases=tile, threads=64)
+        got = gpu_match_packed(t, text, kernel=kernel, threads=threads)
         assert np.array_equal(got, want), (kernel, first_diff(got, want))
     assert (want != 0).sum() >= len(pats) // 2
 
@@ -160,7 +177,7 @@ def test_random_small_sets_both_kernels():
         for jk in (0, 3, 6):
             t = b.Table(pats, jump_k=jk)
             for kernel in (1, 2):
-                got = gpu_match(t, a, kernel=kernel, tile_bases=64, threads=32)
+                got = gpu_match(t, a, kernel=kernel, threads=64)
                 assert np.array_equal(got, want), (text, pats, jk, kernel, first_diff(got, want))
 
 

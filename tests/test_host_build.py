@@ -81,4 +81,4 @@ def test_random_sets(seed):
 def test_small_workload_set():
     w = datagen.small_scan(n_bases=100_000)
     info = check_same_trie((w.blob, w.offsets))
-    assert info["has_nodes"] == 1 and info["jump_k"] == 5
+    assert info["has_nodes"] == 1 and info["jump_k"] == 8
