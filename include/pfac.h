@@ -79,6 +79,11 @@ typedef struct {
                            -1 = none, 1..12 = that order. The jump table maps the first
                            k bases of a walk to the state they reach (an exact
                            shortcut through the same trie). */
+    int32_t filter_b;   /* order of the prefix filter: 0 = automatic (10), -1 = none,
+                           1..12 = that order. One bit per b-mer, clear when a walk over
+                           those b bases ends with no pattern on the way, so the answer
+                           at that offset is 0 whatever follows (an exact property of
+                           the same trie). */
 } pfac_build_opts;
 
 pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, int32_t n,
@@ -105,11 +110,13 @@ typedef struct {
     int32_t max_len;        /* longest pattern = deepest level of the trie */
     int32_t min_len;
     int32_t jump_k;         /* order of the jump table, 0 if none */
+    int32_t filter_b;       /* order of the prefix filter, 0 if none */
     int64_t n_duplicates;   /* patterns whose string was given before */
     int64_t table_bytes;    /* device bytes (all layouts) */
     int64_t rows_bytes;     /* 16-byte rows: 4 x int32 per state */
     int64_t nodes_bytes;    /* 4-byte compact nodes, 0 if unavailable */
     int32_t has_nodes;      /* compact node layout available (fewer than 2^27 states) */
+    int32_t jump_wide;      /* jump entries are 32-bit (else 16-bit) */
     int32_t device;         /* device holding the copy, -1 if host only */
 } pfac_table_info;
 
@@ -123,6 +130,21 @@ int pfac_info_ex(pfac_handle h, pfac_table_info *info);
  * Any output may be NULL. S = n_states from pfac_info. */
 int pfac_export(pfac_handle h, int32_t *rows, int32_t *out_id, int64_t *level);
 
+/* Copy the shortcut tables of a host-only handle (pfac_build_opts.host_only = 1) for
+ * inspection; a handle with a device copy has dropped its host copy and gives
+ * PFAC_ERR_UNSUPPORTED.
+ *   jump[4^jump_k]  : entries of 2 bytes (4 if jump_wide) for the k-mer w whose base j
+ *                     sits in bits 2j..2j+1: 0 = the walk over w ends before depth k
+ *                     with no pattern on the way; 1 = a pattern ends within w;
+ *                     2 + i = the walk reaches the i-th state of depth k
+ *                     (breadth-first state level[k] + i)
+ *   filter[max(1, 4^filter_b / 32)] : bit w (bit w mod 32 of word w / 32) is clear when
+ *                     the walk over the b-mer w ends before depth b with no pattern on
+ *                     the way
+ * Either output may be NULL; sizes are checked against the tables. */
+int pfac_export_shortcuts(pfac_handle h, void *jump, int64_t jump_bytes, uint32_t *filter,
+                          int64_t filter_words);
+
 /* ---------------------------------------------------------------------------
  * Launch configuration (what the autotuner chooses). All fields 0 = automatic.
  * ------------------------------------------------------------------------- */
@@ -130,7 +152,8 @@ typedef struct {
     int32_t kernel;          /* 0 auto, 1 = per-offset walk over 16-byte rows in global
                                 memory (one thread per text offset, the paper's layout),
                                 2 = pipelined: text staged by TMA into a shared-memory
-                                ring, jump table and compact nodes in shared memory */
+                                ring; prefix filter, jump table and compact nodes in
+                                shared memory (needs both tables) */
     int32_t threads;         /* kernel 2: threads per CTA, 64..1024, multiple of 32: one
                                 producer warp plus consumer warps; a tile is 512 bases
                                 per consumer warp */

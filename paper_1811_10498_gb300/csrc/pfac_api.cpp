@@ -96,7 +96,7 @@ pfac_config default_config(const pfac_table *h, int64_t n_bases, bool packed, co
     (void)n_bases;
     (void)dp;
     pfac_config c{};
-    c.kernel = (h->dt.nodes && h->dt.jump) ? 2 : 1;
+    c.kernel = (h->dt.nodes && h->dt.jump && h->dt.filter) ? 2 : 1;
     c.threads = 1024;
     c.ctas_per_sm = 1;
     c.stages = packed ? 4 : 2;
@@ -191,7 +191,8 @@ int run_scan(pfac_handle h, const void *text, bool packed, int64_t n, int32_t *o
 {
     pfac_config c = effective_config(h, n, packed, dp);
     const bool compact = c_off != nullptr;
-    bool tiled = c.kernel == 2 && h->dt.nodes && aligned16(text) && (compact || aligned16(out));
+    bool tiled = c.kernel == 2 && h->dt.nodes && h->dt.jump && h->dt.filter && aligned16(text) &&
+                 (compact || aligned16(out));
     int rc = PFAC_OK;
     if (tiled) {
         pfac::TiledConfig tc = tiled_config(c);
@@ -245,7 +246,7 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
     if (opts) o = *opts;
     pfac_table *h = new (std::nothrow) pfac_table();
     if (!h) { fail(PFAC_ERR_OOM); return nullptr; }
-    int rc = pfac::build_host_tables(patterns, lengths, n, o.jump_k, &h->host);
+    int rc = pfac::build_host_tables(patterns, lengths, n, o.jump_k, o.filter_b, &h->host);
     if (rc != PFAC_OK) { delete h; fail(rc); return nullptr; }
     const pfac::HostTables &T = h->host;
     h->rows_bytes = T.n_states * 16;
@@ -260,7 +261,8 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         const size_t s_out = round256((size_t)T.n_states * 4);
         const size_t jump_bytes = T.jump16.size() * 2 + T.jump32.size() * 4;
         const size_t s_jump = round256(jump_bytes);
-        h->dbytes = s_status + s_rows + s_nodes + s_out + s_jump;
+        const size_t s_filter = round256(T.filter.size() * 4);
+        h->dbytes = s_status + s_rows + s_nodes + s_out + s_jump + s_filter;
         e = cudaMalloc(&h->dmem, h->dbytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -275,12 +277,14 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         h->dt.nodes = T.nodes.empty() ? nullptr : (const uint32_t *)(base + off); off += s_nodes;
         h->dt.out_id = (const int32_t *)(base + off); off += s_out;
         h->dt.jump = jump_bytes ? (const void *)(base + off) : nullptr; off += s_jump;
+        h->dt.filter = T.filter.empty() ? nullptr : (const uint32_t *)(base + off); off += s_filter;
         const void *jump_src = T.jump_wide ? (const void *)T.jump32.data() : (const void *)T.jump16.data();
         struct Up { const void *dst; const void *src; size_t bytes; } ups[] = {
             {h->dt.rows, T.rows.data(), T.rows.size() * 4},
             {h->dt.nodes, T.nodes.data(), T.nodes.size() * 4},
             {h->dt.out_id, T.out_id.data(), T.out_id.size() * 4},
             {h->dt.jump, jump_src, jump_bytes},
+            {h->dt.filter, T.filter.data(), T.filter.size() * 4},
         };
         e = cudaMemset(h->dt.status, 0, s_status);
         for (auto &u : ups)
@@ -296,12 +300,14 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         h->dt.max_len = T.max_len;
         h->dt.jump_k = T.jump_k;
         h->dt.jump_wide = T.jump_wide;
+        h->dt.filter_b = T.filter_b;
         h->dt.level_k = T.jump_k > 0 ? T.level[(size_t)T.jump_k] : 0;
         h->dt.level_k1 = T.jump_k > 0 ? T.level[(size_t)T.jump_k + 1] : 0;
         // The device copy is complete; the host keeps rows, ids and levels for export.
         std::vector<uint32_t>().swap(h->host.nodes);
         std::vector<uint16_t>().swap(h->host.jump16);
         std::vector<uint32_t>().swap(h->host.jump32);
+        std::vector<uint32_t>().swap(h->host.filter);
     }
     return h;
 }
@@ -345,11 +351,13 @@ int pfac_info_ex(pfac_handle h, pfac_table_info *info)
     i.max_len = h->host.max_len;
     i.min_len = h->host.min_len;
     i.jump_k = h->host.jump_k;
+    i.filter_b = h->host.filter_b;
     i.n_duplicates = h->host.n_duplicates;
     i.table_bytes = (int64_t)h->dbytes;
     i.rows_bytes = h->rows_bytes;
     i.nodes_bytes = h->nodes_bytes;
     i.has_nodes = h->nodes_bytes > 0;
+    i.jump_wide = h->host.jump_wide;
     i.device = h->device;
     *info = i;
     return PFAC_OK;
@@ -365,6 +373,24 @@ int pfac_export(pfac_handle h, int32_t *rows, int32_t *out_id, int64_t *level)
     return PFAC_OK;
 }
 
+int pfac_export_shortcuts(pfac_handle h, void *jump, int64_t jump_bytes, uint32_t *filter, int64_t filter_words)
+{
+    if (!h) return fail(PFAC_ERR_INVALID_ARG);
+    const pfac::HostTables &T = h->host;
+    if (h->device >= 0) return fail(PFAC_ERR_UNSUPPORTED);
+    if (jump) {
+        const int64_t need = (int64_t)(T.jump_wide ? T.jump32.size() * 4 : T.jump16.size() * 2);
+        if (jump_bytes < need) return fail(PFAC_ERR_INVALID_ARG);
+        if (T.jump_wide) memcpy(jump, T.jump32.data(), (size_t)need);
+        else memcpy(jump, T.jump16.data(), (size_t)need);
+    }
+    if (filter) {
+        if (filter_words < (int64_t)T.filter.size()) return fail(PFAC_ERR_INVALID_ARG);
+        memcpy(filter, T.filter.data(), T.filter.size() * 4);
+    }
+    return PFAC_OK;
+}
+
 int pfac_set_config(pfac_handle h, const pfac_config *cfg)
 {
     if (!h) return fail(PFAC_ERR_INVALID_ARG);
@@ -373,7 +399,8 @@ int pfac_set_config(pfac_handle h, const pfac_config *cfg)
             (cfg->threads > 0 && cfg->threads < 64) || cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32 ||
             cfg->stages < 0 || cfg->stages == 1 || cfg->stages > 8 || cfg->step_cap < 0 || cfg->step_cap > 24)
             return fail(PFAC_ERR_INVALID_ARG);
-        if (cfg->kernel == 2 && !(h->nodes_bytes > 0 && h->host.jump_k > 0)) return fail(PFAC_ERR_UNSUPPORTED);
+        if (cfg->kernel == 2 && !(h->nodes_bytes > 0 && h->host.jump_k > 0 && h->host.filter_b > 0))
+            return fail(PFAC_ERR_UNSUPPORTED);
     }
     std::lock_guard<std::mutex> lk(h->mu);
     h->cfg_set = cfg != nullptr;

@@ -32,7 +32,13 @@ constexpr int64_t kMaxNodeStates = int64_t(1) << 27;
 //   2 + i         the i-th state of depth k (breadth-first id level[k] + i); no pattern
 //                 ends within the first k bases.
 // Entries are 16-bit when depth k has at most 65533 states, else 32-bit.
+//
+// Prefix filter of order b: one bit per b-mer w. The bit is 0 when the walk over w ends
+// before depth b and no pattern ends on the way, so that the answer at any offset
+// where w starts is 0 whatever follows; it is 1 otherwise (the walk is still going at
+// depth b, or a pattern ends within w). Bit w is bit (w mod 32) of word w / 32.
 constexpr int kMaxJumpK = 12;
+constexpr int kMaxFilterB = 12;
 constexpr uint32_t kJumpDead = 0;
 constexpr uint32_t kJumpSpecial = 1;
 constexpr uint32_t kJumpFirst = 2;
@@ -52,11 +58,13 @@ struct HostTables {
     int32_t jump_wide = 0;           // 1: 32-bit entries (jump32), 0: 16-bit (jump16)
     std::vector<uint16_t> jump16;    // 4^k entries
     std::vector<uint32_t> jump32;    // 4^k entries
+    int32_t filter_b = 0;            // 0 = no prefix filter
+    std::vector<uint32_t> filter;    // 4^b bits
 };
 
 // Status codes match pfac.h.
 int build_host_tables(const char *const *patterns, const int32_t *lengths, int32_t n,
-                      int32_t jump_k_opt, HostTables *out);
+                      int32_t jump_k_opt, int32_t filter_b_opt, HostTables *out);
 
 // Order of the jump table chosen when the caller leaves it to the library, from the
 // number of states per depth level.
@@ -80,6 +88,8 @@ struct DeviceTable {
     int32_t max_len;
     int32_t jump_k;            // 0 = no jump table
     int32_t jump_wide;         // 32-bit jump entries
+    const uint32_t *filter;    // 4^filter_b bits, or nullptr
+    int32_t filter_b;          // 0 = no prefix filter
     int64_t level_k;           // first state of depth jump_k (window slot kJumpFirst)
     int64_t level_k1;          // first state of depth jump_k + 1
     int32_t *status;           // device status word (PFAC_OK or the first error)

@@ -330,7 +330,7 @@ struct ScanParams {
     int32_t qmax;                // a walk still going after qmax bases is deferred
     int32_t jump_smem;           // jump table copied into shared memory
     uint32_t win_len;            // window slots in shared memory (two sentinels + states)
-    uint32_t off_jump, off_win, off_stage, stage_bytes;
+    uint32_t off_filter, off_jump, off_win, off_stage, stage_bytes;
     int64_t timeout_ns;
 };
 
@@ -448,10 +448,11 @@ __device__ __forceinline__ uint32_t node_of_slot(uint32_t v, const uint32_t *sw,
     return v < win_slots ? sw[v] : __ldg(nodes + (level_k + v - kJumpFirst));
 }
 
-template <bool PACKED, bool COMPACT, typename JW, bool FULL>
+template <bool PACKED, bool COMPACT, typename JW, bool FSMEM>
 __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
+    const uint32_t *sf = reinterpret_cast<const uint32_t *>(smem + P.off_filter);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = reinterpret_cast<uint64_t *>(smem + 64);
     volatile uint32_t *abort_flag = reinterpret_cast<volatile uint32_t *>(smem + 128);
@@ -463,6 +464,8 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
     const DeviceTable &T = P.t;
     const int K = T.jump_k;
     const uint32_t kmask = (uint32_t)((1ull << (2 * K)) - 1ull);
+    const int B = T.filter_b;
+    const uint32_t bmask = (uint32_t)((1ull << (2 * B)) - 1ull);
     const int S = P.stages;
     const int64_t n = P.n;
     const uint32_t level_k = (uint32_t)T.level_k;
@@ -478,15 +481,16 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
         fence_mbar_init();
     }
     {
-        // jump table and node window, resident for the whole persistent kernel
-        if (P.jump_smem) {
-            const int64_t bytes = (int64_t)sizeof(JW) << (2 * K);
-            uint8_t *dst = smem + P.off_jump;
-            const uint8_t *src = (const uint8_t *)T.jump;
+        // filter, jump table and node window, resident for the whole persistent kernel
+        auto copy_in = [&](uint32_t off, const void *src_v, int64_t bytes) {
+            uint8_t *dst = smem + off;
+            const uint8_t *src = (const uint8_t *)src_v;
             for (int64_t i = 16 * (int64_t)tid; i + 16 <= bytes; i += 16 * (int64_t)blockDim.x)
                 *reinterpret_cast<uint4 *>(dst + i) = __ldg(reinterpret_cast<const uint4 *>(src + i));
             for (int64_t i = (bytes & ~(int64_t)15) + tid; i < bytes; i += blockDim.x) dst[i] = src[i];
-        }
+        };
+        if (FSMEM) copy_in(P.off_filter, T.filter, (((int64_t)1 << (2 * B)) + 7) / 8);
+        if (P.jump_smem) copy_in(P.off_jump, T.jump, (int64_t)sizeof(JW) << (2 * K));
         uint32_t *ww = reinterpret_cast<uint32_t *>(smem + P.off_win);
         if (tid == 0) {
             ww[kJumpDead] = 0u;              // no edges: the walk ends
@@ -562,19 +566,16 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
         if (lane == 0) mbar_arrive(smem_addr(&empty[st]));   // this warp is done with the stage
         bad &= 0xFFFFFFFFFFFFull;
         const uint32_t valid = rem >= 16 ? 0xFFFFu : (rem > 0 ? ((1u << rem) - 1u) : 0u);
-        const uint32_t fast = clear_runs(bad, K + 1) & valid;   // jump + one step readable
+        const uint32_t fast = clear_runs(bad, B) & valid;   // the b-mer is readable
 
-        // Every offset: jump over the first K bases, then one step through the node
-        // the jump lands on. The walk goes on only where that step exists (or the
-        // entry is the special one, whose sentinel node has every edge).
+        // Every offset: one filter bit for the b bases starting there. A clear bit
+        // means the walk ends before depth b with no pattern on the way: answer 0.
         uint32_t pend = 0;
 #pragma unroll
         for (int j = 0; j < 16; j++) {
-            const uint32_t win = __funnelshift_r(x0, x1, 2 * j);     // bases j .. j+15
-            const uint32_t v = jump_entry<JW>(P, sj, win & kmask);
-            const uint32_t nd = node_of_slot<FULL>(v, sw, win_slots, level_k, T.nodes);
-            const uint32_t c = (win >> (2 * K)) & 3u;
-            pend |= ((nd >> c) & 1u) << j;
+            const uint32_t kmer = __funnelshift_r(x0, x1, 2 * j) & bmask;   // bases j .. j+b-1
+            const uint32_t word = FSMEM ? sf[kmer >> 5] : __ldg(T.filter + (kmer >> 5));
+            pend |= ((word >> (kmer & 31u)) & 1u) << j;
         }
         pend &= fast;
         pend |= valid & ~fast;     // these walk from the root
@@ -617,7 +618,6 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             }
             const uint32_t om = __shfl_sync(0xFFFFFFFFu, pend, owner);
             const uint32_t oe = __shfl_sync(0xFFFFFFFFu, excl, owner);
-            const uint32_t ofast = __shfl_sync(0xFFFFFFFFu, fast, owner);
             const uint32_t ox0 = __shfl_sync(0xFFFFFFFFu, x0, owner);
             const uint32_t ox1 = __shfl_sync(0xFFFFFFFFu, x1, owner);
             const uint32_t ox2 = __shfl_sync(0xFFFFFFFFu, x2, owner);
@@ -636,10 +636,11 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             const int lim = min(wlim, T.max_len);
             uint32_t s = 0, nd, best = 0;
             int q = 0;
-            const uint32_t v = ((ofast >> j) & 1u) ? jump_entry<JW>(P, sj, (uint32_t)rest & kmask) : kJumpSpecial;
+            // jump over the first K bases when they are readable, else walk from the root
+            const uint32_t v = wlim >= K ? jump_entry<JW>(P, sj, (uint32_t)rest & kmask) : kJumpSpecial;
             if (v != kJumpSpecial) {
                 s = level_k + v - kJumpFirst;
-                nd = node_of_slot<FULL>(v, sw, win_slots, level_k, T.nodes);
+                nd = node_of_slot<false>(v, sw, win_slots, level_k, T.nodes);
                 rest >>= 2 * K;
                 q = K;
             } else {
@@ -692,17 +693,20 @@ __global__ void __launch_bounds__(256) tail_kernel(const ScanParams P)
 }
 
 struct ScanLayout {
-    uint32_t off_jump, off_win, off_stage, stage_bytes, total;
+    uint32_t off_filter, off_jump, off_win, off_stage, stage_bytes, total;
     int32_t stage_units;
 };
 
 static inline uint32_t align128(uint64_t x) { return (uint32_t)((x + 127) & ~(uint64_t)127); }
 
-static ScanLayout scan_layout(int consumers, int stages, int64_t jump_smem_bytes, bool packed, uint32_t win_slots)
+static ScanLayout scan_layout(int consumers, int stages, int64_t filter_smem_bytes, int64_t jump_smem_bytes,
+                              bool packed, uint32_t win_slots)
 {
     ScanLayout L{};
     const int64_t tile = 512LL * consumers;
     uint64_t off = kBarBytes;
+    L.off_filter = (uint32_t)off;
+    off += align128((uint64_t)filter_smem_bytes);
     L.off_jump = (uint32_t)off;
     off += align128((uint64_t)jump_smem_bytes);
     L.off_win = (uint32_t)off;
@@ -719,38 +723,57 @@ static ScanLayout scan_layout(int consumers, int stages, int64_t jump_smem_bytes
 static int consumers_of(const TiledConfig &cfg) { return cfg.threads / 32 - 1; }
 static int stages_of(const TiledConfig &cfg, bool packed) { return cfg.stages > 0 ? cfg.stages : (packed ? 4 : 2); }
 
-// Shared memory per CTA: the jump table when it fits beside the stages, then as many
-// states of depth >= jump_k as the remaining budget holds.
-int64_t tiled_smem_bytes(const DeviceTable &t, const TiledConfig &cfg, bool packed, int32_t *win_len_out,
-                         int32_t *jump_smem_out, const DeviceProps &dp)
+// Shared memory per CTA, by priority: the text stages, the prefix filter (read for
+// every offset), the jump table (read for every walk that passes the filter), then
+// as many states of depth >= jump_k as the remaining budget holds.
+struct SmemPlan {
+    int64_t filter_bytes, jump_bytes;   // bytes copied into shared memory (0 = global)
+    int32_t win_len;                    // window slots (two sentinels + states)
+    int64_t total;
+};
+
+static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool packed, const DeviceProps &dp)
 {
+    SmemPlan pl{};
     const int C = consumers_of(cfg);
     const int S = stages_of(cfg, packed);
     const int64_t per_cta = (int64_t)dp.smem_per_sm / std::max(1, cfg.ctas_per_sm) - 1024;
     const int64_t limit = std::min<int64_t>(dp.smem_optin, per_cta);
+    const int64_t fbytes = (((int64_t)1 << (2 * t.filter_b)) + 7) / 8;
     const int64_t jbytes = (t.jump_wide ? 4LL : 2LL) << (2 * t.jump_k);
-    const int64_t base = scan_layout(C, S, 0, packed, kJumpFirst).total;
-    const bool jump_smem = base + align128((uint64_t)jbytes) <= limit;
-    const int64_t fixed = scan_layout(C, S, jump_smem ? jbytes : 0, packed, kJumpFirst).total;
-    if (fixed > limit) return -1;
+    auto total = [&](int64_t f, int64_t j, int64_t w) { return (int64_t)scan_layout(C, S, f, j, packed, (uint32_t)w).total; };
+    if (total(0, 0, kJumpFirst) > limit) {
+        pl.total = -1;
+        return pl;
+    }
+    pl.filter_bytes = total(fbytes, 0, kJumpFirst) <= limit ? fbytes : 0;
+    pl.jump_bytes = total(pl.filter_bytes, jbytes, kJumpFirst) <= limit ? jbytes : 0;
     int64_t states = 0;
     if (cfg.smem_table_bytes >= 0) {
-        const int64_t room = limit - fixed;
+        const int64_t room = limit - total(pl.filter_bytes, pl.jump_bytes, kJumpFirst);
         const int64_t budget = cfg.smem_table_bytes > 0 ? std::min<int64_t>(cfg.smem_table_bytes, room) : room;
         states = std::max<int64_t>(0, std::min<int64_t>(budget / 4, t.n_states - t.level_k));
-        while (states > 0 && scan_layout(C, S, jump_smem ? jbytes : 0, packed, (uint32_t)(kJumpFirst + states)).total > limit)
-            states -= 32;
+        while (states > 0 && total(pl.filter_bytes, pl.jump_bytes, kJumpFirst + states) > limit) states -= 32;
         states = std::max<int64_t>(states, 0);
     }
-    if (win_len_out) *win_len_out = (int32_t)(kJumpFirst + states);
-    if (jump_smem_out) *jump_smem_out = jump_smem;
-    return scan_layout(C, S, jump_smem ? jbytes : 0, packed, (uint32_t)(kJumpFirst + states)).total;
+    pl.win_len = (int32_t)(kJumpFirst + states);
+    pl.total = total(pl.filter_bytes, pl.jump_bytes, pl.win_len);
+    return pl;
 }
 
-template <bool PACKED, bool COMPACT, typename JW, bool FULL>
+int64_t tiled_smem_bytes(const DeviceTable &t, const TiledConfig &cfg, bool packed, int32_t *win_len_out,
+                         int32_t *jump_smem_out, const DeviceProps &dp)
+{
+    const SmemPlan pl = plan_smem(t, cfg, packed, dp);
+    if (win_len_out) *win_len_out = pl.win_len;
+    if (jump_smem_out) *jump_smem_out = pl.jump_bytes > 0;
+    return pl.total;
+}
+
+template <bool PACKED, bool COMPACT, typename JW, bool FSMEM>
 static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t smem, int tail_grid, cudaStream_t st)
 {
-    auto kern = scan_kernel<PACKED, COMPACT, JW, FULL>;
+    auto kern = scan_kernel<PACKED, COMPACT, JW, FSMEM>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return PFAC_ERR_CUDA;
     kern<<<grid, threads, smem, st>>>(P);
@@ -759,15 +782,15 @@ static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t sm
     return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
 }
 
-// 16-bit entries with every depth-k state in shared memory is the fast case; other
-// tables take the general kernel (32-bit entries, window lookups that may miss).
 template <bool PACKED, bool COMPACT>
-static int launch_scan_w(const ScanParams &P, bool wide, bool full, int grid, int threads, uint32_t smem,
+static int launch_scan_w(const ScanParams &P, bool wide, bool fsmem, int grid, int threads, uint32_t smem,
                          int tail_grid, cudaStream_t st)
 {
-    if (!wide && full) return launch_scan_t<PACKED, COMPACT, uint16_t, true>(P, grid, threads, smem, tail_grid, st);
-    return wide ? launch_scan_t<PACKED, COMPACT, uint32_t, false>(P, grid, threads, smem, tail_grid, st)
-                : launch_scan_t<PACKED, COMPACT, uint16_t, false>(P, grid, threads, smem, tail_grid, st);
+    if (wide)
+        return fsmem ? launch_scan_t<PACKED, COMPACT, uint32_t, true>(P, grid, threads, smem, tail_grid, st)
+                     : launch_scan_t<PACKED, COMPACT, uint32_t, false>(P, grid, threads, smem, tail_grid, st);
+    return fsmem ? launch_scan_t<PACKED, COMPACT, uint16_t, true>(P, grid, threads, smem, tail_grid, st)
+                 : launch_scan_t<PACKED, COMPACT, uint16_t, false>(P, grid, threads, smem, tail_grid, st);
 }
 
 int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n, int32_t *out, int64_t *c_off,
@@ -779,14 +802,14 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     if (n == 0) return PFAC_OK;
     const int C = consumers_of(cfg);
     const int S = stages_of(cfg, packed);
-    if (!t.nodes || !t.jump || t.jump_k < 1 || t.jump_k > kMaxJumpK || C < 1 || (cfg.threads & 31) ||
-        cfg.threads > 1024 || S < 2 || S > kMaxStages || !scratch.items || !scratch.count)
+    if (!t.nodes || !t.jump || !t.filter || t.jump_k < 1 || t.jump_k > kMaxJumpK || t.filter_b < 1 ||
+        t.filter_b > kMaxFilterB || C < 1 || (cfg.threads & 31) || cfg.threads > 1024 || S < 2 || S > kMaxStages ||
+        !scratch.items || !scratch.count)
         return PFAC_ERR_INVALID_ARG;
-    int32_t win_len = 0, jump_smem = 0;
-    const int64_t smem = tiled_smem_bytes(t, cfg, packed, &win_len, &jump_smem, dp);
-    if (smem < 0 || smem > dp.smem_optin) return PFAC_ERR_UNSUPPORTED;
-    const int64_t jbytes = (t.jump_wide ? 4LL : 2LL) << (2 * t.jump_k);
-    const ScanLayout L = scan_layout(C, S, jump_smem ? jbytes : 0, packed, (uint32_t)win_len);
+    const SmemPlan pl = plan_smem(t, cfg, packed, dp);
+    if (pl.total < 0 || pl.total > dp.smem_optin) return PFAC_ERR_UNSUPPORTED;
+    const int32_t win_len = pl.win_len;
+    const ScanLayout L = scan_layout(C, S, pl.filter_bytes, pl.jump_bytes, packed, (uint32_t)win_len);
     if (cudaMemsetAsync(scratch.count, 0, sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     ScanParams P{};
     P.t = t;
@@ -807,9 +830,10 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     P.stages = S;
     P.stage_units = L.stage_units;
     // deferred once this many bases are consumed (the register window holds 32)
-    P.qmax = std::min(32, t.jump_k + 1 + (cfg.step_cap > 0 ? cfg.step_cap : 8));
-    P.jump_smem = jump_smem;
+    P.qmax = std::min(32, std::max(t.jump_k, t.filter_b) + 1 + (cfg.step_cap > 0 ? cfg.step_cap : 8));
+    P.jump_smem = pl.jump_bytes > 0;
     P.win_len = (uint32_t)win_len;
+    P.off_filter = L.off_filter;
     P.off_jump = L.off_jump;
     P.off_win = L.off_win;
     P.off_stage = L.off_stage;
@@ -819,13 +843,12 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     const int grid = (int)std::max<int64_t>(1, grid64);
     const int tail_grid = dp.num_sms * 4;
     const bool wide = t.jump_wide != 0;
-    // every state of depth jump_k in the window (slots up to kJumpFirst + that count)
-    const bool full = (int64_t)win_len >= kJumpFirst + t.level_k1 - t.level_k;
+    const bool fsmem = pl.filter_bytes > 0;
     if (packed)
-        return compact ? launch_scan_w<true, true>(P, wide, full, grid, cfg.threads, L.total, tail_grid, st)
-                       : launch_scan_w<true, false>(P, wide, full, grid, cfg.threads, L.total, tail_grid, st);
-    return compact ? launch_scan_w<false, true>(P, wide, full, grid, cfg.threads, L.total, tail_grid, st)
-                   : launch_scan_w<false, false>(P, wide, full, grid, cfg.threads, L.total, tail_grid, st);
+        return compact ? launch_scan_w<true, true>(P, wide, fsmem, grid, cfg.threads, L.total, tail_grid, st)
+                       : launch_scan_w<true, false>(P, wide, fsmem, grid, cfg.threads, L.total, tail_grid, st);
+    return compact ? launch_scan_w<false, true>(P, wide, fsmem, grid, cfg.threads, L.total, tail_grid, st)
+                   : launch_scan_w<false, false>(P, wide, fsmem, grid, cfg.threads, L.total, tail_grid, st);
 }
 
 size_t defer_item_bytes() { return sizeof(DeferItem); }

@@ -47,25 +47,25 @@ constexpr int64_t kMaxStates = int64_t(0x7FFFFFFF);
 
 int32_t auto_jump_k(const std::vector<int64_t> &level, int32_t max_len)
 {
-    // The deepest order whose table (2 bytes per k-mer) and depth-k states (4 bytes
-    // each) fit in about 200 KB of shared memory with 16-bit entries: every level it
-    // covers is one dependent step fewer for every text offset.
+    // The jump table serves the walks that pass the prefix filter. The deepest order
+    // whose 16-bit table and depth-k states fit in about 80 KB of shared memory, next
+    // to a 128 KB filter: every level it covers is one dependent step fewer.
     int32_t best = 1;
     for (int32_t k = 1; k <= 8 && k <= max_len; k++) {
         const int64_t nk = level[(size_t)k + 1] - level[(size_t)k];
         if (nk > kJump16MaxLevel) break;
         const int64_t bytes = 2 * ((int64_t)1 << (2 * k)) + 4 * (nk + 2);
-        if (bytes > 200 * 1024) break;
+        if (bytes > 80 * 1024) break;
         best = k;
     }
     return best;
 }
 
 int build_host_tables(const char *const *patterns, const int32_t *lengths, int32_t n,
-                      int32_t jump_k_opt, HostTables *out)
+                      int32_t jump_k_opt, int32_t filter_b_opt, HostTables *out)
 {
     if (n <= 0 || !patterns || !lengths || !out) return PFAC_ERR_INVALID_ARG;
-    if (jump_k_opt > kMaxJumpK) return PFAC_ERR_INVALID_ARG;
+    if (jump_k_opt > kMaxJumpK || filter_b_opt > kMaxFilterB) return PFAC_ERR_INVALID_ARG;
     try {
         // ---- validate ----------------------------------------------------------
         int64_t total = 0;
@@ -217,6 +217,37 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
             }
             if (T.jump_wide) T.jump32.swap(J);
             else T.jump16.assign(J.begin(), J.end());
+        }
+
+        // ---- step 3d: prefix filter ----------------------------------------------
+        // Same depth-first enumeration to depth b: a b-mer's bit is set when its walk
+        // is still going at depth b, or when a pattern ends on the walk before it stops.
+        const int32_t b = filter_b_opt == 0 ? 10 : (filter_b_opt < 0 ? 0 : filter_b_opt);
+        if (b > 0) {
+            T.filter_b = b;
+            const size_t E = (size_t)1 << (2 * b);
+            T.filter.assign(E / 32 + (E < 32 ? 1 : 0), 0u);
+            struct Frame { int32_t s; int32_t d; uint32_t code; bool term; };
+            std::vector<Frame> stack;
+            stack.push_back({0, 0, 0u, false});
+            while (!stack.empty()) {
+                Frame f = stack.back();
+                stack.pop_back();
+                if (f.d == b) {
+                    T.filter[f.code >> 5] |= 1u << (f.code & 31);
+                    continue;
+                }
+                for (int c = 0; c < 4; c++) {
+                    const uint32_t code = f.code | ((uint32_t)c << (2 * f.d));
+                    const uint32_t e = (uint32_t)T.rows[(size_t)(4 * (int64_t)f.s + c)];
+                    if (e) {
+                        stack.push_back({(int32_t)(e & 0x7FFFFFFFu), f.d + 1, code, f.term || (e & 0x80000000u)});
+                    } else if (f.term) {
+                        const size_t stride = (size_t)1 << (2 * (f.d + 1));
+                        for (size_t idx = code; idx < E; idx += stride) T.filter[idx >> 5] |= 1u << (idx & 31);
+                    }
+                }
+            }
         }
         return PFAC_OK;
     } catch (const std::bad_alloc &) {

@@ -86,12 +86,17 @@ def test_deferred_list_overflow(genome_small, monkeypatch):
     assert np.array_equal(got, want), first_diff(got, want)
 
 
-@pytest.mark.parametrize("jump_k", [-1, 1, 2, 3, 5, 7, 8, 10])
-def test_jump_orders(genome_small, jump_k):
+@pytest.mark.parametrize("jump_k,filter_b", [(-1, 0), (0, -1), (1, 12), (3, 1), (5, 5), (7, 10), (8, 9),
+                                             (10, 4), (12, 11), (2, 10)])
+def test_shortcut_orders(genome_small, jump_k, filter_b):
+    """Jump-table and prefix-filter orders, including a filter shorter than the jump,
+    tables too large for shared memory, and tables without one of them (kernel 1)."""
     w, want = genome_small
-    t = b.Table((w.blob, w.offsets), jump_k=jump_k)
-    assert t.info["jump_k"] == max(jump_k, 0)
+    t = b.Table((w.blob, w.offsets), jump_k=jump_k, filter_b=filter_b)
+    assert t.info["jump_k"] == (0 if jump_k < 0 else (jump_k or t.info["jump_k"]))
     got = gpu_match_packed(t, w.text)
+    assert np.array_equal(got, want), first_diff(got, want)
+    got = gpu_match(t, w.text)
     assert np.array_equal(got, want), first_diff(got, want)
 
 
@@ -174,8 +179,8 @@ def test_random_small_sets_both_kernels():
             continue
         a = np.frombuffer(text, dtype=np.uint8)
         want = ref(a, pats)
-        for jk in (0, 3, 6):
-            t = b.Table(pats, jump_k=jk)
+        for jk, fb in ((0, 0), (3, 2), (6, 9)):
+            t = b.Table(pats, jump_k=jk, filter_b=fb)
             for kernel in (1, 2):
                 got = gpu_match(t, a, kernel=kernel, threads=64)
                 assert np.array_equal(got, want), (text, pats, jk, kernel, first_diff(got, want))
