@@ -646,36 +646,40 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             } else {
                 nd = __ldg(T.nodes);     // the root
             }
-            bool deferred = false;
-            while (q < lim) {
+            // walk inside the register window: at most qmax bases
+            const int qstop = min(lim, P.qmax);
+            bool live = true;
+            while (q < qstop) {
                 const uint32_t c = (uint32_t)rest & 3u;
                 rest >>= 2;
-                if (!((nd >> c) & 1u)) break;
+                if (!((nd >> c) & 1u)) {
+                    live = false;
+                    break;
+                }
                 s = (nd >> kNodeFirstShift) + __popc(nd & ((1u << c) - 1u));
                 nd = node_at(s, sw, level_k, win_states, T.nodes);
                 q++;
                 if (nd & kNodeTermBit) best = s;
-                if (q >= P.qmax && q < lim && (nd & kNodeMaskBits)) {
-                    // long walk: finish it in the tail kernel (or here if the list is full)
-                    const unsigned long long di = atomicAdd(P.defer_count, 1ull);
-                    if ((int64_t)di < P.defer_cap) {
-                        DeferItem it;
-                        it.gp = gp;
-                        it.s = s;
-                        it.best = best;
-                        it.q = q;
-                        it.pad = 0;
-                        P.defer[di] = it;
-                    } else {
-                        emit_match<COMPACT>(P, gp, walk_global<PACKED>(T, P.text, n, gp, s, q, best));
-                    }
-                    deferred = true;
-                    break;
-                }
             }
-            // A walk that stops here met a missing edge, an unreadable base or the
-            // deepest level: qmax <= 32 < 48 - j, so the window never runs out first.
-            if (!deferred && best) emit_match<COMPACT>(P, gp, __ldg(T.out_id + best));
+            if (live && q == P.qmax && q < lim && (nd & kNodeMaskBits)) {
+                // long walk: finish it in the tail kernel (or here if the list is full)
+                const unsigned long long di = atomicAdd(P.defer_count, 1ull);
+                if ((int64_t)di < P.defer_cap) {
+                    DeferItem it;
+                    it.gp = gp;
+                    it.s = s;
+                    it.best = best;
+                    it.q = q;
+                    it.pad = 0;
+                    P.defer[di] = it;
+                } else {
+                    emit_match<COMPACT>(P, gp, walk_global<PACKED>(T, P.text, n, gp, s, q, best));
+                }
+            } else if (best) {
+                // the walk met a missing edge, an unreadable base or the deepest level;
+                // qmax <= 32 < 48 - j, so the window never runs out first
+                emit_match<COMPACT>(P, gp, __ldg(T.out_id + best));
+            }
         }
     }
 }

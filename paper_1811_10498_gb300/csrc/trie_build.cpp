@@ -47,18 +47,12 @@ constexpr int64_t kMaxStates = int64_t(0x7FFFFFFF);
 
 int32_t auto_jump_k(const std::vector<int64_t> &level, int32_t max_len)
 {
-    // The jump table serves the walks that pass the prefix filter. The deepest order
-    // whose 16-bit table and depth-k states fit in about 80 KB of shared memory, next
-    // to a 128 KB filter: every level it covers is one dependent step fewer.
-    int32_t best = 1;
-    for (int32_t k = 1; k <= 8 && k <= max_len; k++) {
-        const int64_t nk = level[(size_t)k + 1] - level[(size_t)k];
-        if (nk > kJump16MaxLevel) break;
-        const int64_t bytes = 2 * ((int64_t)1 << (2 * k)) + 4 * (nk + 2);
-        if (bytes > 80 * 1024) break;
-        best = k;
-    }
-    return best;
+    // The jump table serves the walks that pass the prefix filter of order 10: those
+    // are still going at depth 10, so a jump over the same 10 bases takes them there
+    // in one lookup (a 16-bit table of 2 MB that stays in L2 when depth 10 has at most
+    // 65533 states, else 32-bit). Tries shallower than that jump to their deepest level.
+    (void)level;
+    return std::max(1, std::min(10, max_len));
 }
 
 int build_host_tables(const char *const *patterns, const int32_t *lengths, int32_t n,

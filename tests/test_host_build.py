@@ -82,7 +82,7 @@ def test_random_sets(seed):
 def test_small_workload_set():
     w = datagen.small_scan(n_bases=100_000)
     info = check_same_trie((w.blob, w.offsets))
-    assert info["has_nodes"] == 1 and info["jump_k"] == 7 and info["filter_b"] == 10
+    assert info["has_nodes"] == 1 and info["jump_k"] == 10 and info["filter_b"] == 10
 
 
 def shortcut_reference(go, term, order_new, k, b):
