@@ -331,7 +331,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": workload_name(args.n_bases, args.n_patterns), "n_bases": n,
-                       "n_patterns": args.n_patterns, "n_states": info["n_states"], "jump_k": info["jump_k"],
+                       "n_patterns": args.n_patterns, "n_states": info["n_states"], "filter_b": info["filter_b"],
                        "l2": "flushed between timed steps (memset of 4x L2 outside the events)",
                        "input_resident": "packed text in HBM"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,

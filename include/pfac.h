@@ -75,10 +75,6 @@ pfac_handle pfac_build(const char *const *patterns, const int32_t *lengths, int3
 typedef struct {
     int32_t host_only;  /* 1: build the tables on the host only (no device copy; the
                            scan calls reject the handle with PFAC_ERR_HOST_ONLY). */
-    int32_t jump_k;     /* order of the k-mer jump table: 0 = choose automatically,
-                           -1 = none, 1..12 = that order. The jump table maps the first
-                           k bases of a walk to the state they reach (an exact
-                           shortcut through the same trie). */
     int32_t filter_b;   /* order of the prefix filter: 0 = automatic (10), -1 = none,
                            1..12 = that order. One bit per b-mer, clear when a walk over
                            those b bases ends with no pattern on the way, so the answer
@@ -109,15 +105,16 @@ typedef struct {
     int32_t n_patterns;
     int32_t max_len;        /* longest pattern = deepest level of the trie */
     int32_t min_len;
-    int32_t jump_k;         /* order of the jump table, 0 if none */
     int32_t filter_b;       /* order of the prefix filter, 0 if none */
     int64_t n_duplicates;   /* patterns whose string was given before */
     int64_t table_bytes;    /* device bytes (all layouts) */
     int64_t rows_bytes;     /* 16-byte rows: 4 x int32 per state */
-    int64_t nodes_bytes;    /* 4-byte compact nodes, 0 if unavailable */
-    int32_t has_nodes;      /* compact node layout available (fewer than 2^27 states) */
-    int32_t jump_wide;      /* jump entries are 32-bit (else 16-bit) */
+    int64_t skip_bytes;     /* 16-byte skip entries, 0 if unavailable */
+    int64_t filter_set;     /* b-mers whose filter bit is set (= dense entries) */
+    int32_t has_skip;       /* skip entries available (fewer than 2^27 states) */
+    int32_t rank_wide;      /* the filter's rank index has 32-bit entries */
     int32_t device;         /* device holding the copy, -1 if host only */
+    int32_t pad;
 } pfac_table_info;
 
 int pfac_info_ex(pfac_handle h, pfac_table_info *info);
@@ -130,20 +127,24 @@ int pfac_info_ex(pfac_handle h, pfac_table_info *info);
  * Any output may be NULL. S = n_states from pfac_info. */
 int pfac_export(pfac_handle h, int32_t *rows, int32_t *out_id, int64_t *level);
 
-/* Copy the shortcut tables of a host-only handle (pfac_build_opts.host_only = 1) for
- * inspection; a handle with a device copy has dropped its host copy and gives
- * PFAC_ERR_UNSUPPORTED.
- *   jump[4^jump_k]  : entries of 2 bytes (4 if jump_wide) for the k-mer w whose base j
- *                     sits in bits 2j..2j+1: 0 = the walk over w ends before depth k
- *                     with no pattern on the way; 1 = a pattern ends within w;
- *                     2 + i = the walk reaches the i-th state of depth k
- *                     (breadth-first state level[k] + i)
- *   filter[max(1, 4^filter_b / 32)] : bit w (bit w mod 32 of word w / 32) is clear when
- *                     the walk over the b-mer w ends before depth b with no pattern on
- *                     the way
- * Either output may be NULL; sizes are checked against the tables. */
-int pfac_export_shortcuts(pfac_handle h, void *jump, int64_t jump_bytes, uint32_t *filter,
-                          int64_t filter_words);
+/* Copy the device-side encodings of a host-only handle (pfac_build_opts.host_only =
+ * 1) for inspection; a handle with a device copy has dropped its host copy and gives
+ * PFAC_ERR_UNSUPPORTED. All three describe the same trie as pfac_export:
+ *   skip[4*S]      : per state s, (label, meta, last, node): the chain of single-child
+ *                    edges below s. meta bits 0..4 = chain length L (0..16), bit 8 = s
+ *                    is terminal, bit 10 = the chain's last state is terminal; label
+ *                    holds the L bases (base i in bits 2i..2i+1); last = the state L
+ *                    bases below s; node = s's node word (bits 0..3 child mask, bit 4
+ *                    terminal, bits 5..31 first child)
+ *   filter[max(1, 4^b / 32)] : bit w (bit w mod 32 of word w / 32) of the b-mer w (base
+ *                    j in bits 2j..2j+1) is clear when the walk over w ends before depth
+ *                    b with no pattern on the way
+ *   dense[4*F]     : one entry per set filter bit, in b-mer order: the skip entry of the
+ *                    state of depth b the walk reaches, or meta bit 9 (special) when a
+ *                    pattern ends within the b-mer
+ * Any output may be NULL; sizes (in uint32 words) are checked against the tables. */
+int pfac_export_shortcuts(pfac_handle h, uint32_t *skip, int64_t skip_words, uint32_t *filter,
+                          int64_t filter_words, uint32_t *dense, int64_t dense_words);
 
 /* ---------------------------------------------------------------------------
  * Launch configuration (what the autotuner chooses). All fields 0 = automatic.
@@ -152,19 +153,18 @@ typedef struct {
     int32_t kernel;          /* 0 auto, 1 = per-offset walk over 16-byte rows in global
                                 memory (one thread per text offset, the paper's layout),
                                 2 = pipelined: text staged by TMA into a shared-memory
-                                ring; prefix filter, jump table and compact nodes in
-                                shared memory (needs both tables) */
+                                ring, prefix filter and its rank index in shared memory,
+                                skip-entry walks for the offsets the filter passes (needs
+                                the filter and skip entries) */
     int32_t threads;         /* kernel 2: threads per CTA, 64..1024, multiple of 32: one
                                 producer warp plus consumer warps; a tile is 512 bases
                                 per consumer warp */
     int32_t ctas_per_sm;     /* kernel 2: resident CTAs per SM of the persistent grid */
     int32_t stages;          /* kernel 2: text stages in the ring, 2..8 */
-    int32_t step_cap;        /* kernel 2: a walk still going this many steps past depth
-                                jump_k + 2 is finished by a separate tail kernel */
-    int32_t smem_table_bytes;/* kernel 2: shared memory for the window of compact nodes
-                                below the jump depth; -1 = none, 0 = all that fits */
-    int32_t l2_persist;      /* 1 = pin the nodes after the shared-memory window in L2
-                                with an access-policy window, -1 = never */
+    int32_t rank_in_smem;    /* kernel 2: -1 = keep the filter's rank index in global
+                                memory, 0 = in shared memory when it fits */
+    int32_t l2_persist;      /* 1 = keep the skip entries in L2 with an access-policy
+                                window, -1 = never, 0 = automatic */
 } pfac_config;
 
 /* Set (cfg != NULL) or reset (cfg == NULL) the launch configuration of a handle.

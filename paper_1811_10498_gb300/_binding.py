@@ -35,18 +35,19 @@ class PfacError(RuntimeError):
 
 
 class pfac_build_opts(C.Structure):
-    _fields_ = [("host_only", I32), ("jump_k", I32), ("filter_b", I32)]
+    _fields_ = [("host_only", I32), ("filter_b", I32)]
 
 
 class pfac_table_info(C.Structure):
     _fields_ = [("n_states", I64), ("n_patterns", I32), ("max_len", I32), ("min_len", I32),
-                ("jump_k", I32), ("filter_b", I32), ("n_duplicates", I64), ("table_bytes", I64), ("rows_bytes", I64),
-                ("nodes_bytes", I64), ("has_nodes", I32), ("jump_wide", I32), ("device", I32)]
+                ("filter_b", I32), ("n_duplicates", I64), ("table_bytes", I64), ("rows_bytes", I64),
+                ("skip_bytes", I64), ("filter_set", I64), ("has_skip", I32), ("rank_wide", I32),
+                ("device", I32), ("pad", I32)]
 
 
 class pfac_config(C.Structure):
-    _fields_ = [("kernel", I32), ("threads", I32), ("ctas_per_sm", I32), ("stages", I32), ("step_cap", I32),
-                ("smem_table_bytes", I32), ("l2_persist", I32)]
+    _fields_ = [("kernel", I32), ("threads", I32), ("ctas_per_sm", I32), ("stages", I32), ("rank_in_smem", I32),
+                ("l2_persist", I32)]
 
 
 _lib = None
@@ -62,7 +63,7 @@ _SIGS = {
     "pfac_info": (C.c_int, [P, P, P, P]),
     "pfac_info_ex": (C.c_int, [P, P]),
     "pfac_export": (C.c_int, [P, P, P, P]),
-    "pfac_export_shortcuts": (C.c_int, [P, P, I64, P, I64]),
+    "pfac_export_shortcuts": (C.c_int, [P, P, I64, P, I64, P, I64]),
     "pfac_set_config": (C.c_int, [P, P]),
     "pfac_get_config": (C.c_int, [P, I64, P]),
     "pfac_pack": (C.c_int, [P, I64, P, P, P, P]),
@@ -142,11 +143,11 @@ def _patterns(patterns):
 # Calls with the C names.
 # ---------------------------------------------------------------------------
 
-def pfac_build(patterns, jump_k: int = 0, host_only: bool = False, filter_b: int = 0) -> int:
+def pfac_build(patterns, host_only: bool = False, filter_b: int = 0) -> int:
     """Build a table from ``(blob, offsets)`` or a list of byte strings; returns the handle."""
     L = lib()
     blob, ptrs, lengths, n = _patterns(patterns)
-    opts = pfac_build_opts(int(host_only), int(jump_k), int(filter_b))
+    opts = pfac_build_opts(int(host_only), int(filter_b))
     h = L.pfac_build_ex(ptrs.ctypes.data, lengths.ctypes.data, n, C.byref(opts))
     if not h:
         raise PfacError(L.pfac_last_error(), "pfac_build")
@@ -180,14 +181,16 @@ def pfac_export(h: int):
 
 
 def pfac_export_shortcuts(h: int):
-    """(jump entries, filter words) of a host-only handle."""
+    """(skip entries [S, 4], filter words, dense entries [F, 4]) of a host-only handle."""
     info = pfac_info_ex(h)
-    k, b = info["jump_k"], info["filter_b"]
-    jump = np.zeros(1 << (2 * k) if k else 0, dtype=np.uint32 if info["jump_wide"] else np.uint16)
+    S, b, F = info["n_states"], info["filter_b"], info["filter_set"]
+    skip = np.zeros((S if info["has_skip"] else 0, 4), dtype=np.uint32)
     filt = np.zeros(max(1, (1 << (2 * b)) // 32) if b else 0, dtype=np.uint32)
-    _check(lib().pfac_export_shortcuts(h, jump.ctypes.data if jump.size else None, jump.nbytes,
-                                       filt.ctypes.data if filt.size else None, filt.size), "pfac_export_shortcuts")
-    return jump, filt
+    dense = np.zeros((F, 4), dtype=np.uint32)
+    ptr = lambda a: a.ctypes.data if a.size else None
+    _check(lib().pfac_export_shortcuts(h, ptr(skip), skip.size, ptr(filt), filt.size, ptr(dense), dense.size),
+           "pfac_export_shortcuts")
+    return skip, filt, dense
 
 
 def pfac_set_config(h: int, cfg: dict | None):
@@ -249,8 +252,8 @@ def pfac_debug_timeout_probe(d_status, limit_ns: int, stream=None):
 class Table:
     """Owns one table handle; destroys it when collected or closed."""
 
-    def __init__(self, patterns, jump_k: int = 0, host_only: bool = False, filter_b: int = 0):
-        self.h = pfac_build(patterns, jump_k=jump_k, host_only=host_only, filter_b=filter_b)
+    def __init__(self, patterns, host_only: bool = False, filter_b: int = 0):
+        self.h = pfac_build(patterns, host_only=host_only, filter_b=filter_b)
 
     def close(self):
         h, self.h = getattr(self, "h", None), None

@@ -21,7 +21,7 @@ struct pfac_table {
     int device = -1;
     void *dmem = nullptr;
     size_t dbytes = 0;
-    int64_t rows_bytes = 0, nodes_bytes = 0;
+    int64_t rows_bytes = 0, skip_bytes = 0, filter_set = 0;
     pfac::DeviceTable dt{};
     std::mutex mu;
     bool cfg_set = false;
@@ -42,7 +42,7 @@ int fail(int code)
 int cuda_fail(cudaError_t e)
 {
     g_last_cuda = cudaGetErrorString(e);
-    cudaGetLastError();   // clear a sticky-free error so later calls start clean
+    cudaGetLastError();   // clear a non-sticky error so later calls start clean
     return fail(PFAC_ERR_CUDA);
 }
 
@@ -66,7 +66,7 @@ int device_props(pfac::DeviceProps *out)
     return PFAC_OK;
 }
 
-// A d_* argument must be device (or managed) memory of the current device.
+// A d_* argument must be device (or managed) memory.
 bool is_device_ptr(const void *p)
 {
     if (!p) return false;
@@ -91,24 +91,23 @@ int check_handle_for_launch(pfac_handle h, pfac::DeviceProps *dp)
     return PFAC_OK;
 }
 
-pfac_config default_config(const pfac_table *h, int64_t n_bases, bool packed, const pfac::DeviceProps &dp)
+bool has_kernel2(const pfac_table *h) { return h->dt.skip && h->dt.filter && h->dt.dense; }
+
+pfac_config default_config(const pfac_table *h, bool packed)
 {
-    (void)n_bases;
-    (void)dp;
     pfac_config c{};
-    c.kernel = (h->dt.nodes && h->dt.jump && h->dt.filter) ? 2 : 1;
+    c.kernel = has_kernel2(h) ? 2 : 1;
     c.threads = 1024;
     c.ctas_per_sm = 1;
     c.stages = packed ? 4 : 2;
-    c.step_cap = 8;
-    c.smem_table_bytes = 0;
+    c.rank_in_smem = 0;
     c.l2_persist = 0;
     return c;
 }
 
-pfac_config effective_config(pfac_table *h, int64_t n_bases, bool packed, const pfac::DeviceProps &dp)
+pfac_config effective_config(pfac_table *h, bool packed)
 {
-    pfac_config d = default_config(h, n_bases, packed, dp);
+    pfac_config d = default_config(h, packed);
     std::lock_guard<std::mutex> lk(h->mu);
     if (!h->cfg_set) return d;
     pfac_config c = h->cfg;
@@ -116,7 +115,6 @@ pfac_config effective_config(pfac_table *h, int64_t n_bases, bool packed, const 
     if (c.threads == 0) c.threads = d.threads;
     if (c.ctas_per_sm == 0) c.ctas_per_sm = d.ctas_per_sm;
     if (c.stages == 0) c.stages = d.stages;
-    if (c.step_cap == 0) c.step_cap = d.step_cap;
     return c;
 }
 
@@ -126,8 +124,7 @@ pfac::TiledConfig tiled_config(const pfac_config &c)
     t.threads = c.threads;
     t.ctas_per_sm = c.ctas_per_sm;
     t.stages = c.stages;
-    t.step_cap = c.step_cap;
-    t.smem_table_bytes = c.smem_table_bytes;
+    t.smem_table_bytes = c.rank_in_smem < 0 ? -1 : 0;
     t.l2_persist = c.l2_persist;
     t.timeout_ns = 2000000000LL;
     return t;
@@ -184,15 +181,14 @@ int get_scratch(int dev, cudaStream_t st, int64_t n, pfac::DeferScratch *out)
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Run the scan with the handle's configuration; the tiled kernel needs 16-byte
-// aligned text and output and a table with compact nodes; otherwise kernel 1 runs.
+// Run the scan with the handle's configuration. Kernel 2 needs 16-byte aligned text
+// and output, the filter and the skip entries; otherwise kernel 1 runs.
 int run_scan(pfac_handle h, const void *text, bool packed, int64_t n, int32_t *out, int64_t *c_off,
              int32_t *c_ids, int64_t cap, int64_t *count, cudaStream_t st, const pfac::DeviceProps &dp)
 {
-    pfac_config c = effective_config(h, n, packed, dp);
+    pfac_config c = effective_config(h, packed);
     const bool compact = c_off != nullptr;
-    bool tiled = c.kernel == 2 && h->dt.nodes && h->dt.jump && h->dt.filter && aligned16(text) &&
-                 (compact || aligned16(out));
+    bool tiled = c.kernel == 2 && has_kernel2(h) && aligned16(text) && (compact || aligned16(out));
     int rc = PFAC_OK;
     if (tiled) {
         pfac::TiledConfig tc = tiled_config(c);
@@ -201,7 +197,7 @@ int run_scan(pfac_handle h, const void *text, bool packed, int64_t n, int32_t *o
         if (rc != PFAC_OK) return rc;
         rc = pfac::launch_tiled(h->dt, text, packed, n, out, c_off, c_ids, cap, (unsigned long long *)count, tc,
                                 scratch, st, dp);
-        if (rc == PFAC_ERR_UNSUPPORTED) tiled = false;   // e.g. a halo too long for shared memory
+        if (rc == PFAC_ERR_UNSUPPORTED) tiled = false;   // the configuration does not fit shared memory
         else if (rc != PFAC_OK) return rc == PFAC_ERR_CUDA ? cuda_fail(cudaGetLastError()) : fail(rc);
     }
     if (!tiled) {
@@ -246,23 +242,29 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
     if (opts) o = *opts;
     pfac_table *h = new (std::nothrow) pfac_table();
     if (!h) { fail(PFAC_ERR_OOM); return nullptr; }
-    int rc = pfac::build_host_tables(patterns, lengths, n, o.jump_k, o.filter_b, &h->host);
+    int rc = pfac::build_host_tables(patterns, lengths, n, o.filter_b, &h->host);
     if (rc != PFAC_OK) { delete h; fail(rc); return nullptr; }
     const pfac::HostTables &T = h->host;
     h->rows_bytes = T.n_states * 16;
-    h->nodes_bytes = (int64_t)T.nodes.size() * 4;
+    h->skip_bytes = (int64_t)T.skip.size() * 4;
+    h->filter_set = (int64_t)T.dense.size() / 4;
     if (!o.host_only) {
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) { delete h; cuda_fail(e); return nullptr; }
-        const size_t s_status = 256;
-        const size_t s_rows = round256((size_t)T.n_states * 16);
-        const size_t s_nodes = round256(T.nodes.size() * 4);
-        const size_t s_out = round256((size_t)T.n_states * 4);
-        const size_t jump_bytes = T.jump16.size() * 2 + T.jump32.size() * 4;
-        const size_t s_jump = round256(jump_bytes);
-        const size_t s_filter = round256(T.filter.size() * 4);
-        h->dbytes = s_status + s_rows + s_nodes + s_out + s_jump + s_filter;
+        const size_t rank_bytes = T.rank16.size() * 2 + T.rank32.size() * 4;
+        struct Part { const void **dst; const void *src; size_t bytes; } parts[] = {
+            {(const void **)&h->dt.rows, T.rows.data(), T.rows.size() * 4},
+            {(const void **)&h->dt.out_id, T.out_id.data(), T.out_id.size() * 4},
+            {(const void **)&h->dt.skip, T.skip.data(), T.skip.size() * 4},
+            {(const void **)&h->dt.filter, T.filter.data(), T.filter.size() * 4},
+            {(const void **)&h->dt.rank, T.rank_wide ? (const void *)T.rank32.data() : (const void *)T.rank16.data(),
+             rank_bytes},
+            {(const void **)&h->dt.dense, T.dense.data(), T.dense.size() * 4},
+        };
+        size_t total = 256;   // status word
+        for (auto &p : parts) total += round256(p.bytes);
+        h->dbytes = total;
         e = cudaMalloc(&h->dmem, h->dbytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -271,24 +273,14 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
             return nullptr;
         }
         uint8_t *base = (uint8_t *)h->dmem;
-        size_t off = 0;
-        h->dt.status = (int32_t *)(base + off); off += s_status;
-        h->dt.rows = (const int32_t *)(base + off); off += s_rows;
-        h->dt.nodes = T.nodes.empty() ? nullptr : (const uint32_t *)(base + off); off += s_nodes;
-        h->dt.out_id = (const int32_t *)(base + off); off += s_out;
-        h->dt.jump = jump_bytes ? (const void *)(base + off) : nullptr; off += s_jump;
-        h->dt.filter = T.filter.empty() ? nullptr : (const uint32_t *)(base + off); off += s_filter;
-        const void *jump_src = T.jump_wide ? (const void *)T.jump32.data() : (const void *)T.jump16.data();
-        struct Up { const void *dst; const void *src; size_t bytes; } ups[] = {
-            {h->dt.rows, T.rows.data(), T.rows.size() * 4},
-            {h->dt.nodes, T.nodes.data(), T.nodes.size() * 4},
-            {h->dt.out_id, T.out_id.data(), T.out_id.size() * 4},
-            {h->dt.jump, jump_src, jump_bytes},
-            {h->dt.filter, T.filter.data(), T.filter.size() * 4},
-        };
-        e = cudaMemset(h->dt.status, 0, s_status);
-        for (auto &u : ups)
-            if (e == cudaSuccess && u.dst && u.bytes) e = cudaMemcpy((void *)u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
+        h->dt.status = (int32_t *)base;
+        e = cudaMemset(h->dt.status, 0, 256);
+        size_t off = 256;
+        for (auto &p : parts) {
+            *p.dst = p.bytes ? (const void *)(base + off) : nullptr;
+            if (e == cudaSuccess && p.bytes) e = cudaMemcpy(base + off, p.src, p.bytes, cudaMemcpyHostToDevice);
+            off += round256(p.bytes);
+        }
         if (e != cudaSuccess) {
             cudaFree(h->dmem);
             delete h;
@@ -298,16 +290,14 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         h->device = dev;
         h->dt.n_states = T.n_states;
         h->dt.max_len = T.max_len;
-        h->dt.jump_k = T.jump_k;
-        h->dt.jump_wide = T.jump_wide;
         h->dt.filter_b = T.filter_b;
-        h->dt.level_k = T.jump_k > 0 ? T.level[(size_t)T.jump_k] : 0;
-        h->dt.level_k1 = T.jump_k > 0 ? T.level[(size_t)T.jump_k + 1] : 0;
+        h->dt.rank_wide = T.rank_wide;
         // The device copy is complete; the host keeps rows, ids and levels for export.
-        std::vector<uint32_t>().swap(h->host.nodes);
-        std::vector<uint16_t>().swap(h->host.jump16);
-        std::vector<uint32_t>().swap(h->host.jump32);
+        std::vector<uint32_t>().swap(h->host.skip);
         std::vector<uint32_t>().swap(h->host.filter);
+        std::vector<uint16_t>().swap(h->host.rank16);
+        std::vector<uint32_t>().swap(h->host.rank32);
+        std::vector<uint32_t>().swap(h->host.dense);
     }
     return h;
 }
@@ -350,14 +340,14 @@ int pfac_info_ex(pfac_handle h, pfac_table_info *info)
     i.n_patterns = h->host.n_patterns;
     i.max_len = h->host.max_len;
     i.min_len = h->host.min_len;
-    i.jump_k = h->host.jump_k;
     i.filter_b = h->host.filter_b;
     i.n_duplicates = h->host.n_duplicates;
     i.table_bytes = (int64_t)h->dbytes;
     i.rows_bytes = h->rows_bytes;
-    i.nodes_bytes = h->nodes_bytes;
-    i.has_nodes = h->nodes_bytes > 0;
-    i.jump_wide = h->host.jump_wide;
+    i.skip_bytes = h->skip_bytes;
+    i.filter_set = h->filter_set;
+    i.has_skip = h->skip_bytes > 0;
+    i.rank_wide = h->host.rank_wide;
     i.device = h->device;
     *info = i;
     return PFAC_OK;
@@ -373,21 +363,18 @@ int pfac_export(pfac_handle h, int32_t *rows, int32_t *out_id, int64_t *level)
     return PFAC_OK;
 }
 
-int pfac_export_shortcuts(pfac_handle h, void *jump, int64_t jump_bytes, uint32_t *filter, int64_t filter_words)
+int pfac_export_shortcuts(pfac_handle h, uint32_t *skip, int64_t skip_words, uint32_t *filter, int64_t filter_words,
+                          uint32_t *dense, int64_t dense_words)
 {
     if (!h) return fail(PFAC_ERR_INVALID_ARG);
-    const pfac::HostTables &T = h->host;
     if (h->device >= 0) return fail(PFAC_ERR_UNSUPPORTED);
-    if (jump) {
-        const int64_t need = (int64_t)(T.jump_wide ? T.jump32.size() * 4 : T.jump16.size() * 2);
-        if (jump_bytes < need) return fail(PFAC_ERR_INVALID_ARG);
-        if (T.jump_wide) memcpy(jump, T.jump32.data(), (size_t)need);
-        else memcpy(jump, T.jump16.data(), (size_t)need);
-    }
-    if (filter) {
-        if (filter_words < (int64_t)T.filter.size()) return fail(PFAC_ERR_INVALID_ARG);
-        memcpy(filter, T.filter.data(), T.filter.size() * 4);
-    }
+    const pfac::HostTables &T = h->host;
+    struct Out { uint32_t *dst; int64_t cap; const std::vector<uint32_t> &src; } outs[] = {
+        {skip, skip_words, T.skip}, {filter, filter_words, T.filter}, {dense, dense_words, T.dense}};
+    for (auto &o : outs)
+        if (o.dst && o.cap < (int64_t)o.src.size()) return fail(PFAC_ERR_INVALID_ARG);
+    for (auto &o : outs)
+        if (o.dst) memcpy(o.dst, o.src.data(), o.src.size() * 4);
     return PFAC_OK;
 }
 
@@ -397,10 +384,9 @@ int pfac_set_config(pfac_handle h, const pfac_config *cfg)
     if (cfg) {
         if (cfg->kernel < 0 || cfg->kernel > 2 || cfg->threads < 0 || (cfg->threads & 31) || cfg->threads > 1024 ||
             (cfg->threads > 0 && cfg->threads < 64) || cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32 ||
-            cfg->stages < 0 || cfg->stages == 1 || cfg->stages > 8 || cfg->step_cap < 0 || cfg->step_cap > 24)
+            cfg->stages < 0 || cfg->stages == 1 || cfg->stages > 8)
             return fail(PFAC_ERR_INVALID_ARG);
-        if (cfg->kernel == 2 && !(h->nodes_bytes > 0 && h->host.jump_k > 0 && h->host.filter_b > 0))
-            return fail(PFAC_ERR_UNSUPPORTED);
+        if (cfg->kernel == 2 && !(h->skip_bytes > 0 && h->host.filter_b > 0)) return fail(PFAC_ERR_UNSUPPORTED);
     }
     std::lock_guard<std::mutex> lk(h->mu);
     h->cfg_set = cfg != nullptr;
@@ -410,13 +396,9 @@ int pfac_set_config(pfac_handle h, const pfac_config *cfg)
 
 int pfac_get_config(pfac_handle h, int64_t n_bases, pfac_config *cfg)
 {
+    (void)n_bases;
     if (!h || !cfg) return fail(PFAC_ERR_INVALID_ARG);
-    pfac::DeviceProps dp{};
-    if (h->device >= 0) {
-        int rc = device_props(&dp);
-        if (rc != PFAC_OK) return rc;
-    }
-    *cfg = effective_config(h, n_bases, true, dp);
+    *cfg = effective_config(h, true);
     return PFAC_OK;
 }
 

@@ -21,6 +21,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "../../include/pfac.h"
 #include "pfac_internal.h"
@@ -275,11 +276,6 @@ int launch_walk_rows_any(const DeviceTable &t, const void *text, bool packed, in
     return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
 }
 
-int launch_walk_rows(const DeviceTable &t, const void *text, bool packed, int64_t n, int32_t *out,
-                     cudaStream_t st, const DeviceProps &dp)
-{
-    return launch_walk_rows_any(t, text, packed, n, out, nullptr, nullptr, 0, nullptr, st, dp);
-}
 
 // ---------------------------------------------------------------------------
 // Kernel 2: warp-specialised pipeline.
@@ -288,17 +284,17 @@ int launch_walk_rows(const DeviceTable &t, const void *text, bool packed, int64_
 //     into an S-stage shared-memory ring with TMA bulk copies; full/empty mbarriers
 //     hand stages to the consumer warps and back, with bounded waits;
 //   * each consumer lane owns 16 consecutive offsets and reads one 48-base window
-//     (three packed words) from the stage. A fully unrolled, branch-free block does
-//     for every offset: one jump-table lookup (first k bases) and the next two steps
-//     through compact node words (the node of depth k comes with the jump entry, the
-//     node of depth k+1 from the shared-memory window). Results go out as four
-//     128-bit stores;
-//   * the few walks still going at depth k+2 (or that need a pattern id ending inside
-//     the jump prefix, or sit near the text end) continue in a per-lane loop, from
-//     the same register window, up to depth k+2+cap;
-//   * walks longer than that (true hits along a long pattern) are appended to a
-//     deferred list in global scratch memory and finished by a tail kernel, so no
-//     latency-bound chain ever holds a pipeline stage.
+//     (three packed words) from the stage. A fully unrolled, branch-free block tests
+//     the prefix filter for every offset (one shared-memory load): a clear bit means
+//     the walk ends before depth b with no pattern on the way, answer 0;
+//   * the offsets whose bit is set (a few percent) are spread over the warp by a
+//     shuffle scan; each takes its filter bit's rank (shared-memory rank index) to a
+//     dense skip entry, the state of depth b, and walks on through skip entries
+//     (chains of single-child edges compared up to 16 bases at a time) inside the
+//     register window;
+//   * a walk that reaches the end of the window while the text goes on is appended to
+//     a deferred list in global scratch memory and finished by a tail kernel.
+// Results: zeros go out as 128-bit stores (evict-first), matches as single stores.
 // ---------------------------------------------------------------------------
 
 struct DeferItem {
@@ -327,22 +323,10 @@ struct ScanParams {
     int32_t consumers;           // consumer warps (the producer is warp `consumers`)
     int32_t stages;
     int32_t stage_units;         // packed words or ASCII bytes per stage
-    int32_t qmax;                // a walk still going after qmax bases is deferred
-    int32_t jump_smem;           // jump table copied into shared memory
-    uint32_t win_len;            // window slots in shared memory (two sentinels + states)
-    uint32_t off_filter, off_jump, off_win, off_stage, stage_bytes;
+    int32_t rank_smem;           // rank index copied into shared memory
+    uint32_t off_filter, off_rank, off_stage, stage_bytes;
     int64_t timeout_ns;
 };
-
-// Node word of state s at depth >= jump_k: window slot s - level_k + 2 when the
-// window holds it, else global memory (L2 / HBM). States above depth jump_k (root
-// walks) always come from global memory.
-__device__ __forceinline__ uint32_t node_at(uint32_t s, const uint32_t *sw, uint32_t level_k, uint32_t win_states,
-                                            const uint32_t *__restrict__ nodes)
-{
-    const uint32_t rel = s - level_k;    // wraps for states above depth jump_k
-    return rel < win_states ? sw[rel + kJumpFirst] : __ldg(nodes + s);
-}
 
 constexpr int kMaxStages = 8;
 constexpr uint32_t kBarBytes = 256;   // full[8], empty[8], abort flag
@@ -376,29 +360,65 @@ __device__ __forceinline__ void st_global_v4_hint(int32_t *p, int4 v, uint64_t p
                  : "memory");
 }
 
-// Continue a walk in global memory (text and nodes), for deferred walks and for
-// walks that could not be deferred. Returns the pattern id (0 if none).
+// Mask of the first L 2-bit bases (L = 1..16).
+__device__ __forceinline__ uint32_t base_mask(uint32_t L)
+{
+    return L >= 16 ? 0xFFFFFFFFu : ((1u << (2 * L)) - 1u);
+}
+
+// Sixteen bases of the text from position pos (packed or ASCII) read from global
+// memory, with a mask of the bases that cannot be read (past the end of the text,
+// or ASCII bytes outside ACGT).
+template <bool PACKED>
+__device__ __forceinline__ uint32_t text16(const void *__restrict__ text, int64_t n, int64_t pos, uint32_t *bad)
+{
+    const int64_t rem = n - pos;
+    uint32_t b = rem >= 16 ? 0u : (rem > 0 ? (0xFFFFu << rem) & 0xFFFFu : 0xFFFFu);
+    uint32_t w = 0;
+    if (PACKED) {
+        const int64_t wi = pos >> 4;
+        const int64_t n_words = (n + 15) >> 4;
+        const uint32_t lo = wi < n_words ? __ldg((const uint32_t *)text + wi) : 0u;
+        const uint32_t hi = wi + 1 < n_words ? __ldg((const uint32_t *)text + wi + 1) : 0u;
+        w = __funnelshift_r(lo, hi, (uint32_t)(pos & 15) * 2);
+    } else {
+        for (int i = 0; i < 16 && pos + i < n; i++) {
+            const int c = base_code_or_neg(__ldg((const uint8_t *)text + pos + i));
+            if (c < 0) b |= 1u << i;
+            else w |= (uint32_t)c << (2 * i);
+        }
+    }
+    *bad = b;
+    return w;
+}
+
+// Continue a walk from state s with `q` bases consumed, reading the text from global
+// memory (deferred walks, and walks the deferred list had no room for). Returns the
+// pattern id (0 if none).
 template <bool PACKED>
 __device__ int32_t walk_global(const DeviceTable &T, const void *__restrict__ text, int64_t n, int64_t gp,
                                uint32_t s, int q, uint32_t best)
 {
-    const uint32_t *__restrict__ nodes = T.nodes;
-    uint32_t nd = __ldg(nodes + s);
-    const int64_t lim = min(n - gp, (int64_t)T.max_len);
-    while (q < lim) {
-        const int64_t pos = gp + q;
-        int c;
-        if (PACKED) {
-            c = (int)((__ldg((const uint32_t *)text + (pos >> 4)) >> ((pos & 15) * 2)) & 3u);
+    uint4 e = __ldg(T.skip + s);
+    for (;;) {
+        if (e.y & kSkipSelfTerm) best = s;
+        const uint32_t L = e.y & kSkipLenMask;
+        uint32_t bad;
+        const uint32_t win = text16<PACKED>(text, n, gp + q, &bad);
+        const uint32_t need = L ? L : 1u;
+        if (bad & ((need >= 16) ? 0xFFFFu : ((1u << need) - 1u))) break;   // cannot read the next step
+        if (L) {
+            if ((win ^ e.x) & base_mask(L)) break;
+            q += (int)L;
+            s = e.z;
+            if (e.y & kSkipTargetTerm) best = s;
         } else {
-            c = base_code_or_neg(__ldg((const uint8_t *)text + pos));
-            if (c < 0) break;
+            const uint32_t c = win & 3u;
+            if (!((e.w >> c) & 1u)) break;
+            s = (e.w >> kNodeFirstShift) + __popc(e.w & ((1u << c) - 1u));
+            q++;
         }
-        if (!((nd >> c) & 1u)) break;
-        s = (nd >> kNodeFirstShift) + __popc(nd & ((1u << c) - 1u));
-        nd = __ldg(nodes + s);
-        if (nd & kNodeTermBit) best = s;
-        q++;
+        e = __ldg(T.skip + s);
     }
     return best ? __ldg(T.out_id + best) : 0;
 }
@@ -432,45 +452,33 @@ __device__ __forceinline__ uint32_t clear_runs(uint64_t bad, int w)
     return (uint32_t)(~t) & 0xFFFFu;
 }
 
-template <typename JW>
-__device__ __forceinline__ uint32_t jump_entry(const ScanParams &P, const JW *sj, uint32_t kmer)
+// Sixteen bases of a lane's 48-base window from position p (0 <= p < 48); bases past
+// the window read as 0.
+__device__ __forceinline__ uint32_t window_at(uint32_t x0, uint32_t x1, uint32_t x2, int p)
 {
-    return P.jump_smem ? (uint32_t)sj[kmer] : (uint32_t)__ldg(reinterpret_cast<const JW *>(P.t.jump) + kmer);
+    const uint32_t lo = p < 16 ? x0 : (p < 32 ? x1 : x2);
+    const uint32_t hi = p < 16 ? x1 : (p < 32 ? x2 : 0u);
+    return __funnelshift_r(lo, hi, (uint32_t)(p & 15) * 2);
 }
 
-// Node word of window slot v (a jump entry). FULL: the window holds every state of
-// depth jump_k, so every slot a jump entry names is in shared memory.
-template <bool FULL>
-__device__ __forceinline__ uint32_t node_of_slot(uint32_t v, const uint32_t *sw, uint32_t win_slots, uint32_t level_k,
-                                                 const uint32_t *__restrict__ nodes)
-{
-    if (FULL) return sw[v];
-    return v < win_slots ? sw[v] : __ldg(nodes + (level_k + v - kJumpFirst));
-}
-
-template <bool PACKED, bool COMPACT, typename JW, bool FSMEM>
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16>
 __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    const uint32_t *sf = reinterpret_cast<const uint32_t *>(smem + P.off_filter);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = reinterpret_cast<uint64_t *>(smem + 64);
     volatile uint32_t *abort_flag = reinterpret_cast<volatile uint32_t *>(smem + 128);
-    const JW *sj = reinterpret_cast<const JW *>(smem + P.off_jump);
-    const uint32_t *sw = reinterpret_cast<const uint32_t *>(smem + P.off_win);
+    const uint32_t *sf = reinterpret_cast<const uint32_t *>(smem + P.off_filter);
     uint8_t *stage0 = smem + P.off_stage;
+    using RankT = typename std::conditional<RANK16, uint16_t, uint32_t>::type;
+    const RankT *srank = reinterpret_cast<const RankT *>(smem + P.off_rank);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const DeviceTable &T = P.t;
-    const int K = T.jump_k;
-    const uint32_t kmask = (uint32_t)((1ull << (2 * K)) - 1ull);
     const int B = T.filter_b;
     const uint32_t bmask = (uint32_t)((1ull << (2 * B)) - 1ull);
     const int S = P.stages;
     const int64_t n = P.n;
-    const uint32_t level_k = (uint32_t)T.level_k;
-    const uint32_t win_slots = P.win_len;                 // sentinels included
-    const uint32_t win_states = P.win_len - kJumpFirst;   // states of depth >= jump_k held
 
     if (tid == 0) {
         for (int i = 0; i < S; i++) {
@@ -481,7 +489,7 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
         fence_mbar_init();
     }
     {
-        // filter, jump table and node window, resident for the whole persistent kernel
+        // filter and rank index, resident for the whole persistent kernel
         auto copy_in = [&](uint32_t off, const void *src_v, int64_t bytes) {
             uint8_t *dst = smem + off;
             const uint8_t *src = (const uint8_t *)src_v;
@@ -489,14 +497,9 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                 *reinterpret_cast<uint4 *>(dst + i) = __ldg(reinterpret_cast<const uint4 *>(src + i));
             for (int64_t i = (bytes & ~(int64_t)15) + tid; i < bytes; i += blockDim.x) dst[i] = src[i];
         };
-        if (FSMEM) copy_in(P.off_filter, T.filter, (((int64_t)1 << (2 * B)) + 7) / 8);
-        if (P.jump_smem) copy_in(P.off_jump, T.jump, (int64_t)sizeof(JW) << (2 * K));
-        uint32_t *ww = reinterpret_cast<uint32_t *>(smem + P.off_win);
-        if (tid == 0) {
-            ww[kJumpDead] = 0u;              // no edges: the walk ends
-            ww[kJumpSpecial] = kNodeMaskBits; // every edge: go to the full walk
-        }
-        for (uint32_t i = tid; i < win_states; i += blockDim.x) ww[kJumpFirst + i] = __ldg(T.nodes + level_k + i);
+        const int64_t words = B >= 3 ? ((int64_t)1 << (2 * B)) / 32 : 1;
+        if (FSMEM) copy_in(P.off_filter, T.filter, words * 4);
+        if (P.rank_smem) copy_in(P.off_rank, T.rank, words * (int64_t)sizeof(RankT));
     }
     __syncthreads();
 
@@ -618,6 +621,7 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             }
             const uint32_t om = __shfl_sync(0xFFFFFFFFu, pend, owner);
             const uint32_t oe = __shfl_sync(0xFFFFFFFFu, excl, owner);
+            const uint32_t ofast = __shfl_sync(0xFFFFFFFFu, fast, owner);
             const uint32_t ox0 = __shfl_sync(0xFFFFFFFFu, x0, owner);
             const uint32_t ox1 = __shfl_sync(0xFFFFFFFFu, x1, owner);
             const uint32_t ox2 = __shfl_sync(0xFFFFFFFFu, x2, owner);
@@ -629,39 +633,54 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             for (uint32_t i = r - oe; i > 0; i--) m &= m - 1u;
             const int j = (__ffs(m) - 1) & 15;
             const int64_t gp = t * (int64_t)P.tile + warp * 512 + owner * 16 + j;
-            const uint64_t lo64 = ((uint64_t)ox1 << 32) | ox0;
-            uint64_t rest = j ? ((lo64 >> (2 * j)) | ((uint64_t)ox2 << (64 - 2 * j))) : lo64;   // bases j..j+31
             const uint64_t badj = (((uint64_t)obad_hi << 32) | obad_lo) >> j;
+            // bases readable from the window; `ends` when the text (or the run of ACGT
+            // bytes) really stops there rather than the window
             const int wlim = badj ? __ffsll((long long)badj) - 1 : 48 - j;
-            const int lim = min(wlim, T.max_len);
-            uint32_t s = 0, nd, best = 0;
+            const bool ends = badj != 0;
+            uint32_t s = 0, best = 0;
             int q = 0;
-            // jump over the first K bases when they are readable, else walk from the root
-            const uint32_t v = wlim >= K ? jump_entry<JW>(P, sj, (uint32_t)rest & kmask) : kJumpSpecial;
-            if (v != kJumpSpecial) {
-                s = level_k + v - kJumpFirst;
-                nd = node_of_slot<false>(v, sw, win_slots, level_k, T.nodes);
-                rest >>= 2 * K;
-                q = K;
-            } else {
-                nd = __ldg(T.nodes);     // the root
+            uint4 e;
+            bool from_root = true;
+            if ((ofast >> j) & 1u) {
+                const uint32_t kmer = window_at(ox0, ox1, ox2, j) & bmask;
+                const uint32_t widx = kmer >> 5;
+                const uint32_t word = FSMEM ? sf[widx] : __ldg(T.filter + widx);
+                const uint32_t base_rank = P.rank_smem ? (uint32_t)srank[widx]
+                                                       : (uint32_t)__ldg(reinterpret_cast<const RankT *>(T.rank) + widx);
+                const uint32_t rk = base_rank + __popc(word & ((1u << (kmer & 31u)) - 1u));
+                e = __ldg(T.dense + rk);
+                if (!(e.y & kSkipSpecial)) {
+                    from_root = false;
+                    q = B;
+                }
             }
-            // walk inside the register window: at most qmax bases
-            const int qstop = min(lim, P.qmax);
-            bool live = true;
-            while (q < qstop) {
-                const uint32_t c = (uint32_t)rest & 3u;
-                rest >>= 2;
-                if (!((nd >> c) & 1u)) {
-                    live = false;
+            if (from_root) e = __ldg(T.skip);
+            // walk on through skip entries inside the window
+            bool defer = false;
+            for (;;) {
+                if (e.y & kSkipSelfTerm) best = s;
+                const uint32_t L = e.y & kSkipLenMask;
+                const int need = L ? (int)L : 1;
+                if (q + need > wlim) {
+                    defer = !ends;     // the window ran out before the text did
                     break;
                 }
-                s = (nd >> kNodeFirstShift) + __popc(nd & ((1u << c) - 1u));
-                nd = node_at(s, sw, level_k, win_states, T.nodes);
-                q++;
-                if (nd & kNodeTermBit) best = s;
+                const uint32_t win = window_at(ox0, ox1, ox2, j + q);
+                if (L) {
+                    if ((win ^ e.x) & base_mask(L)) break;
+                    q += (int)L;
+                    s = e.z;
+                    if (e.y & kSkipTargetTerm) best = s;
+                } else {
+                    const uint32_t c = win & 3u;
+                    if (!((e.w >> c) & 1u)) break;
+                    s = (e.w >> kNodeFirstShift) + __popc(e.w & ((1u << c) - 1u));
+                    q++;
+                }
+                e = __ldg(T.skip + s);
             }
-            if (live && q == P.qmax && q < lim && (nd & kNodeMaskBits)) {
+            if (defer) {
                 // long walk: finish it in the tail kernel (or here if the list is full)
                 const unsigned long long di = atomicAdd(P.defer_count, 1ull);
                 if ((int64_t)di < P.defer_cap) {
@@ -676,8 +695,6 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                     emit_match<COMPACT>(P, gp, walk_global<PACKED>(T, P.text, n, gp, s, q, best));
                 }
             } else if (best) {
-                // the walk met a missing edge, an unreadable base or the deepest level;
-                // qmax <= 32 < 48 - j, so the window never runs out first
                 emit_match<COMPACT>(P, gp, __ldg(T.out_id + best));
             }
         }
@@ -697,24 +714,22 @@ __global__ void __launch_bounds__(256) tail_kernel(const ScanParams P)
 }
 
 struct ScanLayout {
-    uint32_t off_filter, off_jump, off_win, off_stage, stage_bytes, total;
+    uint32_t off_filter, off_rank, off_stage, stage_bytes, total;
     int32_t stage_units;
 };
 
 static inline uint32_t align128(uint64_t x) { return (uint32_t)((x + 127) & ~(uint64_t)127); }
 
-static ScanLayout scan_layout(int consumers, int stages, int64_t filter_smem_bytes, int64_t jump_smem_bytes,
-                              bool packed, uint32_t win_slots)
+static ScanLayout scan_layout(int consumers, int stages, int64_t filter_smem_bytes, int64_t rank_smem_bytes,
+                              bool packed)
 {
     ScanLayout L{};
     const int64_t tile = 512LL * consumers;
     uint64_t off = kBarBytes;
     L.off_filter = (uint32_t)off;
     off += align128((uint64_t)filter_smem_bytes);
-    L.off_jump = (uint32_t)off;
-    off += align128((uint64_t)jump_smem_bytes);
-    L.off_win = (uint32_t)off;
-    off += align128((uint64_t)win_slots * 4);
+    L.off_rank = (uint32_t)off;
+    off += align128((uint64_t)rank_smem_bytes);
     // a lane reads 48 bases from its first offset: 2 words (32 bytes) past the tile
     L.stage_units = packed ? (int32_t)(tile / 16 + 4) : (int32_t)(tile + 48);
     L.stage_bytes = align128((uint64_t)L.stage_units * (packed ? 4 : 1));
@@ -728,11 +743,9 @@ static int consumers_of(const TiledConfig &cfg) { return cfg.threads / 32 - 1; }
 static int stages_of(const TiledConfig &cfg, bool packed) { return cfg.stages > 0 ? cfg.stages : (packed ? 4 : 2); }
 
 // Shared memory per CTA, by priority: the text stages, the prefix filter (read for
-// every offset), the jump table (read for every walk that passes the filter), then
-// as many states of depth >= jump_k as the remaining budget holds.
+// every offset), then the rank index (read for every walk the filter passes).
 struct SmemPlan {
-    int64_t filter_bytes, jump_bytes;   // bytes copied into shared memory (0 = global)
-    int32_t win_len;                    // window slots (two sentinels + states)
+    int64_t filter_bytes, rank_bytes;   // bytes copied into shared memory (0 = global)
     int64_t total;
 };
 
@@ -743,58 +756,85 @@ static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool pac
     const int S = stages_of(cfg, packed);
     const int64_t per_cta = (int64_t)dp.smem_per_sm / std::max(1, cfg.ctas_per_sm) - 1024;
     const int64_t limit = std::min<int64_t>(dp.smem_optin, per_cta);
-    const int64_t fbytes = (((int64_t)1 << (2 * t.filter_b)) + 7) / 8;
-    const int64_t jbytes = (t.jump_wide ? 4LL : 2LL) << (2 * t.jump_k);
-    auto total = [&](int64_t f, int64_t j, int64_t w) { return (int64_t)scan_layout(C, S, f, j, packed, (uint32_t)w).total; };
-    if (total(0, 0, kJumpFirst) > limit) {
+    const int64_t words = t.filter_b >= 3 ? ((int64_t)1 << (2 * t.filter_b)) / 32 : 1;
+    const int64_t fbytes = words * 4;
+    const int64_t rbytes = words * (t.rank_wide ? 4 : 2);
+    auto total = [&](int64_t f, int64_t r) { return (int64_t)scan_layout(C, S, f, r, packed).total; };
+    if (total(0, 0) > limit) {
         pl.total = -1;
         return pl;
     }
-    pl.filter_bytes = total(fbytes, 0, kJumpFirst) <= limit ? fbytes : 0;
-    pl.jump_bytes = total(pl.filter_bytes, jbytes, kJumpFirst) <= limit ? jbytes : 0;
-    int64_t states = 0;
-    if (cfg.smem_table_bytes >= 0) {
-        const int64_t room = limit - total(pl.filter_bytes, pl.jump_bytes, kJumpFirst);
-        const int64_t budget = cfg.smem_table_bytes > 0 ? std::min<int64_t>(cfg.smem_table_bytes, room) : room;
-        states = std::max<int64_t>(0, std::min<int64_t>(budget / 4, t.n_states - t.level_k));
-        while (states > 0 && total(pl.filter_bytes, pl.jump_bytes, kJumpFirst + states) > limit) states -= 32;
-        states = std::max<int64_t>(states, 0);
-    }
-    pl.win_len = (int32_t)(kJumpFirst + states);
-    pl.total = total(pl.filter_bytes, pl.jump_bytes, pl.win_len);
+    pl.filter_bytes = total(fbytes, 0) <= limit ? fbytes : 0;
+    pl.rank_bytes = (cfg.smem_table_bytes >= 0 && total(pl.filter_bytes, rbytes) <= limit) ? rbytes : 0;
+    pl.total = total(pl.filter_bytes, pl.rank_bytes);
     return pl;
 }
 
-int64_t tiled_smem_bytes(const DeviceTable &t, const TiledConfig &cfg, bool packed, int32_t *win_len_out,
-                         int32_t *jump_smem_out, const DeviceProps &dp)
+int64_t tiled_smem_bytes(const DeviceTable &t, const TiledConfig &cfg, bool packed, const DeviceProps &dp)
 {
-    const SmemPlan pl = plan_smem(t, cfg, packed, dp);
-    if (win_len_out) *win_len_out = pl.win_len;
-    if (jump_smem_out) *jump_smem_out = pl.jump_bytes > 0;
-    return pl.total;
+    return plan_smem(t, cfg, packed, dp).total;
 }
 
-template <bool PACKED, bool COMPACT, typename JW, bool FSMEM>
-static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t smem, int tail_grid, cudaStream_t st)
+// Access-policy window that keeps the skip entries in L2 (persisting) while the
+// output streams through it.
+static bool g_persist_set[64];
+
+template <typename Kern>
+static cudaError_t launch_with_policy(Kern kern, const ScanParams &P, int grid, int threads, uint32_t smem,
+                                      cudaStream_t st, const TiledConfig &cfg, const DeviceProps &dp)
 {
-    auto kern = scan_kernel<PACKED, COMPACT, JW, FSMEM>;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3((unsigned)threads);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute attr[1];
+    lc.attrs = attr;
+    lc.numAttrs = 0;
+    const int64_t skip_bytes = P.t.n_states * 16;
+    if (cfg.l2_persist > 0 && dp.persist_l2_max > 0 && skip_bytes > 0) {
+        const int dev = dp.device;
+        if (dev >= 0 && dev < 64 && !g_persist_set[dev]) {
+            if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)dp.persist_l2_max) != cudaSuccess)
+                return cudaGetLastError();
+            g_persist_set[dev] = true;
+        }
+        int max_win = 0;
+        cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+        const int64_t win = std::min<int64_t>(skip_bytes, max_win);
+        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[0].val.accessPolicyWindow.base_ptr = (void *)P.t.skip;
+        attr[0].val.accessPolicyWindow.num_bytes = (size_t)win;
+        attr[0].val.accessPolicyWindow.hitRatio =
+            (float)std::min<double>(1.0, (double)dp.persist_l2_max / (double)std::max<int64_t>(win, 1));
+        attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        lc.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&lc, kern, P);
+}
+
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16>
+static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t smem, int tail_grid, cudaStream_t st,
+                         const TiledConfig &cfg, const DeviceProps &dp)
+{
+    auto kern = scan_kernel<PACKED, COMPACT, FSMEM, RANK16>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return PFAC_ERR_CUDA;
-    kern<<<grid, threads, smem, st>>>(P);
-    if (cudaGetLastError() != cudaSuccess) return PFAC_ERR_CUDA;
+    if (launch_with_policy(kern, P, grid, threads, smem, st, cfg, dp) != cudaSuccess) return PFAC_ERR_CUDA;
     tail_kernel<PACKED, COMPACT><<<tail_grid, 256, 0, st>>>(P);
     return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
 }
 
 template <bool PACKED, bool COMPACT>
-static int launch_scan_w(const ScanParams &P, bool wide, bool fsmem, int grid, int threads, uint32_t smem,
-                         int tail_grid, cudaStream_t st)
+static int launch_scan_w(const ScanParams &P, bool fsmem, bool rank16, int grid, int threads, uint32_t smem,
+                         int tail_grid, cudaStream_t st, const TiledConfig &cfg, const DeviceProps &dp)
 {
-    if (wide)
-        return fsmem ? launch_scan_t<PACKED, COMPACT, uint32_t, true>(P, grid, threads, smem, tail_grid, st)
-                     : launch_scan_t<PACKED, COMPACT, uint32_t, false>(P, grid, threads, smem, tail_grid, st);
-    return fsmem ? launch_scan_t<PACKED, COMPACT, uint16_t, true>(P, grid, threads, smem, tail_grid, st)
-                 : launch_scan_t<PACKED, COMPACT, uint16_t, false>(P, grid, threads, smem, tail_grid, st);
+    if (fsmem)
+        return rank16 ? launch_scan_t<PACKED, COMPACT, true, true>(P, grid, threads, smem, tail_grid, st, cfg, dp)
+                      : launch_scan_t<PACKED, COMPACT, true, false>(P, grid, threads, smem, tail_grid, st, cfg, dp);
+    return rank16 ? launch_scan_t<PACKED, COMPACT, false, true>(P, grid, threads, smem, tail_grid, st, cfg, dp)
+                  : launch_scan_t<PACKED, COMPACT, false, false>(P, grid, threads, smem, tail_grid, st, cfg, dp);
 }
 
 int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n, int32_t *out, int64_t *c_off,
@@ -806,14 +846,12 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     if (n == 0) return PFAC_OK;
     const int C = consumers_of(cfg);
     const int S = stages_of(cfg, packed);
-    if (!t.nodes || !t.jump || !t.filter || t.jump_k < 1 || t.jump_k > kMaxJumpK || t.filter_b < 1 ||
-        t.filter_b > kMaxFilterB || C < 1 || (cfg.threads & 31) || cfg.threads > 1024 || S < 2 || S > kMaxStages ||
-        !scratch.items || !scratch.count)
+    if (!t.skip || !t.filter || !t.rank || !t.dense || t.filter_b < 1 || t.filter_b > kMaxFilterB || C < 1 ||
+        (cfg.threads & 31) || cfg.threads > 1024 || S < 2 || S > kMaxStages || !scratch.items || !scratch.count)
         return PFAC_ERR_INVALID_ARG;
     const SmemPlan pl = plan_smem(t, cfg, packed, dp);
     if (pl.total < 0 || pl.total > dp.smem_optin) return PFAC_ERR_UNSUPPORTED;
-    const int32_t win_len = pl.win_len;
-    const ScanLayout L = scan_layout(C, S, pl.filter_bytes, pl.jump_bytes, packed, (uint32_t)win_len);
+    const ScanLayout L = scan_layout(C, S, pl.filter_bytes, pl.rank_bytes, packed);
     if (cudaMemsetAsync(scratch.count, 0, sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     ScanParams P{};
     P.t = t;
@@ -833,26 +871,22 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     P.consumers = C;
     P.stages = S;
     P.stage_units = L.stage_units;
-    // deferred once this many bases are consumed (the register window holds 32)
-    P.qmax = std::min(32, std::max(t.jump_k, t.filter_b) + 1 + (cfg.step_cap > 0 ? cfg.step_cap : 8));
-    P.jump_smem = pl.jump_bytes > 0;
-    P.win_len = (uint32_t)win_len;
+    P.rank_smem = pl.rank_bytes > 0;
     P.off_filter = L.off_filter;
-    P.off_jump = L.off_jump;
-    P.off_win = L.off_win;
+    P.off_rank = L.off_rank;
     P.off_stage = L.off_stage;
     P.stage_bytes = L.stage_bytes;
     P.timeout_ns = cfg.timeout_ns > 0 ? cfg.timeout_ns : 2000000000LL;
     const int64_t grid64 = std::min<int64_t>(P.n_tiles, (int64_t)dp.num_sms * std::max(1, cfg.ctas_per_sm));
     const int grid = (int)std::max<int64_t>(1, grid64);
     const int tail_grid = dp.num_sms * 4;
-    const bool wide = t.jump_wide != 0;
     const bool fsmem = pl.filter_bytes > 0;
+    const bool rank16 = !t.rank_wide;
     if (packed)
-        return compact ? launch_scan_w<true, true>(P, wide, fsmem, grid, cfg.threads, L.total, tail_grid, st)
-                       : launch_scan_w<true, false>(P, wide, fsmem, grid, cfg.threads, L.total, tail_grid, st);
-    return compact ? launch_scan_w<false, true>(P, wide, fsmem, grid, cfg.threads, L.total, tail_grid, st)
-                   : launch_scan_w<false, false>(P, wide, fsmem, grid, cfg.threads, L.total, tail_grid, st);
+        return compact ? launch_scan_w<true, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp)
+                       : launch_scan_w<true, false>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp);
+    return compact ? launch_scan_w<false, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp)
+                   : launch_scan_w<false, false>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp);
 }
 
 size_t defer_item_bytes() { return sizeof(DeferItem); }

@@ -11,10 +11,11 @@
 // is a contiguous range of ids and the children of one state are consecutive. The
 // shallow levels that every walk visits become a short prefix of the table.
 //
-// Step 3: the table is encoded three ways for the device (see pfac_internal.h):
-// 16-byte rows (4 x int32, one per base, bit 31 = target is terminal), 4-byte compact
-// node words, and a k-mer jump table that replaces the first k steps of a walk with
-// one lookup.
+// Step 3: the table is encoded for the device (see pfac_internal.h): 16-byte rows
+// (4 x int32, one per base, bit 31 = target is terminal, the paper's 4-column layout),
+// per-state skip entries that compress chains of single-child edges (up to 16 bases
+// compared at once), and a prefix filter over b-mers with a rank index into skip
+// entries for the states of depth b. All of them describe the same trie exactly.
 #include <stdint.h>
 #include <string.h>
 
@@ -45,21 +46,11 @@ constexpr int64_t kMaxStates = int64_t(0x7FFFFFFF);
 
 }  // namespace
 
-int32_t auto_jump_k(const std::vector<int64_t> &level, int32_t max_len)
-{
-    // The jump table serves the walks that pass the prefix filter of order 10: those
-    // are still going at depth 10, so a jump over the same 10 bases takes them there
-    // in one lookup (a 16-bit table of 2 MB that stays in L2 when depth 10 has at most
-    // 65533 states, else 32-bit). Tries shallower than that jump to their deepest level.
-    (void)level;
-    return std::max(1, std::min(10, max_len));
-}
-
 int build_host_tables(const char *const *patterns, const int32_t *lengths, int32_t n,
-                      int32_t jump_k_opt, int32_t filter_b_opt, HostTables *out)
+                      int32_t filter_b_opt, HostTables *out)
 {
     if (n <= 0 || !patterns || !lengths || !out) return PFAC_ERR_INVALID_ARG;
-    if (jump_k_opt > kMaxJumpK || filter_b_opt > kMaxFilterB) return PFAC_ERR_INVALID_ARG;
+    if (filter_b_opt > kMaxFilterB) return PFAC_ERR_INVALID_ARG;
     try {
         // ---- validate ----------------------------------------------------------
         int64_t total = 0;
@@ -157,70 +148,55 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
         std::vector<int32_t>().swap(renum);
         std::vector<int32_t>().swap(depth_of);
 
-        // ---- step 3b: compact node words -----------------------------------------
+        // ---- step 3b: skip entries ----------------------------------------------
         if (n_states < kMaxNodeStates) {
-            T.nodes.assign((size_t)n_states, 0);
+            std::vector<uint32_t> node((size_t)n_states, 0);
+            std::vector<uint8_t> nchild((size_t)n_states, 0), onlyc((size_t)n_states, 0);
             for (int64_t s = 0; s < n_states; s++) {
                 uint32_t mask = 0, first = 0;
                 for (int c = 3; c >= 0; c--) {
                     uint32_t e = (uint32_t)T.rows[(size_t)(4 * s + c)];
-                    if (e) { mask |= 1u << c; first = e & 0x7FFFFFFFu; }
+                    if (e) { mask |= 1u << c; first = e & 0x7FFFFFFFu; onlyc[(size_t)s] = (uint8_t)c; }
                 }
+                nchild[(size_t)s] = (uint8_t)__builtin_popcount(mask);
                 uint32_t w = mask | (first << kNodeFirstShift);
                 if (T.out_id[(size_t)s]) w |= kNodeTermBit;
-                T.nodes[(size_t)s] = w;
+                node[(size_t)s] = w;
+            }
+            T.skip.assign((size_t)n_states * 4, 0u);
+            for (int64_t s = 0; s < n_states; s++) {
+                uint32_t label = 0, len = 0;
+                int64_t cur = s;
+                while ((int)len < kSkipMaxLen && nchild[(size_t)cur] == 1) {
+                    const int c = onlyc[(size_t)cur];
+                    label |= (uint32_t)c << (2 * len);
+                    len++;
+                    cur = (int64_t)((uint32_t)T.rows[(size_t)(4 * cur + c)] & 0x7FFFFFFFu);
+                    if (T.out_id[(size_t)cur]) break;
+                }
+                uint32_t y = len;
+                if (T.out_id[(size_t)s]) y |= kSkipSelfTerm;
+                if (len && T.out_id[(size_t)cur]) y |= kSkipTargetTerm;
+                uint32_t *e = &T.skip[(size_t)(4 * s)];
+                e[0] = label;
+                e[1] = y;
+                e[2] = len ? (uint32_t)cur : 0u;
+                e[3] = node[(size_t)s];
             }
         }
 
-        // ---- step 3c: k-mer jump table ------------------------------------------
-        int32_t k = jump_k_opt == 0 ? auto_jump_k(T.level, max_len) : (jump_k_opt < 0 ? 0 : jump_k_opt);
-        if (k > max_len) k = max_len;
-        if (k > 0 && !T.nodes.empty()) {
-            T.jump_k = k;
-            const int64_t lk = T.level[(size_t)k];
-            const int64_t nk = T.level[(size_t)k + 1] - lk;
-            T.jump_wide = nk > kJump16MaxLevel;
-            const size_t E = (size_t)1 << (2 * k);
-            std::vector<uint32_t> J(E, kJumpDead);
-            // Depth-first over the trie down to depth k. A prefix of d symbols whose walk
-            // stops at symbol d fixes the entry of every k-mer that starts with it: the
-            // indices congruent to the prefix code modulo 4^(d+1).
-            struct Frame { int32_t s; int32_t d; uint32_t code; bool term; };
-            std::vector<Frame> stack;
-            stack.push_back({0, 0, 0u, false});
-            while (!stack.empty()) {
-                Frame f = stack.back();
-                stack.pop_back();
-                if (f.d == k) {
-                    J[f.code] = f.term ? kJumpSpecial : (uint32_t)(kJumpFirst + (f.s - lk));
-                    continue;
-                }
-                for (int c = 0; c < 4; c++) {
-                    const uint32_t code = f.code | ((uint32_t)c << (2 * f.d));
-                    const uint32_t e = (uint32_t)T.rows[(size_t)(4 * (int64_t)f.s + c)];
-                    if (e) {
-                        stack.push_back({(int32_t)(e & 0x7FFFFFFFu), f.d + 1, code, f.term || (e & 0x80000000u)});
-                    } else {
-                        // the walk over the prefix ends here: an answer from the prefix
-                        // needs the full walk, otherwise the answer is 0
-                        const uint32_t v = f.term ? kJumpSpecial : kJumpDead;
-                        const size_t stride = (size_t)1 << (2 * (f.d + 1));
-                        for (size_t idx = code; idx < E; idx += stride) J[idx] = v;
-                    }
-                }
-            }
-            if (T.jump_wide) T.jump32.swap(J);
-            else T.jump16.assign(J.begin(), J.end());
-        }
-
-        // ---- step 3d: prefix filter ----------------------------------------------
-        // Same depth-first enumeration to depth b: a b-mer's bit is set when its walk
-        // is still going at depth b, or when a pattern ends on the walk before it stops.
+        // ---- step 3c: prefix filter, rank index, dense entries ------------------------
+        // Depth-first over the trie down to depth b. A b-mer's bit is set when its walk
+        // is still going at depth b (its dense entry is that state's skip entry), or when
+        // a pattern ends on the walk before it stops (special entry). A prefix of d
+        // symbols whose walk stops at symbol d fixes every b-mer that starts with it: the
+        // indices congruent to the prefix code modulo 4^(d+1).
         const int32_t b = filter_b_opt == 0 ? 10 : (filter_b_opt < 0 ? 0 : filter_b_opt);
-        if (b > 0) {
+        if (b > 0 && !T.skip.empty()) {
             T.filter_b = b;
             const size_t E = (size_t)1 << (2 * b);
-            T.filter.assign(E / 32 + (E < 32 ? 1 : 0), 0u);
+            const uint32_t kNone = 0xFFFFFFFFu, kSpecialVal = 0xFFFFFFFEu;
+            std::vector<uint32_t> val(E, kNone);      // state reached at depth b, or special
             struct Frame { int32_t s; int32_t d; uint32_t code; bool term; };
             std::vector<Frame> stack;
             stack.push_back({0, 0, 0u, false});
@@ -228,7 +204,7 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
                 Frame f = stack.back();
                 stack.pop_back();
                 if (f.d == b) {
-                    T.filter[f.code >> 5] |= 1u << (f.code & 31);
+                    val[f.code] = f.term ? kSpecialVal : (uint32_t)f.s;
                     continue;
                 }
                 for (int c = 0; c < 4; c++) {
@@ -238,10 +214,32 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
                         stack.push_back({(int32_t)(e & 0x7FFFFFFFu), f.d + 1, code, f.term || (e & 0x80000000u)});
                     } else if (f.term) {
                         const size_t stride = (size_t)1 << (2 * (f.d + 1));
-                        for (size_t idx = code; idx < E; idx += stride) T.filter[idx >> 5] |= 1u << (idx & 31);
+                        for (size_t idx = code; idx < E; idx += stride) val[idx] = kSpecialVal;
                     }
                 }
             }
+            const size_t words = E >= 32 ? E / 32 : 1;
+            T.filter.assign(words, 0u);
+            std::vector<uint32_t> rank(words, 0u);
+            uint64_t count = 0;
+            for (size_t w = 0; w < words; w++) {
+                rank[w] = (uint32_t)count;
+                for (size_t i = 0; i < 32 && w * 32 + i < E; i++) {
+                    const uint32_t v = val[w * 32 + i];
+                    if (v == kNone) continue;
+                    T.filter[w] |= 1u << i;
+                    count++;
+                    if (v == kSpecialVal) {
+                        T.dense.insert(T.dense.end(), {0u, kSkipSpecial, 0u, 0u});
+                    } else {
+                        const uint32_t *e = &T.skip[(size_t)(4 * (int64_t)v)];
+                        T.dense.insert(T.dense.end(), {e[0], e[1], e[2], e[3]});
+                    }
+                }
+            }
+            T.rank_wide = count > 65535;
+            if (T.rank_wide) T.rank32.swap(rank);
+            else T.rank16.assign(rank.begin(), rank.end());
         }
         return PFAC_OK;
     } catch (const std::bad_alloc &) {

@@ -60,11 +60,9 @@ def genome_small():
     dict(kernel=2, threads=96, stages=2),
     dict(kernel=2, threads=512, stages=8),
     dict(kernel=2, threads=1024, stages=3),
-    dict(kernel=2, smem_table_bytes=-1),
-    dict(kernel=2, smem_table_bytes=4096),
+    dict(kernel=2, rank_in_smem=-1),
+    dict(kernel=2, l2_persist=1),
     dict(kernel=2, ctas_per_sm=2, threads=512),
-    dict(kernel=2, step_cap=1),
-    dict(kernel=2, step_cap=24),
 ], ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
 def test_genome_configs(genome_small, cfg, packed):
     w, want = genome_small
@@ -82,18 +80,17 @@ def test_deferred_list_overflow(genome_small, monkeypatch):
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         t = b.Table((w.blob, w.offsets))
-        got = gpu_match_packed(t, w.text, kernel=2, step_cap=1)
+        got = gpu_match_packed(t, w.text, kernel=2)
     assert np.array_equal(got, want), first_diff(got, want)
 
 
-@pytest.mark.parametrize("jump_k,filter_b", [(-1, 0), (0, -1), (1, 12), (3, 1), (5, 5), (7, 10), (8, 9),
-                                             (10, 4), (12, 11), (2, 10)])
-def test_shortcut_orders(genome_small, jump_k, filter_b):
-    """Jump-table and prefix-filter orders, including a filter shorter than the jump,
-    tables too large for shared memory, and tables without one of them (kernel 1)."""
+@pytest.mark.parametrize("filter_b", [-1, 1, 3, 5, 8, 9, 10, 11, 12])
+def test_filter_orders(genome_small, filter_b):
+    """Prefix-filter orders, including filters too large for shared memory and a
+    table without a filter (kernel 1)."""
     w, want = genome_small
-    t = b.Table((w.blob, w.offsets), jump_k=jump_k, filter_b=filter_b)
-    assert t.info["jump_k"] == (0 if jump_k < 0 else (jump_k or t.info["jump_k"]))
+    t = b.Table((w.blob, w.offsets), filter_b=filter_b)
+    assert t.info["filter_b"] == max(filter_b, 0)
     got = gpu_match_packed(t, w.text)
     assert np.array_equal(got, want), first_diff(got, want)
     got = gpu_match(t, w.text)
@@ -168,7 +165,7 @@ def test_matches_across_tile_edges(threads):
 
 def test_random_small_sets_both_kernels():
     """Many tiny random cases (alphabet with N and newline, short patterns so that
-    terminals fall inside the jump prefix)."""
+    terminals fall inside the filter prefix)."""
     import random
 
     import pins
@@ -179,11 +176,11 @@ def test_random_small_sets_both_kernels():
             continue
         a = np.frombuffer(text, dtype=np.uint8)
         want = ref(a, pats)
-        for jk, fb in ((0, 0), (3, 2), (6, 9)):
-            t = b.Table(pats, jump_k=jk, filter_b=fb)
+        for fb in (0, 2, 9):
+            t = b.Table(pats, filter_b=fb)
             for kernel in (1, 2):
                 got = gpu_match(t, a, kernel=kernel, threads=64)
-                assert np.array_equal(got, want), (text, pats, jk, kernel, first_diff(got, want))
+                assert np.array_equal(got, want), (text, pats, fb, kernel, first_diff(got, want))
 
 
 def test_unaligned_buffers_fall_back():

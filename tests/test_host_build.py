@@ -82,62 +82,81 @@ def test_random_sets(seed):
 def test_small_workload_set():
     w = datagen.small_scan(n_bases=100_000)
     info = check_same_trie((w.blob, w.offsets))
-    assert info["has_nodes"] == 1 and info["jump_k"] == 10 and info["filter_b"] == 10
+    assert info["has_skip"] == 1 and info["filter_b"] == 10
 
 
-def shortcut_reference(go, term, order_new, k, b):
-    """Jump entries and filter bits defined by walking the oracle's insertion-order trie
-    over every k-mer / b-mer (base j of a k-mer in bits 2j..2j+1)."""
-    def walk(code, length):
-        s, term_seen = 0, False
-        for j in range(length):
-            c = (code >> (2 * j)) & 3
-            nxt = int(go[s, c])
-            if nxt == 0:
-                return None, term_seen
-            s = nxt
-            term_seen = term_seen or bool(term[s])
-        return s, term_seen
-
-    jump = []
-    for code in range(1 << (2 * k)):
-        s, t = walk(code, k)
-        if t:
-            jump.append(1)
-        elif s is None:
-            jump.append(0)
-        else:
-            jump.append(("state", int(order_new[s])))
-    bits = []
+def reference_shortcuts(go, term, b):
+    """Filter bits and the depth-b state of each b-mer (None for a clear bit, "special"
+    when a pattern ends within it), by walking the oracle's insertion-order trie."""
+    bits, state = [], []
     for code in range(1 << (2 * b)):
-        s, t = walk(code, b)
-        bits.append(1 if (t or s is not None) else 0)
-    return jump, bits
+        s, seen = 0, False
+        for j in range(b):
+            nxt = int(go[s, (code >> (2 * j)) & 3])
+            if nxt == 0:
+                s = None
+                break
+            s = nxt
+            seen = seen or bool(term[s])
+        on = seen or s is not None
+        bits.append(1 if on else 0)
+        state.append(("special" if seen else s) if on else None)
+    return bits, state
 
 
-@pytest.mark.parametrize("seed,k,b", [(1, 3, 4), (2, 4, 3), (3, 5, 5), (4, 2, 6), (5, 1, 1)])
-def test_jump_and_filter_definition(seed, k, b):
+def check_skip_entry(e, s_old, go, term, new):
+    """A skip entry of (breadth-first) state new[s_old] follows the single-child chain
+    of the oracle's trie below s_old."""
+    label, meta, last, node = (int(v) for v in e)
+    L = meta & 31
+    assert bool(meta & (1 << 8)) == bool(term[s_old])
+    children = [c for c in range(4) if go[s_old, c]]
+    mask = sum(1 << c for c in children)
+    assert node & 15 == mask and bool(node & 16) == bool(term[s_old])
+    if children:
+        assert node >> 5 == new[int(go[s_old, children[0]])]
+    cur = s_old
+    for i in range(L):
+        kids = [c for c in range(4) if go[cur, c]]
+        assert len(kids) == 1, "a chain only follows single-child states"
+        assert (label >> (2 * i)) & 3 == kids[0]
+        cur = int(go[cur, kids[0]])
+        if i < L - 1:
+            assert not term[cur], "no terminal strictly inside a chain"
+    if L:
+        assert last == new[cur] and bool(meta & (1 << 10)) == bool(term[cur])
+        stop = term[cur] or L == 16 or len([c for c in range(4) if go[cur, c]]) != 1
+        assert stop, "a chain stops only at 16 bases, a terminal, or a branch or leaf"
+    else:
+        assert len(children) != 1
+
+
+@pytest.mark.parametrize("seed,b", [(1, 4), (2, 3), (3, 5), (4, 6), (5, 1), (6, 2)])
+def test_skip_filter_dense_definition(seed, b):
     rng = datagen.rng_for(seed)
     text = datagen.iid_text(3000, rng)
-    blob, offs = datagen.pattern_set(text, rng, 60, (1, 9), 0.6)
+    blob, offs = datagen.pattern_set(text, rng, 60, (1, 30), 0.6)
     go, term = oracle.Trie((blob, offs)).export()
     order = bfs_relabel(go)
     new = np.empty(go.shape[0], dtype=np.int64)
     new[np.array(order)] = np.arange(go.shape[0])
-    h = b_.pfac_build((blob, offs), host_only=True, jump_k=k, filter_b=b)
+    h = b_.pfac_build((blob, offs), host_only=True, filter_b=b)
     try:
-        rows, out_id, level = b_.pfac_export(h)
-        jump, filt = b_.pfac_export_shortcuts(h)
+        skip, filt, dense = b_.pfac_export_shortcuts(h)
         info = b_.pfac_info_ex(h)
     finally:
         b_.pfac_destroy(h)
-    kk = info["jump_k"]
-    ref_jump, ref_bits = shortcut_reference(go, term, new, kk, b)
-    for code, want in enumerate(ref_jump):
-        v = int(jump[code])
-        if isinstance(want, tuple):
-            assert v >= 2 and level[kk] + v - 2 == want[1], (code, v, want)
+    assert info["filter_b"] == b and skip.shape[0] == go.shape[0]
+    for s_old in range(go.shape[0]):
+        check_skip_entry(skip[new[s_old]], s_old, go, term, new)
+    bits, state = reference_shortcuts(go, term, b)
+    got = [(int(filt[w >> 5]) >> (w & 31)) & 1 for w in range(1 << (2 * b))]
+    assert got == bits
+    on = [st for st in state if st is not None]
+    assert dense.shape[0] == len(on) == info["filter_set"]
+    for r, st in enumerate(on):
+        if st == "special":
+            assert dense[r, 1] & (1 << 9)
         else:
-            assert v == want, (code, v, want)
-    got_bits = [(int(filt[w >> 5]) >> (w & 31)) & 1 for w in range(1 << (2 * b))]
-    assert got_bits == ref_bits
+            assert not dense[r, 1] & (1 << 9)
+            assert np.array_equal(dense[r], skip[new[st]])
