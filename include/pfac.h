@@ -157,7 +157,7 @@ typedef struct {
                                 skip-entry walks for the offsets the filter passes (needs
                                 the filter and skip entries) */
     int32_t threads;         /* kernel 2: threads per CTA, 64..1024, multiple of 32: one
-                                producer warp plus consumer warps; a tile is 512 bases
+                                producer warp plus consumer warps; a tile is 1024 bases
                                 per consumer warp */
     int32_t ctas_per_sm;     /* kernel 2: resident CTAs per SM of the persistent grid */
     int32_t stages;          /* kernel 2: text stages in the ring, 2..8 */
@@ -165,6 +165,8 @@ typedef struct {
                                 memory, 0 = in shared memory when it fits */
     int32_t l2_persist;      /* 1 = keep the skip entries in L2 with an access-policy
                                 window, -1 = never, 0 = automatic */
+    int32_t walk_loads;      /* kernel 2: dependent table loads a walk may take before it
+                                is handed to the tail kernel (0 = 2) */
 } pfac_config;
 
 /* Set (cfg != NULL) or reset (cfg == NULL) the launch configuration of a handle.

@@ -125,6 +125,7 @@ pfac::TiledConfig tiled_config(const pfac_config &c)
     t.ctas_per_sm = c.ctas_per_sm;
     t.stages = c.stages;
     t.smem_table_bytes = c.rank_in_smem < 0 ? -1 : 0;
+    t.walk_loads = c.walk_loads;
     t.l2_persist = c.l2_persist;
     t.timeout_ns = 2000000000LL;
     return t;

@@ -280,11 +280,11 @@ int launch_walk_rows_any(const DeviceTable &t, const void *text, bool packed, in
 // ---------------------------------------------------------------------------
 // Kernel 2: warp-specialised pipeline.
 //
-//   * one producer warp stages the text of each tile (512 bases per consumer warp)
+//   * one producer warp stages the text of each tile (1024 bases per consumer warp)
 //     into an S-stage shared-memory ring with TMA bulk copies; full/empty mbarriers
 //     hand stages to the consumer warps and back, with bounded waits;
-//   * each consumer lane owns 16 consecutive offsets and reads one 48-base window
-//     (three packed words) from the stage. A fully unrolled, branch-free block tests
+//   * each consumer lane owns 32 consecutive offsets and reads one 64-base window
+//     (four packed words) from the stage. A fully unrolled, branch-free block tests
 //     the prefix filter for every offset (one shared-memory load): a clear bit means
 //     the walk ends before depth b with no pattern on the way, answer 0;
 //   * the offsets whose bit is set (a few percent) are spread over the warp by a
@@ -292,8 +292,10 @@ int launch_walk_rows_any(const DeviceTable &t, const void *text, bool packed, in
 //     dense skip entry, the state of depth b, and walks on through skip entries
 //     (chains of single-child edges compared up to 16 bases at a time) inside the
 //     register window;
-//   * a walk that reaches the end of the window while the text goes on is appended to
-//     a deferred list in global scratch memory and finished by a tail kernel.
+//   * a walk that needs more than a couple of dependent table loads, or reaches the end
+//     of the window while the text goes on, is appended to a deferred list in global
+//     scratch memory and finished by a tail kernel, so rounds are never held up by the
+//     few long walks (true hits along long patterns).
 // Results: zeros go out as 128-bit stores (evict-first), matches as single stores.
 // ---------------------------------------------------------------------------
 
@@ -324,6 +326,7 @@ struct ScanParams {
     int32_t stages;
     int32_t stage_units;         // packed words or ASCII bytes per stage
     int32_t rank_smem;           // rank index copied into shared memory
+    int32_t walk_loads;          // dependent table loads a walk may take before it is deferred
     uint32_t off_filter, off_rank, off_stage, stage_bytes;
     int64_t timeout_ns;
 };
@@ -439,7 +442,7 @@ __device__ __forceinline__ void emit_match(const ScanParams &P, int64_t gp, int3
     }
 }
 
-// Mask of positions j (bit j) such that bits j .. j+w-1 of `bad` are all clear.
+// Mask of positions j < 32 (bit j) such that bits j .. j+w-1 of `bad` are all clear.
 __device__ __forceinline__ uint32_t clear_runs(uint64_t bad, int w)
 {
     uint64_t t = bad;
@@ -449,15 +452,16 @@ __device__ __forceinline__ uint32_t clear_runs(uint64_t bad, int w)
         have *= 2;
     }
     if (have < w) t |= t >> (w - have);
-    return (uint32_t)(~t) & 0xFFFFu;
+    return (uint32_t)(~t);
 }
 
-// Sixteen bases of a lane's 48-base window from position p (0 <= p < 48); bases past
+// Sixteen bases of a lane's 64-base window from position p (0 <= p < 64); bases past
 // the window read as 0.
-__device__ __forceinline__ uint32_t window_at(uint32_t x0, uint32_t x1, uint32_t x2, int p)
+__device__ __forceinline__ uint32_t window_at(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3, int p)
 {
-    const uint32_t lo = p < 16 ? x0 : (p < 32 ? x1 : x2);
-    const uint32_t hi = p < 16 ? x1 : (p < 32 ? x2 : 0u);
+    const int w = p >> 4;
+    const uint32_t lo = w == 0 ? x0 : (w == 1 ? x1 : (w == 2 ? x2 : x3));
+    const uint32_t hi = w == 0 ? x1 : (w == 1 ? x2 : (w == 2 ? x3 : 0u));
     return __funnelshift_r(lo, hi, (uint32_t)(p & 15) * 2);
 }
 
@@ -543,40 +547,44 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             return;
         }
         const uint8_t *stage = stage0 + (size_t)st * P.stage_bytes;
-        const int p_rel = warp * 512 + lane * 16;
+        const int p_rel = warp * 1024 + lane * 32;
         const int64_t gp0 = t * (int64_t)P.tile + p_rel;
-        // 48-base window: packed words and a mask of bases that cannot be read (past
+        // 64-base window: packed words and a mask of bases that cannot be read (past
         // the text end, or ASCII bytes outside ACGT).
-        uint32_t x0 = 0, x1 = 0, x2 = 0;
+        uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
         const int64_t rem = n - gp0;
-        uint64_t bad = rem < 48 ? (rem > 0 ? (~0ull << rem) : ~0ull) : 0ull;
+        uint64_t bad = rem < 64 ? (rem > 0 ? (~0ull << rem) : ~0ull) : 0ull;
         if (rem > 0) {
             if (PACKED) {
                 const uint32_t *w = reinterpret_cast<const uint32_t *>(stage) + (p_rel >> 4);
-                x0 = w[0];
-                x1 = w[1];
-                x2 = w[2];
+                const uint2 a = *reinterpret_cast<const uint2 *>(w);
+                const uint2 c = *reinterpret_cast<const uint2 *>(w + 2);
+                x0 = a.x;
+                x1 = a.y;
+                x2 = c.x;
+                x3 = c.y;
             } else {
                 const uint4 *r = reinterpret_cast<const uint4 *>(stage + p_rel);
-                uint32_t b0, b1, b2;
+                uint32_t b0, b1, b2, b3;
                 x0 = pack16(r[0], &b0);
                 x1 = pack16(r[1], &b1);
                 x2 = pack16(r[2], &b2);
-                bad |= (uint64_t)b0 | ((uint64_t)b1 << 16) | ((uint64_t)b2 << 32);
+                x3 = pack16(r[3], &b3);
+                bad |= (uint64_t)b0 | ((uint64_t)b1 << 16) | ((uint64_t)b2 << 32) | ((uint64_t)b3 << 48);
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&empty[st]));   // this warp is done with the stage
-        bad &= 0xFFFFFFFFFFFFull;
-        const uint32_t valid = rem >= 16 ? 0xFFFFu : (rem > 0 ? ((1u << rem) - 1u) : 0u);
+        const uint32_t valid = rem >= 32 ? 0xFFFFFFFFu : (rem > 0 ? ((1u << rem) - 1u) : 0u);
         const uint32_t fast = clear_runs(bad, B) & valid;   // the b-mer is readable
 
         // Every offset: one filter bit for the b bases starting there. A clear bit
         // means the walk ends before depth b with no pattern on the way: answer 0.
         uint32_t pend = 0;
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
-            const uint32_t kmer = __funnelshift_r(x0, x1, 2 * j) & bmask;   // bases j .. j+b-1
+        for (int j = 0; j < 32; j++) {
+            const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
+            const uint32_t kmer = win & bmask;   // bases j .. j+b-1
             const uint32_t word = FSMEM ? sf[kmer >> 5] : __ldg(T.filter + (kmer >> 5));
             pend |= ((word >> (kmer & 31u)) & 1u) << j;
         }
@@ -584,15 +592,13 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
         pend |= valid & ~fast;     // these walk from the root
 
         if (!COMPACT && valid) {
-            if (valid == 0xFFFFu) {
+            if (valid == 0xFFFFFFFFu) {
                 int32_t *o = P.out + gp0;
                 const int4 z = make_int4(0, 0, 0, 0);
-                st_global_v4_hint(o + 0, z, pol);
-                st_global_v4_hint(o + 4, z, pol);
-                st_global_v4_hint(o + 8, z, pol);
-                st_global_v4_hint(o + 12, z, pol);
+#pragma unroll
+                for (int v = 0; v < 8; v++) st_global_v4_hint(o + 4 * v, z, pol);
             } else {
-                for (int j = 0; j < 16; j++)
+                for (int j = 0; j < 32; j++)
                     if ((valid >> j) & 1u) P.out[gp0 + j] = 0;
             }
         }
@@ -625,25 +631,26 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             const uint32_t ox0 = __shfl_sync(0xFFFFFFFFu, x0, owner);
             const uint32_t ox1 = __shfl_sync(0xFFFFFFFFu, x1, owner);
             const uint32_t ox2 = __shfl_sync(0xFFFFFFFFu, x2, owner);
+            const uint32_t ox3 = __shfl_sync(0xFFFFFFFFu, x3, owner);
             const uint32_t obad_lo = __shfl_sync(0xFFFFFFFFu, (uint32_t)bad, owner);
             const uint32_t obad_hi = __shfl_sync(0xFFFFFFFFu, (uint32_t)(bad >> 32), owner);
             if (r >= total) continue;
             // the (r - oe)-th set bit of the owner's mask (r - oe < popcount by construction)
             uint32_t m = om;
             for (uint32_t i = r - oe; i > 0; i--) m &= m - 1u;
-            const int j = (__ffs(m) - 1) & 15;
-            const int64_t gp = t * (int64_t)P.tile + warp * 512 + owner * 16 + j;
+            const int j = (__ffs(m) - 1) & 31;
+            const int64_t gp = t * (int64_t)P.tile + warp * 1024 + owner * 32 + j;
             const uint64_t badj = (((uint64_t)obad_hi << 32) | obad_lo) >> j;
             // bases readable from the window; `ends` when the text (or the run of ACGT
             // bytes) really stops there rather than the window
-            const int wlim = badj ? __ffsll((long long)badj) - 1 : 48 - j;
+            const int wlim = badj ? __ffsll((long long)badj) - 1 : 64 - j;
             const bool ends = badj != 0;
             uint32_t s = 0, best = 0;
             int q = 0;
             uint4 e;
             bool from_root = true;
             if ((ofast >> j) & 1u) {
-                const uint32_t kmer = window_at(ox0, ox1, ox2, j) & bmask;
+                const uint32_t kmer = window_at(ox0, ox1, ox2, ox3, j) & bmask;
                 const uint32_t widx = kmer >> 5;
                 const uint32_t word = FSMEM ? sf[widx] : __ldg(T.filter + widx);
                 const uint32_t base_rank = P.rank_smem ? (uint32_t)srank[widx]
@@ -656,9 +663,10 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                 }
             }
             if (from_root) e = __ldg(T.skip);
-            // walk on through skip entries inside the window
+            // walk on through skip entries inside the window, with at most walk_loads
+            // dependent table loads; a longer walk is deferred
             bool defer = false;
-            for (;;) {
+            for (int loads = 1;; loads++) {
                 if (e.y & kSkipSelfTerm) best = s;
                 const uint32_t L = e.y & kSkipLenMask;
                 const int need = L ? (int)L : 1;
@@ -666,7 +674,7 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                     defer = !ends;     // the window ran out before the text did
                     break;
                 }
-                const uint32_t win = window_at(ox0, ox1, ox2, j + q);
+                const uint32_t win = window_at(ox0, ox1, ox2, ox3, j + q);
                 if (L) {
                     if ((win ^ e.x) & base_mask(L)) break;
                     q += (int)L;
@@ -677,6 +685,10 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                     if (!((e.w >> c) & 1u)) break;
                     s = (e.w >> kNodeFirstShift) + __popc(e.w & ((1u << c) - 1u));
                     q++;
+                }
+                if (loads >= P.walk_loads) {
+                    defer = true;      // the tail kernel takes it from state s
+                    break;
                 }
                 e = __ldg(T.skip + s);
             }
@@ -724,14 +736,14 @@ static ScanLayout scan_layout(int consumers, int stages, int64_t filter_smem_byt
                               bool packed)
 {
     ScanLayout L{};
-    const int64_t tile = 512LL * consumers;
+    const int64_t tile = 1024LL * consumers;
     uint64_t off = kBarBytes;
     L.off_filter = (uint32_t)off;
     off += align128((uint64_t)filter_smem_bytes);
     L.off_rank = (uint32_t)off;
     off += align128((uint64_t)rank_smem_bytes);
-    // a lane reads 48 bases from its first offset: 2 words (32 bytes) past the tile
-    L.stage_units = packed ? (int32_t)(tile / 16 + 4) : (int32_t)(tile + 48);
+    // a lane reads 64 bases from its first offset: 2 words (32 bytes) past the tile
+    L.stage_units = packed ? (int32_t)(tile / 16 + 4) : (int32_t)(tile + 64);
     L.stage_bytes = align128((uint64_t)L.stage_units * (packed ? 4 : 1));
     L.off_stage = (uint32_t)off;
     off += (uint64_t)L.stage_bytes * stages;
@@ -866,12 +878,13 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     P.defer = (DeferItem *)scratch.items;
     P.defer_cap = scratch.cap;
     P.defer_count = scratch.count;
-    P.tile = 512 * C;
+    P.tile = 1024 * C;
     P.n_tiles = (n + P.tile - 1) / P.tile;
     P.consumers = C;
     P.stages = S;
     P.stage_units = L.stage_units;
     P.rank_smem = pl.rank_bytes > 0;
+    P.walk_loads = cfg.walk_loads > 0 ? cfg.walk_loads : 2;
     P.off_filter = L.off_filter;
     P.off_rank = L.off_rank;
     P.off_stage = L.off_stage;

@@ -63,6 +63,8 @@ def genome_small():
     dict(kernel=2, rank_in_smem=-1),
     dict(kernel=2, l2_persist=1),
     dict(kernel=2, ctas_per_sm=2, threads=512),
+    dict(kernel=2, walk_loads=1),
+    dict(kernel=2, walk_loads=64),
 ], ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
 def test_genome_configs(genome_small, cfg, packed):
     w, want = genome_small
@@ -80,7 +82,7 @@ def test_deferred_list_overflow(genome_small, monkeypatch):
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         t = b.Table((w.blob, w.offsets))
-        got = gpu_match_packed(t, w.text, kernel=2)
+        got = gpu_match_packed(t, w.text, kernel=2, walk_loads=1)
     assert np.array_equal(got, want), first_diff(got, want)
 
 
@@ -138,20 +140,20 @@ def test_empty_text():
 @pytest.mark.parametrize("threads", [64, 128, 1024])
 def test_matches_across_tile_edges(threads):
     """Long patterns planted so they start just before, at and after tile edges (a tile
-    is 512 bases per consumer warp) and end exactly at a tile edge, at a 16-base lane
-    batch edge, at a 48-base window edge, and at the text end."""
-    tile = 512 * (threads // 32 - 1)
+    is 1024 bases per consumer warp) and end exactly at a tile edge, at a 32-base lane
+    batch edge, at a 64-base window edge, and at the text end."""
+    tile = 1024 * (threads // 32 - 1)
     rng = datagen.rng_for(99)
     n = tile * 6 + 37
     text = datagen.iid_text(n, rng)
     pats = []
     for edge in range(tile, n, tile):
-        for start in (edge - 40, edge - 17, edge - 1, edge, edge + 1, edge + 15, edge + 33):
+        for start in (edge - 40, edge - 33, edge - 17, edge - 1, edge, edge + 1, edge + 31, edge + 33):
             L = 40 if start + 40 <= n else n - start
             if 0 <= start and L > 0:
                 pats.append(text[start:start + L].tobytes())
         pats.append(text[edge - 25:edge].tobytes())          # ends exactly at the edge
-        pats.append(text[edge + 2:edge + 48].tobytes())      # ends at the 48-base window edge
+        pats.append(text[edge + 2:edge + 64].tobytes())      # ends at the 64-base window edge
     pats.append(text[n - 30:].tobytes())                     # ends at the text end
     want = ref(text, pats)
     t = b.Table(pats)
