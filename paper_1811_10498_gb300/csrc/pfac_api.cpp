@@ -126,6 +126,7 @@ pfac::TiledConfig tiled_config(const pfac_config &c)
     t.stages = c.stages;
     t.smem_table_bytes = c.rank_in_smem < 0 ? -1 : 0;
     t.walk_loads = c.walk_loads;
+    t.lane_offsets = c.lane_offsets;
     t.l2_persist = c.l2_persist;
     t.timeout_ns = 2000000000LL;
     return t;
@@ -385,7 +386,8 @@ int pfac_set_config(pfac_handle h, const pfac_config *cfg)
     if (cfg) {
         if (cfg->kernel < 0 || cfg->kernel > 2 || cfg->threads < 0 || (cfg->threads & 31) || cfg->threads > 1024 ||
             (cfg->threads > 0 && cfg->threads < 64) || cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32 ||
-            cfg->stages < 0 || cfg->stages == 1 || cfg->stages > 8)
+            cfg->stages < 0 || cfg->stages == 1 || cfg->stages > 8 || cfg->walk_loads < 0 ||
+            (cfg->lane_offsets != 0 && cfg->lane_offsets != 16 && cfg->lane_offsets != 32))
             return fail(PFAC_ERR_INVALID_ARG);
         if (cfg->kernel == 2 && !(h->skip_bytes > 0 && h->host.filter_b > 0)) return fail(PFAC_ERR_UNSUPPORTED);
     }

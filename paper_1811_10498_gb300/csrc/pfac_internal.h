@@ -101,6 +101,7 @@ struct TiledConfig {
     int32_t ctas_per_sm;
     int32_t stages;            // text stages in the shared-memory ring (0 = default)
     int32_t walk_loads;        // dependent table loads a walk may take in kernel 2 (0 = default 2)
+    int32_t lane_offsets;      // offsets per consumer lane: 16 (default) or 32
     int32_t smem_table_bytes;  // < 0: keep the rank index in global memory
     int32_t l2_persist;        // > 0: access-policy window over the skip entries
     int64_t timeout_ns;        // limit of every bounded wait

@@ -280,11 +280,12 @@ int launch_walk_rows_any(const DeviceTable &t, const void *text, bool packed, in
 // ---------------------------------------------------------------------------
 // Kernel 2: warp-specialised pipeline.
 //
-//   * one producer warp stages the text of each tile (1024 bases per consumer warp)
+//   * one producer warp stages the text of each tile (32 x 16 or 32 x 32 bases per
+//     consumer warp)
 //     into an S-stage shared-memory ring with TMA bulk copies; full/empty mbarriers
 //     hand stages to the consumer warps and back, with bounded waits;
-//   * each consumer lane owns 32 consecutive offsets and reads one 64-base window
-//     (four packed words) from the stage. A fully unrolled, branch-free block tests
+//   * each consumer lane owns 16 (or 32) consecutive offsets and reads one 64-base
+//     window (four packed words) from the stage. A fully unrolled, branch-free block tests
 //     the prefix filter for every offset (one shared-memory load): a clear bit means
 //     the walk ends before depth b with no pattern on the way, answer 0;
 //   * the offsets whose bit is set (a few percent) are spread over the warp by a
@@ -465,7 +466,7 @@ __device__ __forceinline__ uint32_t window_at(uint32_t x0, uint32_t x1, uint32_t
     return __funnelshift_r(lo, hi, (uint32_t)(p & 15) * 2);
 }
 
-template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16>
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW>
 __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             return;
         }
         const uint8_t *stage = stage0 + (size_t)st * P.stage_bytes;
-        const int p_rel = warp * 1024 + lane * 32;
+        const int p_rel = warp * (32 * LW) + lane * LW;
         const int64_t gp0 = t * (int64_t)P.tile + p_rel;
         // 64-base window: packed words and a mask of bases that cannot be read (past
         // the text end, or ASCII bytes outside ACGT).
@@ -557,12 +558,19 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
         if (rem > 0) {
             if (PACKED) {
                 const uint32_t *w = reinterpret_cast<const uint32_t *>(stage) + (p_rel >> 4);
-                const uint2 a = *reinterpret_cast<const uint2 *>(w);
-                const uint2 c = *reinterpret_cast<const uint2 *>(w + 2);
-                x0 = a.x;
-                x1 = a.y;
-                x2 = c.x;
-                x3 = c.y;
+                if (LW == 32) {   // even word index: two 64-bit loads
+                    const uint2 a = *reinterpret_cast<const uint2 *>(w);
+                    const uint2 c = *reinterpret_cast<const uint2 *>(w + 2);
+                    x0 = a.x;
+                    x1 = a.y;
+                    x2 = c.x;
+                    x3 = c.y;
+                } else {
+                    x0 = w[0];
+                    x1 = w[1];
+                    x2 = w[2];
+                    x3 = w[3];
+                }
             } else {
                 const uint4 *r = reinterpret_cast<const uint4 *>(stage + p_rel);
                 uint32_t b0, b1, b2, b3;
@@ -575,14 +583,15 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&empty[st]));   // this warp is done with the stage
-        const uint32_t valid = rem >= 32 ? 0xFFFFFFFFu : (rem > 0 ? ((1u << rem) - 1u) : 0u);
+        const uint32_t all = LW == 32 ? 0xFFFFFFFFu : ((1u << LW) - 1u);
+        const uint32_t valid = rem >= LW ? all : (rem > 0 ? ((1u << rem) - 1u) : 0u);
         const uint32_t fast = clear_runs(bad, B) & valid;   // the b-mer is readable
 
         // Every offset: one filter bit for the b bases starting there. A clear bit
         // means the walk ends before depth b with no pattern on the way: answer 0.
         uint32_t pend = 0;
 #pragma unroll
-        for (int j = 0; j < 32; j++) {
+        for (int j = 0; j < LW; j++) {
             const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
             const uint32_t kmer = win & bmask;   // bases j .. j+b-1
             const uint32_t word = FSMEM ? sf[kmer >> 5] : __ldg(T.filter + (kmer >> 5));
@@ -592,16 +601,21 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
         pend |= valid & ~fast;     // these walk from the root
 
         if (!COMPACT && valid) {
-            if (valid == 0xFFFFFFFFu) {
+            if (valid == all) {
                 int32_t *o = P.out + gp0;
                 const int4 z = make_int4(0, 0, 0, 0);
 #pragma unroll
-                for (int v = 0; v < 8; v++) st_global_v4_hint(o + 4 * v, z, pol);
+                for (int v = 0; v < LW / 4; v++) st_global_v4_hint(o + 4 * v, z, pol);
             } else {
-                for (int j = 0; j < 32; j++)
+                for (int j = 0; j < LW; j++)
                     if ((valid >> j) & 1u) P.out[gp0 + j] = 0;
             }
         }
+
+        // The zeros above were stored by the lane that owns each offset; a match found
+        // below is stored by whichever lane walks it. The warp barrier orders the
+        // first before the second.
+        __syncwarp();
 
         // -------- walks that go on --------
         // Spread them over the warp: item r of the warp (in lane order, then offset
@@ -638,8 +652,8 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             // the (r - oe)-th set bit of the owner's mask (r - oe < popcount by construction)
             uint32_t m = om;
             for (uint32_t i = r - oe; i > 0; i--) m &= m - 1u;
-            const int j = (__ffs(m) - 1) & 31;
-            const int64_t gp = t * (int64_t)P.tile + warp * 1024 + owner * 32 + j;
+            const int j = (__ffs(m) - 1) & (LW - 1);
+            const int64_t gp = t * (int64_t)P.tile + warp * (32 * LW) + owner * LW + j;
             const uint64_t badj = (((uint64_t)obad_hi << 32) | obad_lo) >> j;
             // bases readable from the window; `ends` when the text (or the run of ACGT
             // bytes) really stops there rather than the window
@@ -732,11 +746,11 @@ struct ScanLayout {
 
 static inline uint32_t align128(uint64_t x) { return (uint32_t)((x + 127) & ~(uint64_t)127); }
 
-static ScanLayout scan_layout(int consumers, int stages, int64_t filter_smem_bytes, int64_t rank_smem_bytes,
+static ScanLayout scan_layout(int consumers, int lw, int stages, int64_t filter_smem_bytes, int64_t rank_smem_bytes,
                               bool packed)
 {
     ScanLayout L{};
-    const int64_t tile = 1024LL * consumers;
+    const int64_t tile = 32LL * lw * consumers;
     uint64_t off = kBarBytes;
     L.off_filter = (uint32_t)off;
     off += align128((uint64_t)filter_smem_bytes);
@@ -752,6 +766,7 @@ static ScanLayout scan_layout(int consumers, int stages, int64_t filter_smem_byt
 }
 
 static int consumers_of(const TiledConfig &cfg) { return cfg.threads / 32 - 1; }
+static int lane_width_of(const TiledConfig &cfg) { return cfg.lane_offsets == 32 ? 32 : 16; }
 static int stages_of(const TiledConfig &cfg, bool packed) { return cfg.stages > 0 ? cfg.stages : (packed ? 4 : 2); }
 
 // Shared memory per CTA, by priority: the text stages, the prefix filter (read for
@@ -765,13 +780,14 @@ static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool pac
 {
     SmemPlan pl{};
     const int C = consumers_of(cfg);
+    const int LW = lane_width_of(cfg);
     const int S = stages_of(cfg, packed);
     const int64_t per_cta = (int64_t)dp.smem_per_sm / std::max(1, cfg.ctas_per_sm) - 1024;
     const int64_t limit = std::min<int64_t>(dp.smem_optin, per_cta);
     const int64_t words = t.filter_b >= 3 ? ((int64_t)1 << (2 * t.filter_b)) / 32 : 1;
     const int64_t fbytes = words * 4;
     const int64_t rbytes = words * (t.rank_wide ? 4 : 2);
-    auto total = [&](int64_t f, int64_t r) { return (int64_t)scan_layout(C, S, f, r, packed).total; };
+    auto total = [&](int64_t f, int64_t r) { return (int64_t)scan_layout(C, LW, S, f, r, packed).total; };
     if (total(0, 0) > limit) {
         pl.total = -1;
         return pl;
@@ -830,7 +846,8 @@ template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16>
 static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t smem, int tail_grid, cudaStream_t st,
                          const TiledConfig &cfg, const DeviceProps &dp)
 {
-    auto kern = scan_kernel<PACKED, COMPACT, FSMEM, RANK16>;
+    auto kern = lane_width_of(cfg) == 32 ? scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32>
+                                         : scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 16>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return PFAC_ERR_CUDA;
     if (launch_with_policy(kern, P, grid, threads, smem, st, cfg, dp) != cudaSuccess) return PFAC_ERR_CUDA;
@@ -857,13 +874,14 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     if (compact && cudaMemsetAsync(count, 0, sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     if (n == 0) return PFAC_OK;
     const int C = consumers_of(cfg);
+    const int LW = lane_width_of(cfg);
     const int S = stages_of(cfg, packed);
     if (!t.skip || !t.filter || !t.rank || !t.dense || t.filter_b < 1 || t.filter_b > kMaxFilterB || C < 1 ||
         (cfg.threads & 31) || cfg.threads > 1024 || S < 2 || S > kMaxStages || !scratch.items || !scratch.count)
         return PFAC_ERR_INVALID_ARG;
     const SmemPlan pl = plan_smem(t, cfg, packed, dp);
     if (pl.total < 0 || pl.total > dp.smem_optin) return PFAC_ERR_UNSUPPORTED;
-    const ScanLayout L = scan_layout(C, S, pl.filter_bytes, pl.rank_bytes, packed);
+    const ScanLayout L = scan_layout(C, LW, S, pl.filter_bytes, pl.rank_bytes, packed);
     if (cudaMemsetAsync(scratch.count, 0, sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     ScanParams P{};
     P.t = t;
@@ -878,7 +896,7 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     P.defer = (DeferItem *)scratch.items;
     P.defer_cap = scratch.cap;
     P.defer_count = scratch.count;
-    P.tile = 1024 * C;
+    P.tile = 32 * LW * C;
     P.n_tiles = (n + P.tile - 1) / P.tile;
     P.consumers = C;
     P.stages = S;

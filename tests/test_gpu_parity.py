@@ -65,6 +65,8 @@ def genome_small():
     dict(kernel=2, ctas_per_sm=2, threads=512),
     dict(kernel=2, walk_loads=1),
     dict(kernel=2, walk_loads=64),
+    dict(kernel=2, lane_offsets=32),
+    dict(kernel=2, lane_offsets=32, threads=64),
 ], ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
 def test_genome_configs(genome_small, cfg, packed):
     w, want = genome_small
@@ -137,12 +139,12 @@ def test_empty_text():
     assert gpu_match(t, np.zeros(0, dtype=np.uint8)).size == 0
 
 
-@pytest.mark.parametrize("threads", [64, 128, 1024])
-def test_matches_across_tile_edges(threads):
+@pytest.mark.parametrize("threads,lw", [(64, 16), (128, 32), (1024, 16)])
+def test_matches_across_tile_edges(threads, lw):
     """Long patterns planted so they start just before, at and after tile edges (a tile
     is 1024 bases per consumer warp) and end exactly at a tile edge, at a 32-base lane
     batch edge, at a 64-base window edge, and at the text end."""
-    tile = 1024 * (threads // 32 - 1)
+    tile = 32 * lw * (threads // 32 - 1)
     rng = datagen.rng_for(99)
     n = tile * 6 + 37
     text = datagen.iid_text(n, rng)
@@ -158,9 +160,9 @@ def test_matches_across_tile_edges(threads):
     want = ref(text, pats)
     t = b.Table(pats)
     for kernel in (1, 2):
-        got = gpu_match(t, text, kernel=kernel, threads=threads)
+        got = gpu_match(t, text, kernel=kernel, threads=threads, lane_offsets=lw)
         assert np.array_equal(got, want), (kernel, first_diff(got, want))
-        got = gpu_match_packed(t, text, kernel=kernel, threads=threads)
+        got = gpu_match_packed(t, text, kernel=kernel, threads=threads, lane_offsets=lw)
         assert np.array_equal(got, want), (kernel, first_diff(got, want))
     assert (want != 0).sum() >= len(pats) // 2
 
@@ -297,3 +299,17 @@ def test_host_pointers_rejected():
     assert rc == b.CODE["PFAC_ERR_INVALID_ARG"]
     rc = b.lib().pfac_match(t.h, out.data_ptr(), 16, cpu.data_ptr(), None)
     assert rc == b.CODE["PFAC_ERR_INVALID_ARG"]
+
+
+@pytest.mark.parametrize("cfg", [dict(kernel=2, lane_offsets=32, walk_loads=8), dict(kernel=2, walk_loads=64)],
+                         ids=["lw32_loads8", "lw16_loads64"])
+def test_repeated_scans_with_long_walks_in_kernel(genome_small, cfg):
+    """Matches found inside the scan kernel are stored by the lane that walks them,
+    after the zero stores of the lane that owns the offset; repeated runs must agree
+    with the oracle every time (this once showed lost and spurious matches when the
+    two stores were not ordered)."""
+    w, want = genome_small
+    t = b.Table((w.blob, w.offsets))
+    for _ in range(6):
+        got = gpu_match_packed(t, w.text, **cfg)
+        assert np.array_equal(got, want), first_diff(got, want)
