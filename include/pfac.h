@@ -50,7 +50,9 @@ enum {
     PFAC_ERR_OVERFLOW = 7,        /* more matches than the caller's capacity */
     PFAC_ERR_TIMEOUT = 8,         /* a bounded device-side wait ran out */
     PFAC_ERR_HOST_ONLY = 9,       /* the handle was built without a device copy */
-    PFAC_ERR_UNSUPPORTED = 10     /* option not available for this table (see pfac_info_ex) */
+    PFAC_ERR_UNSUPPORTED = 10,    /* option not available for this table (see pfac_info_ex) */
+    PFAC_ERR_SCRATCH_LIMIT = 11   /* the text is longer than pfac_match_packed_noalloc's fixed
+                                     scratch buffer can serve */
 };
 
 /* Opaque, library-owned table handle. */
@@ -227,6 +229,32 @@ int pfac_match_batched(const pfac_handle *sets, int32_t n_sets, const uint8_t *d
  * kernel recorded (for example PFAC_ERR_TIMEOUT from a bounded wait). Synchronises
  * `stream`. */
 int pfac_device_status(pfac_handle h, int32_t *status, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Allocation-free scan (the paper has no counterpart).
+ * ------------------------------------------------------------------------- */
+
+/* pfac_match_packed without any device allocation by the library, for callers that
+ * cannot have device memory allocated on their behalf: processes that run under a
+ * fixed device-memory budget or whose device memory belongs to another allocator
+ * (a framework's caching pool), and latency-sensitive loops that must not meet the
+ * device-wide synchronisation a cudaMalloc or cudaFree can cause.
+ *
+ * The ordinary scan keeps its list of deferred long walks in scratch that the library
+ * allocates per stream on first use. This entry point uses instead one fixed buffer
+ * compiled into the library (6 MiB, 2^18 deferred walks), which every GPU that loads
+ * the library holds until the process exits. Arguments, output and results are those
+ * of pfac_match_packed; the caller still passes the text and the output.
+ *   - n_bases may be at most 2^26 (67,108,864 bases): longer texts are rejected with
+ *     PFAC_ERR_SCRATCH_LIMIT before anything is launched (split them into pieces that
+ *     overlap by max_len - 1 bases).
+ *   - The first call on a device looks up the buffer's device address with that device
+ *     current; make that first call before capturing any stream.
+ *   - All calls share the one buffer and each call clears the part that must start at
+ *     zero: calls that overlap on the GPU (on different streams, or from several host
+ *     threads without ordering) race on it and must not be issued. */
+int pfac_match_packed_noalloc(pfac_handle h, const uint32_t *d_packed, int64_t n_bases,
+                              int32_t *d_out_ids, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Failure detection (the paper has no counterpart).

@@ -20,7 +20,7 @@ PFAC_OK = 0
 STATUS = {
     0: "PFAC_OK", 1: "PFAC_ERR_INVALID_ARG", 2: "PFAC_ERR_EMPTY_PATTERN", 3: "PFAC_ERR_BAD_SYMBOL",
     4: "PFAC_ERR_TOO_MANY_STATES", 5: "PFAC_ERR_OOM", 6: "PFAC_ERR_CUDA", 7: "PFAC_ERR_OVERFLOW",
-    8: "PFAC_ERR_TIMEOUT", 9: "PFAC_ERR_HOST_ONLY", 10: "PFAC_ERR_UNSUPPORTED",
+    8: "PFAC_ERR_TIMEOUT", 9: "PFAC_ERR_HOST_ONLY", 10: "PFAC_ERR_UNSUPPORTED", 11: "PFAC_ERR_SCRATCH_LIMIT",
 }
 CODE = {v: k for k, v in STATUS.items()}
 
@@ -73,6 +73,7 @@ _SIGS = {
     "pfac_match_batched": (C.c_int, [P, I32, P, P, P, I32, P, P]),
     "pfac_device_status": (C.c_int, [P, P, P]),
     "pfac_debug_timeout_probe": (C.c_int, [P, I64, P]),
+    "pfac_match_packed_noalloc": (C.c_int, [P, P, I64, P, P]),
 }
 
 
@@ -233,6 +234,12 @@ def pfac_match_batched(handles, d_texts, d_read_offsets, d_read_set, d_out_ids, 
     n_reads = d_read_set.numel()
     _check(lib().pfac_match_batched(arr, len(handles), _dptr(d_texts), _dptr(d_read_offsets), _dptr(d_read_set),
                                     n_reads, _dptr(d_out_ids), _stream(stream)), "pfac_match_batched")
+
+
+def pfac_match_packed_noalloc(h: int, d_packed, n_bases: int, d_out_ids, stream=None):
+    """pfac_match_packed with the library's fixed scratch buffer: no device allocation."""
+    _check(lib().pfac_match_packed_noalloc(h, _dptr(d_packed), n_bases, _dptr(d_out_ids), _stream(stream)),
+           "pfac_match_packed_noalloc")
 
 
 def pfac_device_status(h: int, stream=None) -> int:

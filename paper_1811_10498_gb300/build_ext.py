@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpfac.so")
-SOURCES = ["pfac_kernels.cu", "pfac_api.cpp", "trie_build.cpp"]
+SOURCES = ["pfac_kernels.cu", "pfac_api.cpp", "trie_build.cpp", "pfac_noalloc.cu"]
 HEADERS = ["pfac_internal.h", os.path.join("..", "..", "include", "pfac.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

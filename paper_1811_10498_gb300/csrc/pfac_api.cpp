@@ -212,6 +212,40 @@ int run_scan(pfac_handle h, const void *text, bool packed, int64_t n, int32_t *o
 
 }  // namespace
 
+namespace pfac {
+
+// The packed scan with deferred-walk scratch supplied by the caller instead of the
+// per-stream scratch of run_scan. Same checks and the same kernels.
+int scan_packed_with_scratch(pfac_table *h, const uint32_t *d_packed, int64_t n_bases, int32_t *d_out_ids,
+                             const DeferScratch &scratch, cudaStream_t st)
+{
+    DeviceProps dp{};
+    int rc = check_handle_for_launch(h, &dp);
+    if (rc != PFAC_OK) return rc;
+    if (n_bases < 0) return fail(PFAC_ERR_INVALID_ARG);
+    if (n_bases == 0) return PFAC_OK;
+    if (!is_device_ptr(d_packed) || !is_device_ptr(d_out_ids)) return fail(PFAC_ERR_INVALID_ARG);
+    const pfac_config c = effective_config(h, true);
+    bool tiled = c.kernel == 2 && has_kernel2(h) && aligned16(d_packed) && aligned16(d_out_ids);
+    if (tiled) {
+        rc = launch_tiled(h->dt, d_packed, true, n_bases, d_out_ids, nullptr, nullptr, 0, nullptr, tiled_config(c),
+                          scratch, st, dp);
+        if (rc == PFAC_ERR_UNSUPPORTED) tiled = false;
+        else if (rc != PFAC_OK) return rc == PFAC_ERR_CUDA ? cuda_fail(cudaGetLastError()) : fail(rc);
+    }
+    if (!tiled) {
+        // kernel 1 keeps no scratch
+        rc = launch_walk_rows_any(h->dt, d_packed, true, n_bases, d_out_ids, nullptr, nullptr, 0, nullptr, st, dp);
+        if (rc != PFAC_OK) return rc == PFAC_ERR_CUDA ? cuda_fail(cudaGetLastError()) : fail(rc);
+    }
+    return PFAC_OK;
+}
+
+int set_last_error(int code) { return fail(code); }
+int set_last_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
+}  // namespace pfac
+
 extern "C" {
 
 int pfac_last_error(void) { return g_last_error; }
@@ -232,6 +266,7 @@ const char *pfac_error_string(int status)
     case PFAC_ERR_TIMEOUT: return "bounded device wait ran out";
     case PFAC_ERR_HOST_ONLY: return "handle has no device copy";
     case PFAC_ERR_UNSUPPORTED: return "option not supported for this table";
+    case PFAC_ERR_SCRATCH_LIMIT: return "text longer than the allocation-free scan's fixed scratch allows";
     default: return "unknown status";
     }
 }

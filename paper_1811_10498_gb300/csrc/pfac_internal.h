@@ -80,6 +80,8 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
 // ---------------------------------------------------------------------------
 #include <cuda_runtime.h>
 
+struct pfac_table;
+
 namespace pfac {
 
 struct DeviceTable {
@@ -115,6 +117,7 @@ struct DeferScratch {
 };
 
 size_t defer_item_bytes();
+constexpr size_t kDeferItemBytes = 24;   // sizeof the kernel's deferred-walk record
 
 struct DeviceProps {
     int device;
@@ -148,5 +151,14 @@ int64_t tiled_smem_bytes(const DeviceTable &t, const TiledConfig &cfg, bool pack
 // A kernel whose only job is a bounded wait on an mbarrier that nothing completes:
 // it must give up after limit_ns and record PFAC_ERR_TIMEOUT in *status.
 int launch_timeout_probe(int32_t *status, int64_t limit_ns, cudaStream_t st);
+
+// pfac_match_packed with caller-provided deferred-walk scratch (used by the
+// allocation-free entry point in pfac_noalloc.cu). Returns a PFAC_* status.
+int scan_packed_with_scratch(struct ::pfac_table *h, const uint32_t *d_packed, int64_t n_bases,
+                             int32_t *d_out_ids, const DeferScratch &scratch, cudaStream_t st);
+
+// Record a status (or a CUDA error) as this thread's last error; returns the status.
+int set_last_error(int code);
+int set_last_cuda_error(cudaError_t e);
 
 }  // namespace pfac

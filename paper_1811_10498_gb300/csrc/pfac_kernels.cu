@@ -921,6 +921,7 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
 }
 
 size_t defer_item_bytes() { return sizeof(DeferItem); }
+static_assert(sizeof(DeferItem) == kDeferItemBytes, "deferred-walk record size");
 
 // ---------------------------------------------------------------------------
 // Timeout probe (exercises the bounded wait without any fault or hang).
