@@ -211,18 +211,28 @@ int pfac_match_compact(pfac_handle h, const uint32_t *d_packed, int64_t n_bases,
                        int64_t *d_offsets, int32_t *d_ids, int64_t capacity,
                        int64_t *d_count, void *stream);
 
-/* Many reads against many resident tables in ONE launch.
+/* Many reads against many resident tables in ONE pass (not in the paper, whose input
+ * is newline-separated reads scanned as one text, Table IV).
  *   sets[n_sets]                 : host array of handles built on this device
- *   d_texts                      : all reads' ASCII bytes, concatenated
- *   d_read_offsets[n_reads + 1]  : read r is d_texts[off[r] .. off[r+1]), increasing
+ *                                  (1 <= n_sets <= 65535)
+ *   d_texts[text_len]            : all reads' ASCII bytes, concatenated
+ *   d_read_offsets[n_reads + 1]  : read r is d_texts[off[r] .. off[r+1]) (offsets are
+ *                                  clamped to [0, text_len])
  *   d_read_set[n_reads]          : index into sets[] of the table for read r
- *   d_out_ids                    : same layout as d_texts
- * Walks never cross a read's end. The first call with a given list of handles
- * uploads a small descriptor array (a synchronous copy); later calls with the same
- * list reuse it, so a call issued while a stream is being captured into a CUDA
- * graph must use a list that was seen before capture. */
+ *   d_out_ids[text_len]          : same layout as d_texts; every offset inside a read
+ *                                  gets the longest pattern starting there, within the
+ *                                  read (offsets outside every read are not written)
+ * Walks never cross a read's end; bytes outside ACGT end walks as in pfac_match. A
+ * read_set entry outside [0, n_sets) records PFAC_ERR_INVALID_ARG in the device status
+ * of sets[0] and leaves that read's output unwritten.
+ * The call packs the text, plans the work and runs one persistent scan launch (plus a
+ * tail launch for the few long walks), all on `stream`, with scratch that the library
+ * keeps per stream. The first call with a given list of handles uploads a small
+ * descriptor array, and the first call on a stream (or with a larger text) allocates
+ * scratch; both are synchronous, so issue such a call before capturing the stream
+ * into a CUDA graph; later calls with the same handle list and sizes are capturable. */
 int pfac_match_batched(const pfac_handle *sets, int32_t n_sets, const uint8_t *d_texts,
-                       const int64_t *d_read_offsets, const int32_t *d_read_set,
+                       int64_t text_len, const int64_t *d_read_offsets, const int32_t *d_read_set,
                        int32_t n_reads, int32_t *d_out_ids, void *stream);
 
 /* Read (and clear) the device status word of a handle: PFAC_OK or the first error a

@@ -70,7 +70,7 @@ _SIGS = {
     "pfac_match": (C.c_int, [P, P, I64, P, P]),
     "pfac_match_packed": (C.c_int, [P, P, I64, P, P]),
     "pfac_match_compact": (C.c_int, [P, P, I64, P, P, I64, P, P]),
-    "pfac_match_batched": (C.c_int, [P, I32, P, P, P, I32, P, P]),
+    "pfac_match_batched": (C.c_int, [P, I32, P, I64, P, P, I32, P, P]),
     "pfac_device_status": (C.c_int, [P, P, P]),
     "pfac_debug_timeout_probe": (C.c_int, [P, I64, P]),
     "pfac_match_packed_noalloc": (C.c_int, [P, P, I64, P, P]),
@@ -230,10 +230,12 @@ def pfac_match_compact(h: int, d_packed, n_bases: int, d_offsets, d_ids, d_count
 
 
 def pfac_match_batched(handles, d_texts, d_read_offsets, d_read_set, d_out_ids, stream=None):
+    """Scan every read (``d_texts[off[r]:off[r+1]]``) with the table ``handles[d_read_set[r]]``."""
     arr = (C.c_void_p * max(1, len(handles)))(*handles)
     n_reads = d_read_set.numel()
-    _check(lib().pfac_match_batched(arr, len(handles), _dptr(d_texts), _dptr(d_read_offsets), _dptr(d_read_set),
-                                    n_reads, _dptr(d_out_ids), _stream(stream)), "pfac_match_batched")
+    _check(lib().pfac_match_batched(arr, len(handles), _dptr(d_texts), d_texts.numel(), _dptr(d_read_offsets),
+                                    _dptr(d_read_set), n_reads, _dptr(d_out_ids), _stream(stream)),
+           "pfac_match_batched")
 
 
 def pfac_match_packed_noalloc(h: int, d_packed, n_bases: int, d_out_ids, stream=None):

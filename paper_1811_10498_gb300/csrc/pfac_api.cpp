@@ -183,6 +183,74 @@ int get_scratch(int dev, cudaStream_t st, int64_t n, pfac::DeferScratch *out)
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Batched scans: a device array of table descriptors per distinct list of handles
+// (uploaded once, dropped when one of its handles is destroyed), and scratch per
+// (device, stream) grown on demand.
+std::mutex g_sets_mu;
+std::map<std::pair<int, std::vector<pfac_handle>>, void *> g_sets;
+
+int set_descriptors(const pfac_handle *sets, int32_t n_sets, int dev, const pfac::DeviceTable **out)
+{
+    std::vector<pfac_handle> key(sets, sets + n_sets);
+    std::lock_guard<std::mutex> lk(g_sets_mu);
+    auto it = g_sets.find({dev, key});
+    if (it == g_sets.end()) {
+        std::vector<pfac::DeviceTable> host((size_t)n_sets);
+        for (int32_t i = 0; i < n_sets; i++) host[(size_t)i] = sets[i]->dt;
+        void *d = nullptr;
+        cudaError_t e = cudaMalloc(&d, host.size() * sizeof(pfac::DeviceTable));
+        if (e == cudaSuccess) e = cudaMemcpy(d, host.data(), host.size() * sizeof(pfac::DeviceTable), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (d) cudaFree(d);
+            return cuda_fail(e);
+        }
+        it = g_sets.emplace(std::make_pair(dev, key), d).first;
+    }
+    *out = (const pfac::DeviceTable *)it->second;
+    return PFAC_OK;
+}
+
+void forget_handle(pfac_handle h)
+{
+    std::lock_guard<std::mutex> lk(g_sets_mu);
+    for (auto it = g_sets.begin(); it != g_sets.end();) {
+        const auto &v = it->first.second;
+        if (std::find(v.begin(), v.end(), h) != v.end()) {
+            cudaFree(it->second);
+            it = g_sets.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+std::mutex g_bscratch_mu;
+std::map<std::pair<int, cudaStream_t>, Scratch> g_bscratch;
+
+int batch_scratch(int dev, cudaStream_t st, int64_t bytes, void **out)
+{
+    std::lock_guard<std::mutex> lk(g_bscratch_mu);
+    Scratch &sc = g_bscratch[{dev, st}];
+    if (sc.cap < bytes) {
+        if (sc.mem) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess) e = cudaFree(sc.mem);
+            if (e != cudaSuccess) return cuda_fail(e);
+            sc.mem = nullptr;
+            sc.cap = 0;
+        }
+        cudaError_t e = cudaMalloc(&sc.mem, (size_t)bytes);
+        if (e != cudaSuccess) {
+            sc.mem = nullptr;
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? PFAC_ERR_OOM : PFAC_ERR_CUDA);
+        }
+        sc.cap = bytes;
+    }
+    *out = sc.mem;
+    return PFAC_OK;
+}
+
 // Run the scan with the handle's configuration. Kernel 2 needs 16-byte aligned text
 // and output, the filter and the skip entries; otherwise kernel 1 runs.
 int run_scan(pfac_handle h, const void *text, bool packed, int64_t n, int32_t *out, int64_t *c_off,
@@ -347,6 +415,7 @@ pfac_handle pfac_build(const char *const *patterns, const int32_t *lengths, int3
 int pfac_destroy(pfac_handle h)
 {
     if (!h) return PFAC_OK;
+    forget_handle(h);
     int rc = PFAC_OK;
     if (h->dmem) {
         int cur = 0;
@@ -508,13 +577,33 @@ int pfac_device_status(pfac_handle h, int32_t *status, void *stream)
     return PFAC_OK;
 }
 
-int pfac_match_batched(const pfac_handle *sets, int32_t n_sets, const uint8_t *d_texts,
-                       const int64_t *d_read_offsets, const int32_t *d_read_set, int32_t n_reads,
-                       int32_t *d_out_ids, void *stream)
+int pfac_match_batched(const pfac_handle *sets, int32_t n_sets, const uint8_t *d_texts, int64_t text_len,
+                       const int64_t *d_read_offsets, const int32_t *d_read_set, int32_t n_reads, int32_t *d_out_ids,
+                       void *stream)
 {
-    (void)sets; (void)n_sets; (void)d_texts; (void)d_read_offsets; (void)d_read_set; (void)n_reads;
-    (void)d_out_ids; (void)stream;
-    return fail(PFAC_ERR_UNSUPPORTED);
+    if (!sets || n_sets < 1 || n_sets > 65535 || text_len < 0 || n_reads < 0) return fail(PFAC_ERR_INVALID_ARG);
+    pfac::DeviceProps dp{};
+    for (int32_t i = 0; i < n_sets; i++) {
+        int rc = check_handle_for_launch(sets[i], &dp);
+        if (rc != PFAC_OK) return rc;
+        if (!has_kernel2(sets[i])) return fail(PFAC_ERR_UNSUPPORTED);
+    }
+    if (text_len == 0 || n_reads == 0) return PFAC_OK;
+    if (!is_device_ptr(d_texts) || !is_device_ptr(d_read_offsets) || !is_device_ptr(d_read_set) ||
+        !is_device_ptr(d_out_ids))
+        return fail(PFAC_ERR_INVALID_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    const pfac::DeviceTable *d_sets = nullptr;
+    int rc = set_descriptors(sets, n_sets, dp.device, &d_sets);
+    if (rc != PFAC_OK) return rc;
+    const int64_t defer_cap = defer_capacity(text_len);
+    void *scratch = nullptr;
+    rc = batch_scratch(dp.device, st, pfac::batch_scratch_bytes(text_len, n_reads, defer_cap), &scratch);
+    if (rc != PFAC_OK) return rc;
+    const pfac_config c = effective_config(sets[0], false);
+    rc = pfac::launch_batched(d_sets, n_sets, d_texts, text_len, d_read_offsets, d_read_set, n_reads, d_out_ids,
+                              scratch, defer_cap, c.walk_loads, st, dp);
+    return rc == PFAC_OK ? PFAC_OK : cuda_fail(cudaGetLastError());
 }
 
 int pfac_debug_timeout_probe(int32_t *d_status, int64_t limit_ns, void *stream)

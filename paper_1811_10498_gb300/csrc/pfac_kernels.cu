@@ -304,8 +304,8 @@ struct DeferItem {
     long long gp;      // text offset of the walk
     uint32_t s;        // state reached
     uint32_t best;     // deepest terminal state passed (0 = none)
-    int32_t q;         // bases consumed
-    int32_t pad;
+    uint32_t q_set;    // bases consumed (low 16 bits) | table index in a batch (high 16 bits)
+    int32_t span;      // bases from gp to the end of the walk's text (or read), capped at 2^31-1
 };
 
 struct ScanParams {
@@ -371,22 +371,30 @@ __device__ __forceinline__ uint32_t base_mask(uint32_t L)
 }
 
 // Sixteen bases of the text from position pos (packed or ASCII) read from global
-// memory, with a mask of the bases that cannot be read (past the end of the text,
-// or ASCII bytes outside ACGT).
+// memory, with a mask of the bases that cannot be read (at or past `end`, ASCII bytes
+// outside ACGT, or bases marked in the optional invalid-base bitmap of packed text).
 template <bool PACKED>
-__device__ __forceinline__ uint32_t text16(const void *__restrict__ text, int64_t n, int64_t pos, uint32_t *bad)
+__device__ __forceinline__ uint32_t text16(const void *__restrict__ text, const uint32_t *__restrict__ invalid,
+                                           int64_t end, int64_t pos, uint32_t *bad)
 {
-    const int64_t rem = n - pos;
+    const int64_t rem = end - pos;
     uint32_t b = rem >= 16 ? 0u : (rem > 0 ? (0xFFFFu << rem) & 0xFFFFu : 0xFFFFu);
     uint32_t w = 0;
     if (PACKED) {
         const int64_t wi = pos >> 4;
-        const int64_t n_words = (n + 15) >> 4;
+        const int64_t n_words = (end + 15) >> 4;
         const uint32_t lo = wi < n_words ? __ldg((const uint32_t *)text + wi) : 0u;
         const uint32_t hi = wi + 1 < n_words ? __ldg((const uint32_t *)text + wi + 1) : 0u;
         w = __funnelshift_r(lo, hi, (uint32_t)(pos & 15) * 2);
+        if (invalid) {
+            const int64_t bi = pos >> 5;
+            const int64_t n_bw = (end + 31) >> 5;
+            const uint32_t blo = bi < n_bw ? __ldg(invalid + bi) : 0xFFFFFFFFu;
+            const uint32_t bhi = bi + 1 < n_bw ? __ldg(invalid + bi + 1) : 0xFFFFFFFFu;
+            b |= __funnelshift_r(blo, bhi, (uint32_t)(pos & 31)) & 0xFFFFu;
+        }
     } else {
-        for (int i = 0; i < 16 && pos + i < n; i++) {
+        for (int i = 0; i < 16 && pos + i < end; i++) {
             const int c = base_code_or_neg(__ldg((const uint8_t *)text + pos + i));
             if (c < 0) b |= 1u << i;
             else w |= (uint32_t)c << (2 * i);
@@ -397,18 +405,19 @@ __device__ __forceinline__ uint32_t text16(const void *__restrict__ text, int64_
 }
 
 // Continue a walk from state s with `q` bases consumed, reading the text from global
-// memory (deferred walks, and walks the deferred list had no room for). Returns the
-// pattern id (0 if none).
+// memory up to `end` (deferred walks, and walks the deferred list had no room for).
+// Returns the pattern id (0 if none).
 template <bool PACKED>
-__device__ int32_t walk_global(const DeviceTable &T, const void *__restrict__ text, int64_t n, int64_t gp,
-                               uint32_t s, int q, uint32_t best)
+__device__ int32_t walk_global(const DeviceTable &T, const void *__restrict__ text,
+                               const uint32_t *__restrict__ invalid, int64_t end, int64_t gp, uint32_t s, int q,
+                               uint32_t best)
 {
     uint4 e = __ldg(T.skip + s);
     for (;;) {
         if (e.y & kSkipSelfTerm) best = s;
         const uint32_t L = e.y & kSkipLenMask;
         uint32_t bad;
-        const uint32_t win = text16<PACKED>(text, n, gp + q, &bad);
+        const uint32_t win = text16<PACKED>(text, invalid, end, gp + q, &bad);
         const uint32_t need = L ? L : 1u;
         if (bad & ((need >= 16) ? 0xFFFFu : ((1u << need) - 1u))) break;   // cannot read the next step
         if (L) {
@@ -427,19 +436,32 @@ __device__ int32_t walk_global(const DeviceTable &T, const void *__restrict__ te
     return best ? __ldg(T.out_id + best) : 0;
 }
 
-// Record a non-zero result: dense output (the slot already holds 0) or the match list.
+// Where results go: the dense output array (whose slots already hold 0) or the match
+// list, plus the deferred-walk list.
+struct Sink {
+    int32_t *out;
+    int64_t *c_off;
+    int32_t *c_ids;
+    int64_t cap;
+    unsigned long long *count;
+    DeferItem *defer;
+    int64_t defer_cap;
+    unsigned long long *defer_count;
+};
+
+// Record a non-zero result.
 template <bool COMPACT>
-__device__ __forceinline__ void emit_match(const ScanParams &P, int64_t gp, int32_t v)
+__device__ __forceinline__ void emit_match(const Sink &K, int64_t gp, int32_t v)
 {
     if (!v) return;
     if (COMPACT) {
-        const unsigned long long k = atomicAdd(P.count, 1ull);
-        if ((int64_t)k < P.cap) {
-            P.c_off[k] = gp;
-            P.c_ids[k] = v;
+        const unsigned long long k = atomicAdd(K.count, 1ull);
+        if ((int64_t)k < K.cap) {
+            K.c_off[k] = gp;
+            K.c_ids[k] = v;
         }
     } else {
-        P.out[gp] = v;
+        K.out[gp] = v;
     }
 }
 
@@ -466,6 +488,167 @@ __device__ __forceinline__ uint32_t window_at(uint32_t x0, uint32_t x1, uint32_t
     return __funnelshift_r(lo, hi, (uint32_t)(p & 15) * 2);
 }
 
+// One warp-batch: lane `lane` owns the LW offsets gp0 = warp_base + lane*LW .. +LW-1
+// and holds the 64 bases from gp0 in x0..x3 with `bad` marking the bases that cannot
+// be read (past the end of its text or read, or not A/C/G/T); `valid` marks the
+// offsets this call must answer. Every offset's prefix-filter bit is tested; the
+// offsets that pass are spread over the warp and walked through skip entries inside
+// the window (at most walk_loads dependent loads), longer walks are deferred.
+// sf / srank: filter and rank index in shared memory, or nullptr for global memory.
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW>
+__device__ __forceinline__ void scan_lane_batch(const DeviceTable &T, const Sink &K, const uint32_t *sf,
+                                                const void *srank, int walk_loads, uint32_t set_index,
+                                                const void *text, const uint32_t *invalid, int64_t end,
+                                                int64_t warp_base, int lane, uint32_t x0, uint32_t x1, uint32_t x2,
+                                                uint32_t x3, uint64_t bad, uint32_t valid, bool vec_ok, uint64_t pol)
+{
+    using RankT = typename std::conditional<RANK16, uint16_t, uint32_t>::type;
+    const int B = T.filter_b;
+    const uint32_t bmask = (uint32_t)((1ull << (2 * B)) - 1ull);
+    const int64_t gp0 = warp_base + (int64_t)lane * LW;
+    const uint32_t all = LW == 32 ? 0xFFFFFFFFu : ((1u << LW) - 1u);
+    const uint32_t fast = clear_runs(bad, B) & valid;   // the b-mer is readable
+
+    // Every offset: one filter bit for the b bases starting there. A clear bit means
+    // the walk ends before depth b with no pattern on the way: answer 0.
+    uint32_t pend = 0;
+#pragma unroll
+    for (int j = 0; j < LW; j++) {
+        const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
+        const uint32_t kmer = win & bmask;   // bases j .. j+b-1
+        const uint32_t word = FSMEM ? sf[kmer >> 5] : __ldg(T.filter + (kmer >> 5));
+        pend |= ((word >> (kmer & 31u)) & 1u) << j;
+    }
+    pend &= fast;
+    pend |= valid & ~fast;     // these walk from the root
+
+    if (!COMPACT && valid) {
+        if (vec_ok && valid == all) {
+            int32_t *o = K.out + gp0;
+            const int4 z = make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int v = 0; v < LW / 4; v++) st_global_v4_hint(o + 4 * v, z, pol);
+        } else {
+            for (int j = 0; j < LW; j++)
+                if ((valid >> j) & 1u) K.out[gp0 + j] = 0;
+        }
+    }
+
+    // The zeros above were stored by the lane that owns each offset; a match found
+    // below is stored by whichever lane walks it. The warp barrier orders the first
+    // before the second.
+    __syncwarp();
+
+    // -------- walks that go on --------
+    // Spread them over the warp: item r of the warp (in lane order, then offset order)
+    // goes to lane r mod 32 in round r / 32. The owner's window comes by shuffle.
+    const uint32_t cnt = __popc(pend);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += o;
+    }
+    const uint32_t excl = incl - cnt;
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+        const uint32_t r = r0 + lane;
+        // owner = the last lane whose first item is <= r
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t e = __shfl_sync(0xFFFFFFFFu, excl, owner + step);
+            if (e <= r) owner += step;
+        }
+        const uint32_t om = __shfl_sync(0xFFFFFFFFu, pend, owner);
+        const uint32_t oe = __shfl_sync(0xFFFFFFFFu, excl, owner);
+        const uint32_t ofast = __shfl_sync(0xFFFFFFFFu, fast, owner);
+        const uint32_t ox0 = __shfl_sync(0xFFFFFFFFu, x0, owner);
+        const uint32_t ox1 = __shfl_sync(0xFFFFFFFFu, x1, owner);
+        const uint32_t ox2 = __shfl_sync(0xFFFFFFFFu, x2, owner);
+        const uint32_t ox3 = __shfl_sync(0xFFFFFFFFu, x3, owner);
+        const uint32_t obad_lo = __shfl_sync(0xFFFFFFFFu, (uint32_t)bad, owner);
+        const uint32_t obad_hi = __shfl_sync(0xFFFFFFFFu, (uint32_t)(bad >> 32), owner);
+        if (r >= total) continue;
+        // the (r - oe)-th set bit of the owner's mask (r - oe < popcount by construction)
+        uint32_t m = om;
+        for (uint32_t i = r - oe; i > 0; i--) m &= m - 1u;
+        const int j = (__ffs(m) - 1) & (LW - 1);
+        const int64_t gp = warp_base + (int64_t)owner * LW + j;
+        const uint64_t badj = (((uint64_t)obad_hi << 32) | obad_lo) >> j;
+        // bases readable from the window; `ends` when the text (or the run of ACGT
+        // bytes) really stops there rather than the window
+        const int wlim = badj ? __ffsll((long long)badj) - 1 : 64 - j;
+        const bool ends = badj != 0;
+        uint32_t s = 0, best = 0;
+        int q = 0;
+        uint4 e;
+        bool from_root = true;
+        if ((ofast >> j) & 1u) {
+            const uint32_t kmer = window_at(ox0, ox1, ox2, ox3, j) & bmask;
+            const uint32_t widx = kmer >> 5;
+            const uint32_t word = FSMEM ? sf[widx] : __ldg(T.filter + widx);
+            uint32_t base_rank;
+            if (srank) base_rank = (uint32_t)reinterpret_cast<const RankT *>(srank)[widx];
+            else if (T.rank_wide) base_rank = __ldg(reinterpret_cast<const uint32_t *>(T.rank) + widx);
+            else base_rank = (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(T.rank) + widx);
+            const uint32_t rk = base_rank + __popc(word & ((1u << (kmer & 31u)) - 1u));
+            e = __ldg(T.dense + rk);
+            if (!(e.y & kSkipSpecial)) {
+                from_root = false;
+                q = B;
+            }
+        }
+        if (from_root) e = __ldg(T.skip);
+        // walk on through skip entries inside the window, with at most walk_loads
+        // dependent table loads; a longer walk is deferred
+        bool defer = false;
+        for (int loads = 1;; loads++) {
+            if (e.y & kSkipSelfTerm) best = s;
+            const uint32_t L = e.y & kSkipLenMask;
+            const int need = L ? (int)L : 1;
+            if (q + need > wlim) {
+                defer = !ends;     // the window ran out before the text did
+                break;
+            }
+            const uint32_t win = window_at(ox0, ox1, ox2, ox3, j + q);
+            if (L) {
+                if ((win ^ e.x) & base_mask(L)) break;
+                q += (int)L;
+                s = e.z;
+                if (e.y & kSkipTargetTerm) best = s;
+            } else {
+                const uint32_t c = win & 3u;
+                if (!((e.w >> c) & 1u)) break;
+                s = (e.w >> kNodeFirstShift) + __popc(e.w & ((1u << c) - 1u));
+                q++;
+            }
+            if (loads >= walk_loads) {
+                defer = true;      // the tail kernel takes it from state s
+                break;
+            }
+            e = __ldg(T.skip + s);
+        }
+        if (defer) {
+            // long walk: finish it in the tail kernel (or here if the list is full)
+            const unsigned long long di = atomicAdd(K.defer_count, 1ull);
+            if ((int64_t)di < K.defer_cap) {
+                DeferItem it;
+                it.gp = gp;
+                it.s = s;
+                it.best = best;
+                it.q_set = (uint32_t)q | (set_index << 16);
+                it.span = (int32_t)min(end - gp, (int64_t)0x7FFFFFFF);
+                K.defer[di] = it;
+            } else {
+                emit_match<COMPACT>(K, gp, walk_global<PACKED>(T, text, invalid, end, gp, s, q, best));
+            }
+        } else if (best) {
+            emit_match<COMPACT>(K, gp, __ldg(T.out_id + best));
+        }
+    }
+}
+
 template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW>
 __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
 {
@@ -481,7 +664,6 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const DeviceTable &T = P.t;
     const int B = T.filter_b;
-    const uint32_t bmask = (uint32_t)((1ull << (2 * B)) - 1ull);
     const int S = P.stages;
     const int64_t n = P.n;
 
@@ -540,6 +722,15 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
 
     // ---------------- consumer warps ----------------
     const uint64_t pol = policy_evict_first();
+    Sink K;
+    K.out = P.out;
+    K.c_off = P.c_off;
+    K.c_ids = P.c_ids;
+    K.cap = P.cap;
+    K.count = P.count;
+    K.defer = P.defer;
+    K.defer_cap = P.defer_cap;
+    K.defer_count = P.defer_count;
     int k = 0;
     for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, k++) {
         const int st = k % S;
@@ -585,145 +776,10 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
         if (lane == 0) mbar_arrive(smem_addr(&empty[st]));   // this warp is done with the stage
         const uint32_t all = LW == 32 ? 0xFFFFFFFFu : ((1u << LW) - 1u);
         const uint32_t valid = rem >= LW ? all : (rem > 0 ? ((1u << rem) - 1u) : 0u);
-        const uint32_t fast = clear_runs(bad, B) & valid;   // the b-mer is readable
-
-        // Every offset: one filter bit for the b bases starting there. A clear bit
-        // means the walk ends before depth b with no pattern on the way: answer 0.
-        uint32_t pend = 0;
-#pragma unroll
-        for (int j = 0; j < LW; j++) {
-            const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
-            const uint32_t kmer = win & bmask;   // bases j .. j+b-1
-            const uint32_t word = FSMEM ? sf[kmer >> 5] : __ldg(T.filter + (kmer >> 5));
-            pend |= ((word >> (kmer & 31u)) & 1u) << j;
-        }
-        pend &= fast;
-        pend |= valid & ~fast;     // these walk from the root
-
-        if (!COMPACT && valid) {
-            if (valid == all) {
-                int32_t *o = P.out + gp0;
-                const int4 z = make_int4(0, 0, 0, 0);
-#pragma unroll
-                for (int v = 0; v < LW / 4; v++) st_global_v4_hint(o + 4 * v, z, pol);
-            } else {
-                for (int j = 0; j < LW; j++)
-                    if ((valid >> j) & 1u) P.out[gp0 + j] = 0;
-            }
-        }
-
-        // The zeros above were stored by the lane that owns each offset; a match found
-        // below is stored by whichever lane walks it. The warp barrier orders the
-        // first before the second.
-        __syncwarp();
-
-        // -------- walks that go on --------
-        // Spread them over the warp: item r of the warp (in lane order, then offset
-        // order) goes to lane r mod 32 in round r / 32. The owner's window comes by
-        // shuffle.
-        const uint32_t cnt = __popc(pend);
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-            if (lane >= d) incl += o;
-        }
-        const uint32_t excl = incl - cnt;
-        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        for (uint32_t r0 = 0; r0 < total; r0 += 32) {
-            const uint32_t r = r0 + lane;
-            // owner = the last lane whose first item is <= r
-            int owner = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const uint32_t e = __shfl_sync(0xFFFFFFFFu, excl, owner + step);
-                if (e <= r) owner += step;
-            }
-            const uint32_t om = __shfl_sync(0xFFFFFFFFu, pend, owner);
-            const uint32_t oe = __shfl_sync(0xFFFFFFFFu, excl, owner);
-            const uint32_t ofast = __shfl_sync(0xFFFFFFFFu, fast, owner);
-            const uint32_t ox0 = __shfl_sync(0xFFFFFFFFu, x0, owner);
-            const uint32_t ox1 = __shfl_sync(0xFFFFFFFFu, x1, owner);
-            const uint32_t ox2 = __shfl_sync(0xFFFFFFFFu, x2, owner);
-            const uint32_t ox3 = __shfl_sync(0xFFFFFFFFu, x3, owner);
-            const uint32_t obad_lo = __shfl_sync(0xFFFFFFFFu, (uint32_t)bad, owner);
-            const uint32_t obad_hi = __shfl_sync(0xFFFFFFFFu, (uint32_t)(bad >> 32), owner);
-            if (r >= total) continue;
-            // the (r - oe)-th set bit of the owner's mask (r - oe < popcount by construction)
-            uint32_t m = om;
-            for (uint32_t i = r - oe; i > 0; i--) m &= m - 1u;
-            const int j = (__ffs(m) - 1) & (LW - 1);
-            const int64_t gp = t * (int64_t)P.tile + warp * (32 * LW) + owner * LW + j;
-            const uint64_t badj = (((uint64_t)obad_hi << 32) | obad_lo) >> j;
-            // bases readable from the window; `ends` when the text (or the run of ACGT
-            // bytes) really stops there rather than the window
-            const int wlim = badj ? __ffsll((long long)badj) - 1 : 64 - j;
-            const bool ends = badj != 0;
-            uint32_t s = 0, best = 0;
-            int q = 0;
-            uint4 e;
-            bool from_root = true;
-            if ((ofast >> j) & 1u) {
-                const uint32_t kmer = window_at(ox0, ox1, ox2, ox3, j) & bmask;
-                const uint32_t widx = kmer >> 5;
-                const uint32_t word = FSMEM ? sf[widx] : __ldg(T.filter + widx);
-                const uint32_t base_rank = P.rank_smem ? (uint32_t)srank[widx]
-                                                       : (uint32_t)__ldg(reinterpret_cast<const RankT *>(T.rank) + widx);
-                const uint32_t rk = base_rank + __popc(word & ((1u << (kmer & 31u)) - 1u));
-                e = __ldg(T.dense + rk);
-                if (!(e.y & kSkipSpecial)) {
-                    from_root = false;
-                    q = B;
-                }
-            }
-            if (from_root) e = __ldg(T.skip);
-            // walk on through skip entries inside the window, with at most walk_loads
-            // dependent table loads; a longer walk is deferred
-            bool defer = false;
-            for (int loads = 1;; loads++) {
-                if (e.y & kSkipSelfTerm) best = s;
-                const uint32_t L = e.y & kSkipLenMask;
-                const int need = L ? (int)L : 1;
-                if (q + need > wlim) {
-                    defer = !ends;     // the window ran out before the text did
-                    break;
-                }
-                const uint32_t win = window_at(ox0, ox1, ox2, ox3, j + q);
-                if (L) {
-                    if ((win ^ e.x) & base_mask(L)) break;
-                    q += (int)L;
-                    s = e.z;
-                    if (e.y & kSkipTargetTerm) best = s;
-                } else {
-                    const uint32_t c = win & 3u;
-                    if (!((e.w >> c) & 1u)) break;
-                    s = (e.w >> kNodeFirstShift) + __popc(e.w & ((1u << c) - 1u));
-                    q++;
-                }
-                if (loads >= P.walk_loads) {
-                    defer = true;      // the tail kernel takes it from state s
-                    break;
-                }
-                e = __ldg(T.skip + s);
-            }
-            if (defer) {
-                // long walk: finish it in the tail kernel (or here if the list is full)
-                const unsigned long long di = atomicAdd(P.defer_count, 1ull);
-                if ((int64_t)di < P.defer_cap) {
-                    DeferItem it;
-                    it.gp = gp;
-                    it.s = s;
-                    it.best = best;
-                    it.q = q;
-                    it.pad = 0;
-                    P.defer[di] = it;
-                } else {
-                    emit_match<COMPACT>(P, gp, walk_global<PACKED>(T, P.text, n, gp, s, q, best));
-                }
-            } else if (best) {
-                emit_match<COMPACT>(P, gp, __ldg(T.out_id + best));
-            }
-        }
+        scan_lane_batch<PACKED, COMPACT, FSMEM, RANK16, LW>(T, K, sf, P.rank_smem ? (const void *)srank : nullptr,
+                                                            P.walk_loads, 0u, P.text, nullptr, n,
+                                                            t * (int64_t)P.tile + warp * (32 * LW), lane, x0, x1, x2,
+                                                            x3, bad, valid, true, pol);
     }
 }
 
@@ -735,7 +791,14 @@ __global__ void __launch_bounds__(256) tail_kernel(const ScanParams P)
     const int64_t m = min((int64_t)cnt, P.defer_cap);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         const DeferItem it = P.defer[i];
-        emit_match<COMPACT>(P, it.gp, walk_global<PACKED>(P.t, P.text, P.n, it.gp, it.s, it.q, it.best));
+        Sink K;
+        K.out = P.out;
+        K.c_off = P.c_off;
+        K.c_ids = P.c_ids;
+        K.cap = P.cap;
+        K.count = P.count;
+        emit_match<COMPACT>(K, it.gp, walk_global<PACKED>(P.t, P.text, nullptr, it.gp + it.span, it.gp, it.s,
+                                                          (int)(it.q_set & 0xFFFFu), it.best));
     }
 }
 
@@ -921,6 +984,236 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
 }
 
 size_t defer_item_bytes() { return sizeof(DeferItem); }
+
+// ---------------------------------------------------------------------------
+// Batched scan: many reads of uneven length, each against its own table, in one
+// persistent launch (plus the pack, plan and tail kernels around it).
+//   pack_bits_kernel    ASCII reads -> 2-bit words + one invalid bit per base
+//   plan_kernel         reads -> first work item of each read (512 offsets per item)
+//   batched_scan_kernel warps take items from a counter; each item runs the same
+//                       per-warp filter test and skip walks as kernel 2, with its
+//                       read's table and every walk bounded by its read's end
+//   batched_tail_kernel deferred long walks, with the table recorded in each item
+// ---------------------------------------------------------------------------
+
+constexpr int kBatchItem = 512;   // offsets per work item (32 lanes x 16)
+
+struct BatchParams {
+    const DeviceTable *sets;
+    int32_t n_sets;
+    const uint32_t *packed;
+    const uint32_t *invalid;
+    int64_t n;
+    const int64_t *read_off;
+    const int32_t *read_set;
+    int32_t n_reads;
+    const int64_t *item_start;
+    unsigned long long *item_next;
+    int32_t *out;
+    DeferItem *defer;
+    int64_t defer_cap;
+    unsigned long long *defer_count;
+    int32_t walk_loads;
+};
+
+__global__ void pack_bits_kernel(const uint8_t *__restrict__ text, int64_t len, uint32_t *__restrict__ packed,
+                                 uint32_t *__restrict__ invalid)
+{
+    const int64_t n_bw = (len + 31) >> 5;
+    const int64_t n_words = (len + 15) >> 4;
+    const bool aligned = ((uintptr_t)text & 15u) == 0;
+    for (int64_t bw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; bw < n_bw; bw += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t inv = 0;
+        for (int h = 0; h < 2; h++) {
+            const int64_t b0 = (bw << 5) + 16 * h;
+            uint32_t word = 0, badm = 0;
+            if (aligned && b0 + 16 <= len) {
+                word = pack16(__ldg(reinterpret_cast<const uint4 *>(text + b0)), &badm);
+            } else {
+                for (int i = 0; i < 16; i++) {
+                    const int c = b0 + i < len ? base_code_or_neg(text[b0 + i]) : -1;
+                    if (c < 0) badm |= 1u << i;
+                    else word |= (uint32_t)c << (2 * i);
+                }
+            }
+            if (2 * bw + h < n_words) packed[2 * bw + h] = word;
+            inv |= badm << (16 * h);
+        }
+        invalid[bw] = inv;
+    }
+}
+
+__device__ __forceinline__ void read_bounds(const int64_t *read_off, int32_t r, int64_t n, int64_t *rs, int64_t *re)
+{
+    const int64_t a = min(max(read_off[r], (int64_t)0), n);
+    const int64_t b = min(max(read_off[r + 1], a), n);
+    *rs = a;
+    *re = b;
+}
+
+// One CTA: exclusive prefix of the number of work items per read.
+__global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ read_off, int32_t n_reads, int64_t n,
+                                                    int64_t *__restrict__ item_start)
+{
+    __shared__ int64_t warp_sum[32];
+    __shared__ int64_t carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n_reads; base += blockDim.x) {
+        const int64_t r = base + tid;
+        int64_t v = 0;
+        if (r < n_reads) {
+            int64_t rs, re;
+            read_bounds(read_off, (int32_t)r, n, &rs, &re);
+            v = (re - rs + kBatchItem - 1) / kBatchItem;
+        }
+        int64_t incl = v;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t ws = lane < (int)(blockDim.x >> 5) ? warp_sum[lane] : 0;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t o = __shfl_up_sync(0xFFFFFFFFu, ws, d);
+                if (lane >= d) ws += o;
+            }
+            warp_sum[lane] = ws;   // inclusive over warps
+        }
+        __syncthreads();
+        const int64_t before = (warp ? warp_sum[warp - 1] : 0) + incl - v;
+        if (r < n_reads) item_start[r] = carry + before;
+        __syncthreads();
+        if (tid == 0) carry += warp_sum[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (tid == 0) item_start[n_reads] = carry;
+}
+
+__global__ void __launch_bounds__(256) batched_scan_kernel(const BatchParams P)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t total = P.item_start[P.n_reads];
+    const uint64_t pol = policy_evict_first();
+    Sink K{};
+    K.out = P.out;
+    K.defer = P.defer;
+    K.defer_cap = P.defer_cap;
+    K.defer_count = P.defer_count;
+    const int64_t n_words = (P.n + 15) >> 4;
+    const int64_t n_bw = (P.n + 31) >> 5;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(P.item_next, 1ull);
+        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        if ((int64_t)it >= total) break;
+        // the read holding item `it`: the last r with item_start[r] <= it
+        int32_t lo = 0, hi = P.n_reads - 1;
+        while (lo < hi) {
+            const int32_t mid = (int32_t)(((int64_t)lo + hi + 1) >> 1);
+            if (P.item_start[mid] <= (int64_t)it) lo = mid;
+            else hi = mid - 1;
+        }
+        int64_t rs, re;
+        read_bounds(P.read_off, lo, P.n, &rs, &re);
+        const int64_t base = rs + ((int64_t)it - P.item_start[lo]) * kBatchItem;
+        const int64_t item_end = min(base + kBatchItem, re);
+        const int32_t set = P.read_set[lo];
+        if (set < 0 || set >= P.n_sets) {
+            if (lane == 0) record_error(P.sets[0].status, PFAC_ERR_INVALID_ARG);
+            continue;
+        }
+        const DeviceTable T = P.sets[set];
+        // this lane's 16 offsets and the 64 bases from its first one
+        const int64_t p0 = base + 16 * lane;
+        const int64_t wi = p0 >> 4;
+        const uint32_t sh = (uint32_t)(p0 & 15) * 2;
+        uint32_t w[5];
+#pragma unroll
+        for (int k = 0; k < 5; k++) w[k] = (wi + k < n_words) ? __ldg(P.packed + wi + k) : 0u;
+        const uint32_t x0 = __funnelshift_r(w[0], w[1], sh), x1 = __funnelshift_r(w[1], w[2], sh);
+        const uint32_t x2 = __funnelshift_r(w[2], w[3], sh), x3 = __funnelshift_r(w[3], w[4], sh);
+        const int64_t bi = p0 >> 5;
+        const uint32_t sb = (uint32_t)(p0 & 31);
+        uint32_t iv[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) iv[k] = (bi + k < n_bw) ? __ldg(P.invalid + bi + k) : 0xFFFFFFFFu;
+        uint64_t bad = ((uint64_t)__funnelshift_r(iv[1], iv[2], sb) << 32) | __funnelshift_r(iv[0], iv[1], sb);
+        const int64_t rem_read = re - p0;   // walks stop at the read's end
+        if (rem_read < 64) bad |= rem_read > 0 ? (~0ull << rem_read) : ~0ull;
+        const int64_t rem_item = item_end - p0;
+        const uint32_t valid = rem_item >= 16 ? 0xFFFFu : (rem_item > 0 ? ((1u << rem_item) - 1u) : 0u);
+        const bool vec_ok = (((uintptr_t)(P.out + base)) & 15u) == 0;
+        scan_lane_batch<true, false, false, true, 16>(T, K, nullptr, nullptr, P.walk_loads, (uint32_t)set, P.packed,
+                                                      P.invalid, re, base, lane, x0, x1, x2, x3, bad, valid, vec_ok,
+                                                      pol);
+    }
+}
+
+__global__ void __launch_bounds__(256) batched_tail_kernel(const BatchParams P)
+{
+    const unsigned long long cnt = *P.defer_count;
+    const int64_t m = min((int64_t)cnt, P.defer_cap);
+    Sink K{};
+    K.out = P.out;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const DeferItem it = P.defer[i];
+        const DeviceTable T = P.sets[it.q_set >> 16];
+        emit_match<false>(K, it.gp, walk_global<true>(T, P.packed, P.invalid, it.gp + it.span, it.gp, it.s,
+                                                      (int)(it.q_set & 0xFFFFu), it.best));
+    }
+}
+
+int64_t batch_scratch_bytes(int64_t n, int32_t n_reads, int64_t defer_cap)
+{
+    const int64_t words = (n + 15) / 16, bw = (n + 31) / 32;
+    return 256 + ((words * 4 + 255) & ~255LL) + (((bw + 1) * 4 + 255) & ~255LL) +
+           ((((int64_t)n_reads + 1) * 8 + 255) & ~255LL) + defer_cap * (int64_t)sizeof(DeferItem);
+}
+
+int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *texts, int64_t n, const int64_t *read_off,
+                   const int32_t *read_set, int32_t n_reads, int32_t *out, void *scratch, int64_t defer_cap,
+                   int32_t walk_loads, cudaStream_t st, const DeviceProps &dp)
+{
+    if (n == 0 || n_reads == 0) return PFAC_OK;
+    uint8_t *p = (uint8_t *)scratch;
+    unsigned long long *counters = (unsigned long long *)p;       // [0] next item, [1] deferred walks
+    p += 256;
+    const int64_t words = (n + 15) / 16, bw = (n + 31) / 32;
+    uint32_t *packed = (uint32_t *)p;
+    p += (words * 4 + 255) & ~255LL;
+    uint32_t *invalid = (uint32_t *)p;
+    p += ((bw + 1) * 4 + 255) & ~255LL;
+    int64_t *item_start = (int64_t *)p;
+    p += ((((int64_t)n_reads + 1) * 8) + 255) & ~255LL;
+    DeferItem *defer = (DeferItem *)p;
+    if (cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
+    const int pack_blocks = (int)std::min<int64_t>((bw + 255) / 256, (int64_t)dp.num_sms * 16);
+    pack_bits_kernel<<<std::max(1, pack_blocks), 256, 0, st>>>(texts, n, packed, invalid);
+    plan_kernel<<<1, 1024, 0, st>>>(read_off, n_reads, n, item_start);
+    BatchParams P{};
+    P.sets = d_sets;
+    P.n_sets = n_sets;
+    P.packed = packed;
+    P.invalid = invalid;
+    P.n = n;
+    P.read_off = read_off;
+    P.read_set = read_set;
+    P.n_reads = n_reads;
+    P.item_start = item_start;
+    P.item_next = counters;
+    P.out = out;
+    P.defer = defer;
+    P.defer_cap = defer_cap;
+    P.defer_count = counters + 1;
+    P.walk_loads = walk_loads > 0 ? walk_loads : 2;
+    batched_scan_kernel<<<dp.num_sms * 4, 256, 0, st>>>(P);
+    batched_tail_kernel<<<dp.num_sms * 4, 256, 0, st>>>(P);
+    return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
+}
 static_assert(sizeof(DeferItem) == kDeferItemBytes, "deferred-walk record size");
 
 // ---------------------------------------------------------------------------
