@@ -1,0 +1,183 @@
+"""A serving loop for the scan: requests arrive over time, each naming a resident
+table and carrying a DNA text; the server batches whatever has arrived into one
+``pfac_match_batched`` pass per slot and keeps several slots in flight.
+
+* Tables stay on the device for the server's lifetime (built once).
+* Admission by free device memory: a request is admitted only while the bytes of
+  all batches in flight (text in, ids out) stay under a budget taken from the free
+  HBM at start-up (and within one slot's capacity).
+* Continuous batching: whenever a slot is free, everything admitted so far goes into
+  its next batch, so requests that arrive while other batches are on the GPU join
+  the next one; each slot has its own stream, pinned buffers and device buffers,
+  so the copies and scans of different batches overlap.
+* Latency of a request = time from its arrival to the moment its ids are on the host.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _binding as b
+
+
+@dataclass
+class Request:
+    rid: int
+    set_id: int
+    text: np.ndarray          # ASCII uint8
+    arrival: float            # seconds from the start of the run
+
+
+@dataclass
+class _Slot:
+    stream: object
+    h_in: object              # pinned uint8
+    h_out: object             # pinned int32
+    d_in: object
+    d_out: object
+    d_offs: object
+    d_sets: object
+    event: object = None
+    requests: list = field(default_factory=list)
+    starts: list = field(default_factory=list)
+    bytes: int = 0
+
+
+class Server:
+    def __init__(self, tables, slot_bases: int = 1 << 24, n_slots: int = 3, max_reads: int = 4096,
+                 hbm_fraction: float = 0.5, keep_results: bool = False):
+        import torch
+        self.torch = torch
+        self.tables = list(tables)
+        self.handles = [t.h for t in self.tables]
+        self.slot_bases = int(slot_bases)
+        self.max_reads = int(max_reads)
+        free, _total = torch.cuda.mem_get_info()
+        # device bytes one base costs while in flight: its byte in, its int32 id out
+        self.budget = int(free * hbm_fraction)
+        self.keep_results = keep_results
+        self.slots = []
+        for _ in range(n_slots):
+            self.slots.append(_Slot(
+                stream=torch.cuda.Stream(),
+                h_in=torch.empty(self.slot_bases, dtype=torch.uint8).pin_memory(),
+                h_out=torch.empty(self.slot_bases, dtype=torch.int32).pin_memory(),
+                d_in=torch.empty(self.slot_bases, dtype=torch.uint8, device="cuda"),
+                d_out=torch.empty(self.slot_bases, dtype=torch.int32, device="cuda"),
+                d_offs=torch.empty(self.max_reads + 1, dtype=torch.int64, device="cuda"),
+                d_sets=torch.empty(self.max_reads, dtype=torch.int32, device="cuda")))
+        # first batched call per stream: uploads the descriptors and allocates scratch
+        for sl in self.slots:
+            with torch.cuda.stream(sl.stream):
+                sl.d_in[:1].fill_(ord("A"))
+                offs = torch.tensor([0, 1], dtype=torch.int64, device="cuda")
+                b.pfac_match_batched(self.handles, sl.d_in[:1], offs, sl.d_sets[:1].zero_(), sl.d_out[:1],
+                                     sl.stream)
+            sl.stream.synchronize()
+
+    @staticmethod
+    def request_bytes(req: Request) -> int:
+        return 5 * int(req.text.shape[0])
+
+    def _launch(self, sl: _Slot, batch: list):
+        torch = self.torch
+        lens = np.array([r.text.shape[0] for r in batch], dtype=np.int64)
+        offs = np.zeros(len(batch) + 1, dtype=np.int64)
+        np.cumsum(lens, out=offs[1:])
+        total = int(offs[-1])
+        hin = sl.h_in.numpy()
+        for r, o in zip(batch, offs[:-1]):
+            hin[o:o + r.text.shape[0]] = r.text
+        sets = np.array([r.set_id for r in batch], dtype=np.int32)
+        with torch.cuda.stream(sl.stream):
+            sl.d_in[:total].copy_(sl.h_in[:total], non_blocking=True)
+            sl.d_offs[:len(batch) + 1].copy_(torch.from_numpy(offs), non_blocking=True)
+            sl.d_sets[:len(batch)].copy_(torch.from_numpy(sets), non_blocking=True)
+            b.pfac_match_batched(self.handles, sl.d_in[:total], sl.d_offs[:len(batch) + 1],
+                                 sl.d_sets[:len(batch)], sl.d_out[:total], sl.stream)
+            sl.h_out[:total].copy_(sl.d_out[:total], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(sl.stream)
+        sl.event = ev
+        sl.requests = batch
+        sl.starts = offs
+        sl.bytes = 5 * total
+
+    def run(self, requests, realtime: bool = True):
+        """Serve `requests` (sorted by arrival). Returns (per-request latency in s,
+        results by request id if keep_results, statistics)."""
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        waiting = deque()
+        in_flight = 0
+        latency = {}
+        results = {}
+        matches = 0
+        batches = 0
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        n_total = len(pending)
+        done = 0
+        while done < n_total:
+            t = now()
+            # arrivals (all at once when not in real time)
+            while pending and (not realtime or pending[0].arrival <= t):
+                waiting.append(pending.popleft())
+            # completions
+            progressed = False
+            for sl in self.slots:
+                if sl.event is not None and sl.event.query():
+                    tdone = now()
+                    out = sl.h_out.numpy()
+                    for r, o in zip(sl.requests, sl.starts[:-1]):
+                        latency[r.rid] = tdone - (r.arrival if realtime else 0.0)
+                        if self.keep_results:
+                            ids = out[o:o + r.text.shape[0]]
+                            matches += int(np.count_nonzero(ids))
+                            results[r.rid] = ids.copy()
+                    in_flight -= sl.bytes
+                    done += len(sl.requests)
+                    sl.event, sl.requests, sl.bytes = None, [], 0
+                    progressed = True
+            # admission and batching into free slots
+            for sl in self.slots:
+                if sl.event is not None or not waiting:
+                    continue
+                batch, bases = [], 0
+                while waiting and len(batch) < self.max_reads:
+                    r = waiting[0]
+                    n = int(r.text.shape[0])
+                    if n > self.slot_bases:
+                        raise ValueError(f"request {r.rid} ({n} bases) exceeds the slot capacity")
+                    if bases + n > self.slot_bases:
+                        break
+                    if in_flight + 5 * (bases + n) > self.budget and (in_flight or batch):
+                        break        # admitted only when device memory frees up
+                    batch.append(waiting.popleft())
+                    bases += n
+                if batch:
+                    self._launch(sl, batch)
+                    in_flight += sl.bytes
+                    batches += 1
+                    progressed = True
+            if not progressed:
+                # nothing to do until the next arrival or completion
+                nxt = pending[0].arrival - now() if (pending and realtime) else 0.0
+                time.sleep(min(max(nxt, 0.0), 0.0002) if nxt > 0 else 0.00005)
+        wall = now()
+        lat = np.array([latency[r.rid] for r in requests]) if requests else np.zeros(0)
+        bases = int(sum(r.text.shape[0] for r in requests))
+        stats = {"requests": n_total, "batches": batches, "bases": bases, "wall_s": wall,
+                 "gbases_s": bases / wall / 1e9 if wall > 0 else 0.0,
+                 "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
+                 "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
+                 "matches": matches if self.keep_results else None}
+        return lat, results, stats
+
+
+def requests_from_stream(stream, limit: int | None = None):
+    """Request objects for a datagen RequestStream."""
+    n = len(stream.arrivals) if limit is None else min(limit, len(stream.arrivals))
+    return [Request(i, int(stream.set_id[i]), stream.text(i), float(stream.arrivals[i])) for i in range(n)]
