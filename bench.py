@@ -112,7 +112,7 @@ def kernel_source_hash():
 def profiled_traffic():
     """DRAM bytes per launch of the scan kernel from the committed ncu summary, if it
     was taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "tiled_kernel_genome_scan.md")
+    p = os.path.join(ROOT, "profiles", "scan_kernel_genome_scan.md")
     try:
         txt = open(p).read()
     except OSError:
@@ -159,6 +159,76 @@ def cpu_baseline(w, got_prefix: np.ndarray | None, seconds: float = 8.0):
     return out
 
 
+def batched_measure(steps: int):
+    """The batched workload: 4,096 reads (log-normal lengths, median 1,500) against 64
+    resident tables; one captured CUDA graph per batch vs one launch per read."""
+    import torch
+    from paper_1811_10498_gb300 import _binding as b
+    from paper_1811_10498_gb300 import datagen
+    from paper_1811_10498_gb300.batched import BatchedScanner, scan_per_read
+    w = datagen.read_batch(seed=4)
+    t0 = time.perf_counter()
+    tables = [b.Table(s) for s in w.sets]
+    build_s = time.perf_counter() - t0
+    n = int(w.reads.size)
+    sc = BatchedScanner(tables, max_bases=n, max_reads=len(w.read_set), graph=True)
+    sc.load(w.reads, w.read_offsets, w.read_set)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        sc.run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        with torch.cuda.stream(sc.stream):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(sc.stream)
+        sc.run()
+        with torch.cuda.stream(sc.stream):
+            e1.record(sc.stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    batched_out = sc.out[:n].clone()
+    ms = statistics.median(times)
+    d_text = sc.texts[:n]
+    out = torch.zeros(n, dtype=torch.int32, device="cuda")
+    scan_per_read(tables, d_text, w.read_offsets, w.read_set, out)      # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    scan_per_read(tables, d_text, w.read_offsets, w.read_set, out)
+    e1.record()
+    torch.cuda.synchronize()
+    per_ms = e0.elapsed_time(e1)
+    same = bool(torch.equal(out, batched_out))
+    for t in tables:
+        t.close()
+    return {"workload": w.name, "bases": n, "reads": int(len(w.read_set)), "tables": len(w.sets),
+            "table_build_s": build_s, "graph_replay_ms": ms, "gbases_s": n / ms / 1e6,
+            "per_read_launches_ms": per_ms, "per_read_gbases_s": n / per_ms / 1e6,
+            "batched_vs_per_read": per_ms / ms, "same_output": same,
+            "launches_per_batch": 4, "launches_per_read_pass": 2 * int(len(w.read_set))}
+
+
+def serving_measure(seconds: float):
+    """The serving workload: Poisson arrivals at 2,000 requests/s, 16 resident tables of
+    1,000-200,000 patterns, texts of 1 kb-10 Mb; p50/p99 latency and throughput."""
+    from paper_1811_10498_gb300 import _binding as b
+    from paper_1811_10498_gb300 import datagen
+    from paper_1811_10498_gb300.serving import Server, requests_from_stream
+    st = datagen.request_stream(seed=5, duration=seconds)
+    tables = [b.Table(s) for s in st.sets]
+    srv = Server(tables, slot_bases=1 << 24, n_slots=3, max_reads=4096)
+    reqs = requests_from_stream(st)
+    _, _, stats = srv.run(reqs, realtime=True)
+    stats["workload"] = st.name
+    stats["offered_gbases_s"] = stats["bases"] / seconds / 1e9
+    for t in tables:
+        t.close()
+    return stats
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores: each step scans a bounded sample."""
     rank = int(os.environ.get("RANK", "0"))
@@ -199,13 +269,16 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-bases", type=int, default=N_BASES)
     ap.add_argument("--n-patterns", type=int, default=N_PATTERNS)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -256,14 +329,13 @@ def main():
     def step():
         b.pfac_match_packed(table.h, packed, n, out, stream)
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
-
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(local) as clocks:
+    with ClockSampler(local) as clocks:      # samples the warm-up and the timed steps
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -293,8 +365,8 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profiled_traffic(), "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": BYTES_PER_BASE * n,
-                "kernel": "tiled_kernel<packed> (kernel 2)" if b.pfac_get_config(table.h, n)["kernel"] == 2
-                else "walk_rows_kernel<packed> (kernel 1)"}
+                "kernel": "scan_kernel<packed> (kernel 2; plus tail_kernel, both inside each step)"
+                if b.pfac_get_config(table.h, n)["kernel"] == 2 else "walk_rows_kernel<packed> (kernel 1)"}
 
     # end to end through the public API with host buffers: H2D of the ASCII text,
     # pack, scan, D2H of the ids, every step.
@@ -334,13 +406,17 @@ def main():
                        "n_patterns": args.n_patterns, "n_states": info["n_states"], "filter_b": info["filter_b"],
                        "l2": "flushed between timed steps (memset of 4x L2 outside the events)",
                        "input_resident": "packed text in HBM"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
             "clocks": clocks.summary(),
             "wall_s_timed_region": wall,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "extra": {"pack_gbases_s": pack_gbs, "build_s": build_s,
                       "frac_of_roofline_gbases": value / world / (peak / BYTES_PER_BASE)},
         }
+        if not args.no_batched:
+            line["batched"] = batched_measure(20)
+        if not args.no_serving:
+            line["serving"] = serving_measure(args.serve_seconds)
         print(json.dumps(line), flush=True)
     table.close()
     if world > 1:
