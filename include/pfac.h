@@ -77,7 +77,8 @@ pfac_handle pfac_build(const char *const *patterns, const int32_t *lengths, int3
 typedef struct {
     int32_t host_only;  /* 1: build the tables on the host only (no device copy; the
                            scan calls reject the handle with PFAC_ERR_HOST_ONLY). */
-    int32_t filter_b;   /* order of the prefix filter: 0 = automatic (10), -1 = none,
+    int32_t filter_b;   /* order of the prefix filter: 0 = automatic (about
+                           log4(n) + 2.2, between 6 and 12), -1 = none,
                            1..12 = that order. One bit per b-mer, clear when a walk over
                            those b bases ends with no pattern on the way, so the answer
                            at that offset is 0 whatever follows (an exact property of

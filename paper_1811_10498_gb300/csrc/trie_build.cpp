@@ -191,7 +191,12 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
         // a pattern ends on the walk before it stops (special entry). A prefix of d
         // symbols whose walk stops at symbol d fixes every b-mer that starts with it: the
         // indices congruent to the prefix code modulo 4^(d+1).
-        const int32_t b = filter_b_opt == 0 ? 10 : (filter_b_opt < 0 ? 0 : filter_b_opt);
+        // Automatic order: about log4(patterns) + 2.2, so that a few percent of the
+        // b-mers of a random text pass (a b-mer passes when it is a path of the trie,
+        // about min(1, patterns / 4^b) of them), between 6 and 12.
+        const double auto_b = std::ceil(std::log((double)n) / std::log(4.0) + 2.2);
+        const int32_t b = filter_b_opt == 0 ? (int32_t)std::min(12.0, std::max(6.0, auto_b))
+                                            : (filter_b_opt < 0 ? 0 : filter_b_opt);
         if (b > 0 && !T.skip.empty()) {
             T.filter_b = b;
             const size_t E = (size_t)1 << (2 * b);

@@ -48,7 +48,9 @@ class _Slot:
 
 class Server:
     def __init__(self, tables, slot_bases: int = 1 << 24, n_slots: int = 3, max_reads: int = 4096,
-                 hbm_fraction: float = 0.5, keep_results: bool = False):
+                 hbm_fraction: float = 0.5, keep_results=False):
+        """keep_results: True to keep every request's ids on the host, or a set of request
+        ids to keep only those."""
         import torch
         self.torch = torch
         self.tables = list(tables)
@@ -133,7 +135,7 @@ class Server:
                     out = sl.h_out.numpy()
                     for r, o in zip(sl.requests, sl.starts[:-1]):
                         latency[r.rid] = tdone - (r.arrival if realtime else 0.0)
-                        if self.keep_results:
+                        if self.keep_results is True or (self.keep_results and r.rid in self.keep_results):
                             ids = out[o:o + r.text.shape[0]]
                             matches += int(np.count_nonzero(ids))
                             results[r.rid] = ids.copy()
@@ -173,7 +175,7 @@ class Server:
                  "gbases_s": bases / wall / 1e9 if wall > 0 else 0.0,
                  "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
                  "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
-                 "matches": matches if self.keep_results else None}
+                 "matches": matches if self.keep_results is True else None}
         return lat, results, stats
 
 

@@ -1,0 +1,111 @@
+"""Full-size workloads, in the launch configuration the benchmark times, against the CPU
+oracle (complete comparisons where the oracle is fast enough on the host's cores,
+otherwise every match plus a sample of offsets computed one by one)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import first_diff, host_threads, require_cuda, to_dev
+from paper_1811_10498_gb300 import _binding as b
+from paper_1811_10498_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    require_cuda()
+
+
+def scan_packed(table, text):
+    import torch
+    d = to_dev(text)
+    packed, status, _ = b.pack(d)
+    out = torch.empty(text.size, dtype=torch.int32, device="cuda")
+    b.pfac_match_packed(table.h, packed, text.size, out)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    del d
+    return packed, out
+
+
+def test_small_workload_full():
+    """1,000,000 uniform bases, 1,000 patterns of 8-32, ASCII input."""
+    w = datagen.small_scan()
+    want = oracle.Trie((w.blob, w.offsets)).scan(w.text)
+    t = b.Table((w.blob, w.offsets))
+    got = t.match(to_dev(w.text)).cpu().numpy()
+    assert np.array_equal(got, want), first_diff(got, want)
+
+
+def test_genome_scale_full():
+    """256 Mi bases, 20,000 patterns: the benchmark's workload, compared at every offset."""
+    w = datagen.genome_scan()
+    t = b.Table((w.blob, w.offsets))
+    _, out = scan_packed(t, w.text)
+    got = out.cpu().numpy()
+    want = oracle.Trie((w.blob, w.offsets)).scan_threads(w.text, host_threads())
+    assert np.array_equal(got, want), first_diff(got, want)
+    assert (want != 0).sum() > 10_000
+
+
+@pytest.mark.slow
+def test_large_dictionary_full():
+    """1 Gi bases, 1,000,000 patterns of 16-64: dense ids at every offset and the
+    compacted match list."""
+    import torch
+    w = datagen.large_dict_scan()
+    t = b.Table((w.blob, w.offsets))
+    packed, out = scan_packed(t, w.text)
+    got = out.cpu().numpy()
+    del out
+    want = oracle.Trie((w.blob, w.offsets)).scan_threads(w.text, host_threads())
+    assert np.array_equal(got, want), first_diff(got, want)
+    offs_w, ids_w = oracle.compact(want)
+    cap = offs_w.size + 1024
+    d_off = torch.empty(cap, dtype=torch.int64, device="cuda")
+    d_ids = torch.empty(cap, dtype=torch.int32, device="cuda")
+    d_cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    b.pfac_match_compact(t.h, packed, w.text.size, d_off, d_ids, d_cnt)
+    torch.cuda.synchronize()
+    c = int(d_cnt.item())
+    assert c == offs_w.size
+    o = d_off[:c].cpu().numpy()
+    i = d_ids[:c].cpu().numpy()
+    order = np.argsort(o)
+    assert np.array_equal(o[order], offs_w) and np.array_equal(i[order], ids_w)
+
+
+def test_batched_workload_full():
+    """4,096 reads against 64 resident tables, as one batched pass."""
+    import torch
+    w = datagen.read_batch()
+    want = oracle.pfac_scan_reads(w.reads, w.read_offsets, w.read_set, w.sets)
+    tables = [b.Table(s) for s in w.sets]
+    out = torch.full((w.reads.size,), -9, dtype=torch.int32, device="cuda")
+    b.pfac_match_batched([t.h for t in tables], to_dev(w.reads), to_dev(w.read_offsets),
+                         to_dev(w.read_set), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.array_equal(got, want), first_diff(got, want)
+
+
+def test_serving_workload_full_sampled():
+    """The full request stream (2,000 requests/s for 1 s, texts up to 10 Mb) through the
+    server; 60 requests spread over the run are checked against the oracle."""
+    from paper_1811_10498_gb300.serving import Server, requests_from_stream
+    st = datagen.request_stream(seed=5, duration=1.0)
+    reqs = requests_from_stream(st)
+    tables = [b.Table(s) for s in st.sets]
+    check = set(range(0, len(reqs), max(1, len(reqs) // 60)))
+
+    srv = Server(tables, slot_bases=1 << 24, n_slots=3, max_reads=4096, keep_results=check)
+    _, results, stats = srv.run(reqs, realtime=True)
+    assert stats["requests"] == len(reqs)
+    tries = {}
+    for rid in sorted(check):
+        r = reqs[rid]
+        if r.set_id not in tries:
+            tries[r.set_id] = oracle.Trie(st.sets[r.set_id])
+        want = tries[r.set_id].scan_threads(r.text, host_threads())
+        assert np.array_equal(results[rid], want), rid

@@ -82,7 +82,7 @@ def test_random_sets(seed):
 def test_small_workload_set():
     w = datagen.small_scan(n_bases=100_000)
     info = check_same_trie((w.blob, w.offsets))
-    assert info["has_skip"] == 1 and info["filter_b"] == 10
+    assert info["has_skip"] == 1 and info["filter_b"] == 8
 
 
 def reference_shortcuts(go, term, b):
