@@ -328,12 +328,17 @@ struct ScanParams {
     int32_t stage_units;         // packed words or ASCII bytes per stage
     int32_t rank_smem;           // rank index copied into shared memory
     int32_t walk_loads;          // dependent table loads a walk may take before it is deferred
-    uint32_t off_filter, off_rank, off_stage, stage_bytes;
+    uint32_t off_filter, off_rank, off_bar, off_queue, off_stage, stage_bytes;
     int64_t timeout_ns;
 };
 
 constexpr int kMaxStages = 8;
 constexpr uint32_t kBarBytes = 256;   // full[8], empty[8], abort flag
+// Packed text: offsets that pass the filter wait in a per-warp ring of kQueue entries
+// until a full warp of them can be walked together. An entry is the offset coded as
+// (tile round of the CTA) << kRelBits | (offset within the tile).
+constexpr uint32_t kQueue = 64;
+constexpr int kRelBits = 15;
 
 // Wait for an mbarrier phase, giving up after limit_ns or when another warp of the
 // CTA has raised the abort flag. Returns false if it gave up.
@@ -355,6 +360,25 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, int
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Shared-memory loads the compiler keeps in program order with the other asm
+// statements (the stage words, read before the stage is released).
+__device__ __forceinline__ uint32_t lds_u32(const void *p)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint4 lds_v4(const void *p)
+{
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(smem_addr(p))
+                 : "memory");
+    return v;
 }
 
 __device__ __forceinline__ void st_global_v4_hint(int32_t *p, int4 v, uint64_t pol)
@@ -488,12 +512,153 @@ __device__ __forceinline__ uint32_t window_at(uint32_t x0, uint32_t x1, uint32_t
     return __funnelshift_r(lo, hi, (uint32_t)(p & 15) * 2);
 }
 
+// Prefix-filter bits of a lane's LW offsets: bit j is the filter bit of the b bases
+// from offset j (window bases j .. j+b-1; x0, x1, x2 hold window bases 0 .. 47). A
+// clear bit means the walk from offset j ends before depth b with no pattern on the
+// way. With the filter at shared-memory offset 0 and b >= 3, the byte address of a
+// filter word is the window shifted and masked, and the bit index is the window's low
+// five bits, which a rotate uses as they are.
+template <bool FSMEM, int LW>
+__device__ __forceinline__ uint32_t filter_bits(const DeviceTable &T, const uint32_t *sf, uint32_t x0, uint32_t x1,
+                                                uint32_t x2, uint32_t bmask)
+{
+    uint32_t pend = 0;
+    if (FSMEM && bmask >= 31u) {
+        const uint32_t amask = (bmask >> 3) & ~3u;
+        const uint8_t *fb = reinterpret_cast<const uint8_t *>(sf);
+#pragma unroll
+        for (int j = 0; j < LW; j++) {
+            const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
+            const uint32_t word = *reinterpret_cast<const uint32_t *>(fb + ((win >> 3) & amask));
+            pend |= (__funnelshift_r(word, word, win) & 1u) << j;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < LW; j++) {
+            const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
+            const uint32_t kmer = win & bmask;
+            const uint32_t word = FSMEM ? sf[kmer >> 5] : __ldg(T.filter + (kmer >> 5));
+            pend |= ((word >> (kmer & 31u)) & 1u) << j;
+        }
+    }
+    return pend;
+}
+
+// Zeros for a warp-batch's valid offsets. Any lane may store any of the warp's zeros.
+// When the whole batch is valid its 32*LW outputs are contiguous from warp_base, and
+// each 16-byte store instruction covers 512 contiguous bytes (lane l at warp_base +
+// 4l + 128v): full sectors, where a lane writing its own offsets would leave every
+// sector half-written by two instructions.
+template <int LW>
+__device__ __forceinline__ void zero_batch(const Sink &K, int64_t warp_base, int lane, uint32_t valid, bool vec_ok,
+                                           uint64_t pol)
+{
+    const uint32_t all = LW == 32 ? 0xFFFFFFFFu : ((1u << LW) - 1u);
+    const int64_t gp0 = warp_base + (int64_t)lane * LW;
+    const int4 z = make_int4(0, 0, 0, 0);
+    if (__all_sync(0xFFFFFFFFu, vec_ok && valid == all)) {
+        int32_t *o = K.out + warp_base + 4 * lane;
+#pragma unroll
+        for (int v = 0; v < LW / 4; v++) st_global_v4_hint(o + 128 * v, z, pol);
+    } else if (vec_ok && valid == all) {
+        int32_t *o = K.out + gp0;
+#pragma unroll
+        for (int v = 0; v < LW / 4; v++) st_global_v4_hint(o + 4 * v, z, pol);
+    } else if (valid) {
+        for (int j = 0; j < LW; j++)
+            if ((valid >> j) & 1u) K.out[gp0 + j] = 0;
+    }
+}
+
+// The walk from one offset gp that passed the filter (or could not be tested). The
+// text from gp is window bases j, j+1, ... of x0..x3 (64 bases), of which wlim can be
+// read; `ends` when the text (or the run of readable bases) really stops there rather
+// than the window. `fast`: the b bases from gp are readable, so the walk starts at the
+// dense entry of their b-mer (unless that entry is marked special) at depth b; else at
+// the root. It goes on through skip entries inside the window with at most walk_loads
+// dependent table loads; a longer walk is deferred to the tail kernel.
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16>
+__device__ __forceinline__ void walk_item(const DeviceTable &T, const Sink &K, const uint32_t *sf, const void *srank,
+                                          int walk_loads, uint32_t set_index, const void *text,
+                                          const uint32_t *invalid, int64_t end, int64_t gp, uint32_t x0, uint32_t x1,
+                                          uint32_t x2, uint32_t x3, int j, int wlim, bool ends, bool fast)
+{
+    using RankT = typename std::conditional<RANK16, uint16_t, uint32_t>::type;
+    const int B = T.filter_b;
+    const uint32_t bmask = (uint32_t)((1ull << (2 * B)) - 1ull);
+    uint32_t s = 0, best = 0;
+    int q = 0;
+    uint4 e;
+    bool from_root = true;
+    if (fast) {
+        const uint32_t kmer = window_at(x0, x1, x2, x3, j) & bmask;
+        const uint32_t widx = kmer >> 5;
+        const uint32_t word = FSMEM ? sf[widx] : __ldg(T.filter + widx);
+        uint32_t base_rank;
+        if (srank) base_rank = (uint32_t)reinterpret_cast<const RankT *>(srank)[widx];
+        else if (T.rank_wide) base_rank = __ldg(reinterpret_cast<const uint32_t *>(T.rank) + widx);
+        else base_rank = (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(T.rank) + widx);
+        const uint32_t rk = base_rank + __popc(word & ((1u << (kmer & 31u)) - 1u));
+        e = __ldg(T.dense + rk);
+        if (!(e.y & kSkipSpecial)) {
+            from_root = false;
+            q = B;
+        }
+    }
+    if (from_root) e = __ldg(T.skip);
+    bool defer = false;
+    for (int loads = 1;; loads++) {
+        if (e.y & kSkipSelfTerm) best = s;
+        const uint32_t L = e.y & kSkipLenMask;
+        const int need = L ? (int)L : 1;
+        if (q + need > wlim) {
+            defer = !ends;     // the window ran out before the text did
+            break;
+        }
+        const uint32_t win = window_at(x0, x1, x2, x3, j + q);
+        if (L) {
+            if ((win ^ e.x) & base_mask(L)) break;
+            q += (int)L;
+            s = e.z;
+            if (e.y & kSkipTargetTerm) best = s;
+        } else {
+            const uint32_t c = win & 3u;
+            if (!((e.w >> c) & 1u)) break;
+            s = (e.w >> kNodeFirstShift) + __popc(e.w & ((1u << c) - 1u));
+            q++;
+        }
+        if (loads >= walk_loads) {
+            defer = true;      // the tail kernel takes it from state s
+            break;
+        }
+        e = __ldg(T.skip + s);
+    }
+    if (defer) {
+        // long walk: finish it in the tail kernel (or here if the list is full)
+        const unsigned long long di = atomicAdd(K.defer_count, 1ull);
+        if ((int64_t)di < K.defer_cap) {
+            DeferItem it;
+            it.gp = gp;
+            it.s = s;
+            it.best = best;
+            it.q_set = (uint32_t)q | (set_index << 16);
+            it.span = (int32_t)min(end - gp, (int64_t)0x7FFFFFFF);
+            K.defer[di] = it;
+        } else {
+            emit_match<COMPACT>(K, gp, walk_global<PACKED>(T, text, invalid, end, gp, s, q, best));
+        }
+    } else if (best) {
+        emit_match<COMPACT>(K, gp, __ldg(T.out_id + best));
+    }
+}
+
 // One warp-batch: lane `lane` owns the LW offsets gp0 = warp_base + lane*LW .. +LW-1
 // and holds the 64 bases from gp0 in x0..x3 with `bad` marking the bases that cannot
 // be read (past the end of its text or read, or not A/C/G/T); `valid` marks the
 // offsets this call must answer. Every offset's prefix-filter bit is tested; the
-// offsets that pass are spread over the warp and walked through skip entries inside
-// the window (at most walk_loads dependent loads), longer walks are deferred.
+// offsets that pass are spread over the warp (item r of the warp, in lane order then
+// offset order, goes to lane r mod 32 in round r / 32, with the owner's window by
+// shuffle) and walked at once. Used for ASCII text and for batched reads.
 // sf / srank: filter and rank index in shared memory, or nullptr for global memory.
 template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW>
 __device__ __forceinline__ void scan_lane_batch(const DeviceTable &T, const Sink &K, const uint32_t *sf,
@@ -502,46 +667,18 @@ __device__ __forceinline__ void scan_lane_batch(const DeviceTable &T, const Sink
                                                 int64_t warp_base, int lane, uint32_t x0, uint32_t x1, uint32_t x2,
                                                 uint32_t x3, uint64_t bad, uint32_t valid, bool vec_ok, uint64_t pol)
 {
-    using RankT = typename std::conditional<RANK16, uint16_t, uint32_t>::type;
     const int B = T.filter_b;
     const uint32_t bmask = (uint32_t)((1ull << (2 * B)) - 1ull);
-    const int64_t gp0 = warp_base + (int64_t)lane * LW;
-    const uint32_t all = LW == 32 ? 0xFFFFFFFFu : ((1u << LW) - 1u);
     const uint32_t fast = clear_runs(bad, B) & valid;   // the b-mer is readable
-
-    // Every offset: one filter bit for the b bases starting there. A clear bit means
-    // the walk ends before depth b with no pattern on the way: answer 0.
-    uint32_t pend = 0;
-#pragma unroll
-    for (int j = 0; j < LW; j++) {
-        const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
-        const uint32_t kmer = win & bmask;   // bases j .. j+b-1
-        const uint32_t word = FSMEM ? sf[kmer >> 5] : __ldg(T.filter + (kmer >> 5));
-        pend |= ((word >> (kmer & 31u)) & 1u) << j;
-    }
-    pend &= fast;
+    uint32_t pend = filter_bits<FSMEM, LW>(T, sf, x0, x1, x2, bmask) & fast;
     pend |= valid & ~fast;     // these walk from the root
 
-    if (!COMPACT && valid) {
-        if (vec_ok && valid == all) {
-            int32_t *o = K.out + gp0;
-            const int4 z = make_int4(0, 0, 0, 0);
-#pragma unroll
-            for (int v = 0; v < LW / 4; v++) st_global_v4_hint(o + 4 * v, z, pol);
-        } else {
-            for (int j = 0; j < LW; j++)
-                if ((valid >> j) & 1u) K.out[gp0 + j] = 0;
-        }
-    }
-
-    // The zeros above were stored by the lane that owns each offset; a match found
-    // below is stored by whichever lane walks it. The warp barrier orders the first
-    // before the second.
+    if (!COMPACT) zero_batch<LW>(K, warp_base, lane, valid, vec_ok, pol);
+    // The zeros above were stored by one lane and a match found below is stored by
+    // whichever lane walks it, often another. The warp barrier orders the first before
+    // the second.
     __syncwarp();
 
-    // -------- walks that go on --------
-    // Spread them over the warp: item r of the warp (in lane order, then offset order)
-    // goes to lane r mod 32 in round r / 32. The owner's window comes by shuffle.
     const uint32_t cnt = __popc(pend);
     uint32_t incl = cnt;
 #pragma unroll
@@ -579,84 +716,46 @@ __device__ __forceinline__ void scan_lane_batch(const DeviceTable &T, const Sink
         // bases readable from the window; `ends` when the text (or the run of ACGT
         // bytes) really stops there rather than the window
         const int wlim = badj ? __ffsll((long long)badj) - 1 : 64 - j;
-        const bool ends = badj != 0;
-        uint32_t s = 0, best = 0;
-        int q = 0;
-        uint4 e;
-        bool from_root = true;
-        if ((ofast >> j) & 1u) {
-            const uint32_t kmer = window_at(ox0, ox1, ox2, ox3, j) & bmask;
-            const uint32_t widx = kmer >> 5;
-            const uint32_t word = FSMEM ? sf[widx] : __ldg(T.filter + widx);
-            uint32_t base_rank;
-            if (srank) base_rank = (uint32_t)reinterpret_cast<const RankT *>(srank)[widx];
-            else if (T.rank_wide) base_rank = __ldg(reinterpret_cast<const uint32_t *>(T.rank) + widx);
-            else base_rank = (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(T.rank) + widx);
-            const uint32_t rk = base_rank + __popc(word & ((1u << (kmer & 31u)) - 1u));
-            e = __ldg(T.dense + rk);
-            if (!(e.y & kSkipSpecial)) {
-                from_root = false;
-                q = B;
-            }
-        }
-        if (from_root) e = __ldg(T.skip);
-        // walk on through skip entries inside the window, with at most walk_loads
-        // dependent table loads; a longer walk is deferred
-        bool defer = false;
-        for (int loads = 1;; loads++) {
-            if (e.y & kSkipSelfTerm) best = s;
-            const uint32_t L = e.y & kSkipLenMask;
-            const int need = L ? (int)L : 1;
-            if (q + need > wlim) {
-                defer = !ends;     // the window ran out before the text did
-                break;
-            }
-            const uint32_t win = window_at(ox0, ox1, ox2, ox3, j + q);
-            if (L) {
-                if ((win ^ e.x) & base_mask(L)) break;
-                q += (int)L;
-                s = e.z;
-                if (e.y & kSkipTargetTerm) best = s;
-            } else {
-                const uint32_t c = win & 3u;
-                if (!((e.w >> c) & 1u)) break;
-                s = (e.w >> kNodeFirstShift) + __popc(e.w & ((1u << c) - 1u));
-                q++;
-            }
-            if (loads >= walk_loads) {
-                defer = true;      // the tail kernel takes it from state s
-                break;
-            }
-            e = __ldg(T.skip + s);
-        }
-        if (defer) {
-            // long walk: finish it in the tail kernel (or here if the list is full)
-            const unsigned long long di = atomicAdd(K.defer_count, 1ull);
-            if ((int64_t)di < K.defer_cap) {
-                DeferItem it;
-                it.gp = gp;
-                it.s = s;
-                it.best = best;
-                it.q_set = (uint32_t)q | (set_index << 16);
-                it.span = (int32_t)min(end - gp, (int64_t)0x7FFFFFFF);
-                K.defer[di] = it;
-            } else {
-                emit_match<COMPACT>(K, gp, walk_global<PACKED>(T, text, invalid, end, gp, s, q, best));
-            }
-        } else if (best) {
-            emit_match<COMPACT>(K, gp, __ldg(T.out_id + best));
-        }
+        walk_item<PACKED, COMPACT, FSMEM, RANK16>(T, K, sf, srank, walk_loads, set_index, text, invalid, end, gp,
+                                                  ox0, ox1, ox2, ox3, j, wlim, badj != 0, (ofast >> j) & 1u);
     }
+}
+
+// Walk `count` (<= 32) queued offsets of packed text, one per lane. Each lane reads the
+// 64 bases from its offset straight from the packed text (an L2 hit: the tile was
+// staged moments ago), so nothing moves between lanes.
+template <bool COMPACT, bool FSMEM, bool RANK16>
+__device__ __forceinline__ void queue_round(const ScanParams &P, const Sink &K, const uint32_t *sf,
+                                            const void *srank, const volatile uint32_t *queue, uint32_t head, uint32_t count,
+                                            int lane)
+{
+    if ((uint32_t)lane >= count) return;
+    const uint32_t code = queue[(head + (uint32_t)lane) & (kQueue - 1)];
+    const int64_t t = (int64_t)blockIdx.x + (int64_t)(code >> kRelBits) * gridDim.x;
+    const int64_t gp = t * P.tile + (code & ((1u << kRelBits) - 1u));
+    const int64_t rem = P.n - gp;
+    const uint32_t *words = reinterpret_cast<const uint32_t *>(P.text);
+    const int64_t wi = gp >> 4;
+    const uint32_t sh = (uint32_t)(gp & 15) * 2;
+    uint32_t w[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) w[k] = wi + k < P.n_units ? __ldg(words + wi + k) : 0u;
+    const uint32_t x0 = __funnelshift_r(w[0], w[1], sh), x1 = __funnelshift_r(w[1], w[2], sh);
+    const uint32_t x2 = __funnelshift_r(w[2], w[3], sh), x3 = __funnelshift_r(w[3], w[4], sh);
+    const int wlim = rem < 64 ? (int)rem : 64;
+    walk_item<true, COMPACT, FSMEM, RANK16>(P.t, K, sf, srank, P.walk_loads, 0u, P.text, nullptr, P.n, gp, x0, x1,
+                                            x2, x3, 0, wlim, rem <= 64, wlim >= P.t.filter_b);
 }
 
 template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW>
 __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *empty = reinterpret_cast<uint64_t *>(smem + 64);
-    volatile uint32_t *abort_flag = reinterpret_cast<volatile uint32_t *>(smem + 128);
-    const uint32_t *sf = reinterpret_cast<const uint32_t *>(smem + P.off_filter);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + P.off_bar);
+    uint64_t *empty = reinterpret_cast<uint64_t *>(smem + P.off_bar + 64);
+    volatile uint32_t *abort_flag = reinterpret_cast<volatile uint32_t *>(smem + P.off_bar + 128);
+    // the filter sits at offset 0 when it is in shared memory
+    const uint32_t *sf = reinterpret_cast<const uint32_t *>(smem);
     uint8_t *stage0 = smem + P.off_stage;
     using RankT = typename std::conditional<RANK16, uint16_t, uint32_t>::type;
     const RankT *srank = reinterpret_cast<const RankT *>(smem + P.off_rank);
@@ -731,6 +830,11 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
     K.defer = P.defer;
     K.defer_cap = P.defer_cap;
     K.defer_count = P.defer_count;
+    const void *rank_ptr = P.rank_smem ? (const void *)srank : nullptr;
+    const uint32_t all = LW == 32 ? 0xFFFFFFFFu : ((1u << LW) - 1u);
+    const uint32_t bmask = (uint32_t)((1ull << (2 * B)) - 1ull);
+    volatile uint32_t *queue = reinterpret_cast<volatile uint32_t *>(smem + P.off_queue) + warp * kQueue;
+    uint32_t qhead = 0, qcount = 0;   // warp-uniform
     int k = 0;
     for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, k++) {
         const int st = k % S;
@@ -740,47 +844,88 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
         }
         const uint8_t *stage = stage0 + (size_t)st * P.stage_bytes;
         const int p_rel = warp * (32 * LW) + lane * LW;
+        const int64_t warp_base = t * (int64_t)P.tile + warp * (32 * LW);
         const int64_t gp0 = t * (int64_t)P.tile + p_rel;
-        // 64-base window: packed words and a mask of bases that cannot be read (past
-        // the text end, or ASCII bytes outside ACGT).
-        uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
         const int64_t rem = n - gp0;
         uint64_t bad = rem < 64 ? (rem > 0 ? (~0ull << rem) : ~0ull) : 0ull;
-        if (rem > 0) {
-            if (PACKED) {
+        const uint32_t valid = rem >= LW ? all : (rem > 0 ? ((1u << rem) - 1u) : 0u);
+        if constexpr (PACKED) {
+            // The filter reads window bases 0 .. LW+b-2 (three words at most); the walks
+            // of the offsets that pass read their text again when their round comes.
+            uint32_t x0 = 0, x1 = 0, x2 = 0;
+            if (rem > 0) {
                 const uint32_t *w = reinterpret_cast<const uint32_t *>(stage) + (p_rel >> 4);
-                if (LW == 32) {   // even word index: two 64-bit loads
-                    const uint2 a = *reinterpret_cast<const uint2 *>(w);
-                    const uint2 c = *reinterpret_cast<const uint2 *>(w + 2);
-                    x0 = a.x;
-                    x1 = a.y;
-                    x2 = c.x;
-                    x3 = c.y;
-                } else {
-                    x0 = w[0];
-                    x1 = w[1];
-                    x2 = w[2];
-                    x3 = w[3];
+                x0 = lds_u32(w);
+                x1 = lds_u32(w + 1);
+                if (LW == 32) x2 = lds_u32(w + 2);
+            }
+            const uint32_t fast = bad ? clear_runs(bad, B) & valid : valid;   // the b-mer is readable
+            uint32_t pend = filter_bits<FSMEM, LW>(T, sf, x0, x1, x2, bmask) & fast;
+            pend |= valid & ~fast;     // these walk from the root
+            // Release the stage only once every lane has used its words: the producer
+            // refills it as soon as all consumer warps have arrived, and a word read
+            // after that would come from the next fill.
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(&empty[st]));
+            if (!COMPACT) zero_batch<LW>(K, warp_base, lane, valid, true, pol);
+            // Zeros stored above by one lane are ordered before matches stored by another
+            // lane in a later round by the warp barriers between them (this one first).
+            __syncwarp();
+
+            // Queue the offsets that pass: lane l's items take the places after those of
+            // lanes 0 .. l-1 (exclusive prefix of the counts, by ballots).
+            const uint32_t c = __popc(pend);
+            const uint32_t lt = (1u << lane) - 1u;
+            uint32_t idx = 0, total = 0;
+            for (uint32_t b = 0; b < (uint32_t)LW; b++) {
+                const uint32_t vb = __ballot_sync(0xFFFFFFFFu, c > b);
+                if (!vb) break;
+                idx += __popc(vb & lt);
+                total += __popc(vb);
+            }
+            const uint32_t code0 = ((uint32_t)k << kRelBits) | (uint32_t)p_rel;
+            uint32_t mine = pend;
+            while (total) {   // warp-uniform
+                const uint32_t take = min(kQueue - qcount, total);
+                while (mine && idx < take) {
+                    const int j = __ffs(mine) - 1;
+                    mine &= mine - 1u;
+                    queue[(qhead + qcount + idx) & (kQueue - 1)] = code0 + (uint32_t)j;
+                    idx++;
                 }
-            } else {
-                const uint4 *r = reinterpret_cast<const uint4 *>(stage + p_rel);
+                idx -= min(idx, take);
+                qcount += take;
+                total -= take;
+                __syncwarp();
+                while (qcount >= 32) {
+                    queue_round<COMPACT, FSMEM, RANK16>(P, K, sf, rank_ptr, queue, qhead, 32, lane);
+                    qhead = (qhead + 32) & (kQueue - 1);
+                    qcount -= 32;
+                    __syncwarp();   // the entries just read may be written again
+                }
+            }
+        } else {
+            // ASCII: the lane packs its 64-base window from the stage and walks what
+            // passes at once, through scan_lane_batch.
+            uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
+            if (rem > 0) {
+                const uint8_t *r = stage + p_rel;
                 uint32_t b0, b1, b2, b3;
-                x0 = pack16(r[0], &b0);
-                x1 = pack16(r[1], &b1);
-                x2 = pack16(r[2], &b2);
-                x3 = pack16(r[3], &b3);
+                x0 = pack16(lds_v4(r), &b0);
+                x1 = pack16(lds_v4(r + 16), &b1);
+                x2 = pack16(lds_v4(r + 32), &b2);
+                x3 = pack16(lds_v4(r + 48), &b3);
                 bad |= (uint64_t)b0 | ((uint64_t)b1 << 16) | ((uint64_t)b2 << 32) | ((uint64_t)b3 << 48);
             }
+            // release the stage once every lane has used its bytes (see the packed path)
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(&empty[st]));
+            scan_lane_batch<PACKED, COMPACT, FSMEM, RANK16, LW>(T, K, sf, rank_ptr, P.walk_loads, 0u, P.text,
+                                                                nullptr, n, warp_base, lane, x0, x1, x2, x3, bad,
+                                                                valid, true, pol);
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(&empty[st]));   // this warp is done with the stage
-        const uint32_t all = LW == 32 ? 0xFFFFFFFFu : ((1u << LW) - 1u);
-        const uint32_t valid = rem >= LW ? all : (rem > 0 ? ((1u << rem) - 1u) : 0u);
-        scan_lane_batch<PACKED, COMPACT, FSMEM, RANK16, LW>(T, K, sf, P.rank_smem ? (const void *)srank : nullptr,
-                                                            P.walk_loads, 0u, P.text, nullptr, n,
-                                                            t * (int64_t)P.tile + warp * (32 * LW), lane, x0, x1, x2,
-                                                            x3, bad, valid, true, pol);
     }
+    if (PACKED && qcount) queue_round<COMPACT, FSMEM, RANK16>(P, K, sf, rank_ptr, queue, qhead, qcount, lane);
 }
 
 // Deferred walks: one thread per item.
@@ -803,7 +948,7 @@ __global__ void __launch_bounds__(256) tail_kernel(const ScanParams P)
 }
 
 struct ScanLayout {
-    uint32_t off_filter, off_rank, off_stage, stage_bytes, total;
+    uint32_t off_filter, off_rank, off_bar, off_queue, off_stage, stage_bytes, total;
     int32_t stage_units;
 };
 
@@ -814,11 +959,16 @@ static ScanLayout scan_layout(int consumers, int lw, int stages, int64_t filter_
 {
     ScanLayout L{};
     const int64_t tile = 32LL * lw * consumers;
-    uint64_t off = kBarBytes;
+    // The filter comes first, at offset 0, so that its lookups need no base address.
+    uint64_t off = 0;
     L.off_filter = (uint32_t)off;
     off += align128((uint64_t)filter_smem_bytes);
     L.off_rank = (uint32_t)off;
     off += align128((uint64_t)rank_smem_bytes);
+    L.off_bar = (uint32_t)off;
+    off += kBarBytes;
+    L.off_queue = (uint32_t)off;
+    if (packed) off += align128((uint64_t)consumers * kQueue * 4);
     // a lane reads 64 bases from its first offset: 2 words (32 bytes) past the tile
     L.stage_units = packed ? (int32_t)(tile / 16 + 4) : (int32_t)(tile + 64);
     L.stage_bytes = align128((uint64_t)L.stage_units * (packed ? 4 : 1));
@@ -961,6 +1111,7 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     P.defer_count = scratch.count;
     P.tile = 32 * LW * C;
     P.n_tiles = (n + P.tile - 1) / P.tile;
+    if (P.tile > (1 << kRelBits)) return PFAC_ERR_INVALID_ARG;
     P.consumers = C;
     P.stages = S;
     P.stage_units = L.stage_units;
@@ -968,11 +1119,15 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     P.walk_loads = cfg.walk_loads > 0 ? cfg.walk_loads : 2;
     P.off_filter = L.off_filter;
     P.off_rank = L.off_rank;
+    P.off_bar = L.off_bar;
+    P.off_queue = L.off_queue;
     P.off_stage = L.off_stage;
     P.stage_bytes = L.stage_bytes;
     P.timeout_ns = cfg.timeout_ns > 0 ? cfg.timeout_ns : 2000000000LL;
     const int64_t grid64 = std::min<int64_t>(P.n_tiles, (int64_t)dp.num_sms * std::max(1, cfg.ctas_per_sm));
     const int grid = (int)std::max<int64_t>(1, grid64);
+    // a queued offset codes its tile round in 32 - kRelBits bits
+    if (packed && (P.n_tiles + grid - 1) / grid > ((int64_t)1 << (32 - kRelBits))) return PFAC_ERR_UNSUPPORTED;
     const int tail_grid = dp.num_sms * 4;
     const bool fsmem = pl.filter_bytes > 0;
     const bool rank16 = !t.rank_wide;
