@@ -171,8 +171,9 @@ def batched_measure(steps: int):
     tables = [b.Table(s) for s in w.sets]
     build_s = time.perf_counter() - t0
     n = int(w.reads.size)
-    sc = BatchedScanner(tables, max_bases=n, max_reads=len(w.read_set), graph=True)
+    sc = BatchedScanner(tables, max_bases=n, max_reads=len(w.read_set), graph=False)
     sc.load(w.reads, w.read_offsets, w.read_set)
+    tuned = sc.tune(use_cache=False)      # picks the launch shape, then captures the graph
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(3):
         sc.run()
@@ -208,6 +209,8 @@ def batched_measure(steps: int):
             "table_build_s": build_s, "graph_replay_ms": ms, "gbases_s": n / ms / 1e6,
             "per_read_launches_ms": per_ms, "per_read_gbases_s": n / per_ms / 1e6,
             "batched_vs_per_read": per_ms / ms, "same_output": same,
+            "autotune": {k: tuned.get(k) for k in ("lane_offsets", "threads", "ctas_per_sm", "walk_loads",
+                                                   "ms", "default_ms", "candidates")},
             "launches_per_batch": 4, "launches_per_read_pass": 2 * int(len(w.read_set))}
 
 
@@ -279,6 +282,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--no-tune", action="store_true", help="use the library's default launch configuration")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -316,6 +320,12 @@ def main():
     flush = torch.empty(max(4 * l2, 256 << 20), dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
     assert int(status.item()) == 0
+
+    # launch configuration: the autotuner's pick for this table and text size
+    tuned = {}
+    if not args.no_tune:
+        from paper_1811_10498_gb300 import autotune
+        tuned = autotune.tune_scan(table, packed, n, packed=True, use_cache=False)
 
     # pack throughput (not part of a step: the text is packed once)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -410,6 +420,9 @@ def main():
             "clocks": clocks.summary(),
             "wall_s_timed_region": wall,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+            "autotune": {k: tuned.get(k) for k in ("lane_offsets", "threads", "stages", "walk_loads",
+                                                   "rank_in_smem", "ms", "default_ms", "candidates")}
+            if tuned else None,
             "extra": {"pack_gbases_s": pack_gbs, "build_s": build_s,
                       "frac_of_roofline_gbases": value / world / (peak / BYTES_PER_BASE)},
         }

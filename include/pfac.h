@@ -166,7 +166,9 @@ typedef struct {
     int32_t rank_in_smem;    /* kernel 2: -1 = keep the filter's rank index in global
                                 memory, 0 = in shared memory when it fits */
     int32_t l2_persist;      /* 1 = keep the skip entries in L2 with an access-policy
-                                window, -1 = never, 0 = automatic */
+                                window (this sets the context's persisting-L2 limit,
+                                which the next launch without the window gives back),
+                                -1 or 0 = no window */
     int32_t walk_loads;      /* kernel 2: dependent table loads a walk may take before it
                                 is handed to the tail kernel (0 = 2) */
     int32_t lane_offsets;    /* kernel 2: consecutive offsets per consumer lane, 16 or 32
@@ -228,7 +230,10 @@ int pfac_match_compact(pfac_handle h, const uint32_t *d_packed, int64_t n_bases,
  * of sets[0] and leaves that read's output unwritten.
  * The call packs the text, plans the work and runs one persistent scan launch (plus a
  * tail launch for the few long walks), all on `stream`, with scratch that the library
- * keeps per stream. The first call with a given list of handles uploads a small
+ * keeps per stream. Its launch shape comes from the configuration of sets[0]
+ * (pfac_set_config): a work item is 32 x lane_offsets offsets of one read, the scan
+ * kernel runs threads x ctas_per_sm threads per SM in 256-thread blocks (1 to 8 blocks),
+ * and walk_loads bounds the in-kernel walks as in kernel 2. The first call with a given list of handles uploads a small
  * descriptor array, and the first call on a stream (or with a larger text) allocates
  * scratch; both are synchronous, so issue such a call before capturing the stream
  * into a CUDA graph; later calls with the same handle list and sizes are capturable. */

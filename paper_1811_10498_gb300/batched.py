@@ -4,7 +4,7 @@
 offsets, read-to-table map, output) and runs ``pfac_match_batched`` on them, either
 directly or by replaying a CUDA graph captured once: every replay is one pack, one
 plan, one persistent scan and one tail launch with the inputs the caller copied into
-the buffers. ``scan_per_read`` is the baseline it is measured against: one
+the buffers. ``tune`` picks the launch shape with the autotuner before capturing. ``scan_per_read`` is the baseline it is measured against: one
 ``pfac_match`` launch per read.
 """
 from __future__ import annotations
@@ -28,16 +28,32 @@ class BatchedScanner:
         self.out = torch.zeros(self.max_bases, dtype=torch.int32, device=device)
         self.stream = torch.cuda.Stream(device=device)
         self.graph = None
+        if graph:
+            self.capture()
+
+    def capture(self):
+        """Capture one batched call into a CUDA graph, which ``run`` then replays. The
+        launch shape (the configuration of the first table) is fixed at capture."""
+        torch = self.torch
         # First call: uploads the table descriptors and allocates the scratch, which
         # must happen before capture.
         with torch.cuda.stream(self.stream):
             self._call()
         self.stream.synchronize()
-        if graph:
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=self.stream):
-                self._call()
-            self.graph = g
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.stream):
+            self._call()
+        self.graph = g
+
+    def tune(self, **kw):
+        """Autotune the batched launch shape on the loaded batch (see autotune.py), then
+        capture the graph. Returns the chosen configuration."""
+        from . import autotune
+        with self.torch.cuda.stream(self.stream):
+            cfg = autotune.tune_batched(self.tables, self.texts, self.offsets, self.read_set, self.out, **kw)
+        self.stream.synchronize()
+        self.capture()
+        return cfg
 
     def _call(self):
         b.pfac_match_batched(self.handles, self.texts, self.offsets, self.read_set, self.out,

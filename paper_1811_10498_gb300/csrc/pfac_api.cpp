@@ -600,9 +600,15 @@ int pfac_match_batched(const pfac_handle *sets, int32_t n_sets, const uint8_t *d
     void *scratch = nullptr;
     rc = batch_scratch(dp.device, st, pfac::batch_scratch_bytes(text_len, n_reads, defer_cap), &scratch);
     if (rc != PFAC_OK) return rc;
+    // The pass takes its launch shape from the configuration of sets[0]: offsets per
+    // lane, walk_loads, and threads x ctas_per_sm threads per SM in 256-thread blocks.
     const pfac_config c = effective_config(sets[0], false);
+    pfac::BatchConfig bc{};
+    bc.lane_offsets = c.lane_offsets;
+    bc.blocks_per_sm = (int32_t)std::max<int64_t>(1, (int64_t)c.threads * c.ctas_per_sm / 256);
+    bc.walk_loads = c.walk_loads;
     rc = pfac::launch_batched(d_sets, n_sets, d_texts, text_len, d_read_offsets, d_read_set, n_reads, d_out_ids,
-                              scratch, defer_cap, c.walk_loads, st, dp);
+                              scratch, defer_cap, bc, st, dp);
     return rc == PFAC_OK ? PFAC_OK : cuda_fail(cudaGetLastError());
 }
 

@@ -145,13 +145,22 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
                  const TiledConfig &cfg, const DeferScratch &scratch, cudaStream_t st,
                  const DeviceProps &dp);
 
+// Launch shape of the batched scan: offsets per lane (16 or 32; a work item is 32 x that),
+// 256-thread blocks per SM of the persistent scan kernel (1..8), dependent table loads a
+// walk may take before it is deferred (0 = 2).
+struct BatchConfig {
+    int32_t lane_offsets;
+    int32_t blocks_per_sm;
+    int32_t walk_loads;
+};
+
 // Batched scan: scratch bytes for n bases, n_reads reads and defer_cap deferred walks,
 // and the launch (pack, plan, scan and tail kernels on `st`). d_sets: device array of
 // n_sets table descriptors.
 int64_t batch_scratch_bytes(int64_t n, int32_t n_reads, int64_t defer_cap);
 int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *texts, int64_t n,
                    const int64_t *read_off, const int32_t *read_set, int32_t n_reads, int32_t *out,
-                   void *scratch, int64_t defer_cap, int32_t walk_loads, cudaStream_t st,
+                   void *scratch, int64_t defer_cap, const BatchConfig &bc, cudaStream_t st,
                    const DeviceProps &dp);
 
 // Shared memory kernel 2 would use for a configuration (bytes), -1 if it cannot run.

@@ -21,6 +21,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "../../include/pfac.h"
@@ -1017,8 +1018,22 @@ int64_t tiled_smem_bytes(const DeviceTable &t, const TiledConfig &cfg, bool pack
 }
 
 // Access-policy window that keeps the skip entries in L2 (persisting) while the
-// output streams through it.
+// output streams through it. The set-aside for persisting lines is a limit of the whole
+// context: it is set by the first launch that asks for the window and given back
+// (limit 0, persisting lines reset to normal) by the next launch that does not, so the
+// other launches of the process keep the whole L2.
+static std::mutex g_persist_mu;
 static bool g_persist_set[64];
+
+static cudaError_t release_persisting_l2(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_persist_mu);
+    if (dev < 0 || dev >= 64 || !g_persist_set[dev]) return cudaSuccess;
+    cudaError_t e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0);
+    if (e == cudaSuccess) e = cudaCtxResetPersistingL2Cache();
+    if (e == cudaSuccess) g_persist_set[dev] = false;
+    return e;
+}
 
 template <typename Kern>
 static cudaError_t launch_with_policy(Kern kern, const ScanParams &P, int grid, int threads, uint32_t smem,
@@ -1035,10 +1050,13 @@ static cudaError_t launch_with_policy(Kern kern, const ScanParams &P, int grid, 
     const int64_t skip_bytes = P.t.n_states * 16;
     if (cfg.l2_persist > 0 && dp.persist_l2_max > 0 && skip_bytes > 0) {
         const int dev = dp.device;
-        if (dev >= 0 && dev < 64 && !g_persist_set[dev]) {
-            if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)dp.persist_l2_max) != cudaSuccess)
-                return cudaGetLastError();
-            g_persist_set[dev] = true;
+        {
+            std::lock_guard<std::mutex> lk(g_persist_mu);
+            if (dev >= 0 && dev < 64 && !g_persist_set[dev]) {
+                if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)dp.persist_l2_max) != cudaSuccess)
+                    return cudaGetLastError();
+                g_persist_set[dev] = true;
+            }
         }
         int max_win = 0;
         cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, dev);
@@ -1051,6 +1069,9 @@ static cudaError_t launch_with_policy(Kern kern, const ScanParams &P, int grid, 
         attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
         attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
         lc.numAttrs = 1;
+    } else {
+        const cudaError_t e = release_persisting_l2(dp.device);
+        if (e != cudaSuccess) return e;
     }
     return cudaLaunchKernelEx(&lc, kern, P);
 }
@@ -1151,7 +1172,7 @@ size_t defer_item_bytes() { return sizeof(DeferItem); }
 //   batched_tail_kernel deferred long walks, with the table recorded in each item
 // ---------------------------------------------------------------------------
 
-constexpr int kBatchItem = 512;   // offsets per work item (32 lanes x 16)
+// A work item is 32 lanes x LW offsets (LW = 16 or 32): 512 or 1024 offsets.
 
 struct BatchParams {
     const DeviceTable *sets;
@@ -1164,6 +1185,7 @@ struct BatchParams {
     int32_t n_reads;
     const int64_t *item_start;
     unsigned long long *item_next;
+    int32_t item;                // offsets per work item (32 x LW)
     int32_t *out;
     DeferItem *defer;
     int64_t defer_cap;
@@ -1208,7 +1230,7 @@ __device__ __forceinline__ void read_bounds(const int64_t *read_off, int32_t r, 
 
 // One CTA: exclusive prefix of the number of work items per read.
 __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ read_off, int32_t n_reads, int64_t n,
-                                                    int64_t *__restrict__ item_start)
+                                                    int32_t item, int64_t *__restrict__ item_start)
 {
     __shared__ int64_t warp_sum[32];
     __shared__ int64_t carry;
@@ -1221,7 +1243,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         if (r < n_reads) {
             int64_t rs, re;
             read_bounds(read_off, (int32_t)r, n, &rs, &re);
-            v = (re - rs + kBatchItem - 1) / kBatchItem;
+            v = (re - rs + item - 1) / item;
         }
         int64_t incl = v;
         for (int d = 1; d < 32; d <<= 1) {
@@ -1248,8 +1270,11 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     if (tid == 0) item_start[n_reads] = carry;
 }
 
+template <int LW>
 __global__ void __launch_bounds__(256) batched_scan_kernel(const BatchParams P)
 {
+    constexpr int kItem = 32 * LW;
+    constexpr uint32_t kAll = LW == 32 ? 0xFFFFFFFFu : ((1u << LW) - 1u);
     const int lane = threadIdx.x & 31;
     const int64_t total = P.item_start[P.n_reads];
     const uint64_t pol = policy_evict_first();
@@ -1274,16 +1299,16 @@ __global__ void __launch_bounds__(256) batched_scan_kernel(const BatchParams P)
         }
         int64_t rs, re;
         read_bounds(P.read_off, lo, P.n, &rs, &re);
-        const int64_t base = rs + ((int64_t)it - P.item_start[lo]) * kBatchItem;
-        const int64_t item_end = min(base + kBatchItem, re);
+        const int64_t base = rs + ((int64_t)it - P.item_start[lo]) * kItem;
+        const int64_t item_end = min(base + kItem, re);
         const int32_t set = P.read_set[lo];
         if (set < 0 || set >= P.n_sets) {
             if (lane == 0) record_error(P.sets[0].status, PFAC_ERR_INVALID_ARG);
             continue;
         }
         const DeviceTable T = P.sets[set];
-        // this lane's 16 offsets and the 64 bases from its first one
-        const int64_t p0 = base + 16 * lane;
+        // this lane's LW offsets and the 64 bases from its first one
+        const int64_t p0 = base + LW * lane;
         const int64_t wi = p0 >> 4;
         const uint32_t sh = (uint32_t)(p0 & 15) * 2;
         uint32_t w[5];
@@ -1300,9 +1325,9 @@ __global__ void __launch_bounds__(256) batched_scan_kernel(const BatchParams P)
         const int64_t rem_read = re - p0;   // walks stop at the read's end
         if (rem_read < 64) bad |= rem_read > 0 ? (~0ull << rem_read) : ~0ull;
         const int64_t rem_item = item_end - p0;
-        const uint32_t valid = rem_item >= 16 ? 0xFFFFu : (rem_item > 0 ? ((1u << rem_item) - 1u) : 0u);
+        const uint32_t valid = rem_item >= LW ? kAll : (rem_item > 0 ? ((1u << rem_item) - 1u) : 0u);
         const bool vec_ok = (((uintptr_t)(P.out + base)) & 15u) == 0;
-        scan_lane_batch<true, false, false, true, 16>(T, K, nullptr, nullptr, P.walk_loads, (uint32_t)set, P.packed,
+        scan_lane_batch<true, false, false, true, LW>(T, K, nullptr, nullptr, P.walk_loads, (uint32_t)set, P.packed,
                                                       P.invalid, re, base, lane, x0, x1, x2, x3, bad, valid, vec_ok,
                                                       pol);
     }
@@ -1331,8 +1356,10 @@ int64_t batch_scratch_bytes(int64_t n, int32_t n_reads, int64_t defer_cap)
 
 int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *texts, int64_t n, const int64_t *read_off,
                    const int32_t *read_set, int32_t n_reads, int32_t *out, void *scratch, int64_t defer_cap,
-                   int32_t walk_loads, cudaStream_t st, const DeviceProps &dp)
+                   const BatchConfig &bc, cudaStream_t st, const DeviceProps &dp)
 {
+    const int lw = bc.lane_offsets == 32 ? 32 : 16;
+    const int blocks_per_sm = std::min(8, std::max(1, bc.blocks_per_sm));
     if (n == 0 || n_reads == 0) return PFAC_OK;
     uint8_t *p = (uint8_t *)scratch;
     unsigned long long *counters = (unsigned long long *)p;       // [0] next item, [1] deferred walks
@@ -1348,7 +1375,7 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
     if (cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     const int pack_blocks = (int)std::min<int64_t>((bw + 255) / 256, (int64_t)dp.num_sms * 16);
     pack_bits_kernel<<<std::max(1, pack_blocks), 256, 0, st>>>(texts, n, packed, invalid);
-    plan_kernel<<<1, 1024, 0, st>>>(read_off, n_reads, n, item_start);
+    plan_kernel<<<1, 1024, 0, st>>>(read_off, n_reads, n, 32 * lw, item_start);
     BatchParams P{};
     P.sets = d_sets;
     P.n_sets = n_sets;
@@ -1364,8 +1391,10 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
     P.defer = defer;
     P.defer_cap = defer_cap;
     P.defer_count = counters + 1;
-    P.walk_loads = walk_loads > 0 ? walk_loads : 2;
-    batched_scan_kernel<<<dp.num_sms * 4, 256, 0, st>>>(P);
+    P.item = 32 * lw;
+    P.walk_loads = bc.walk_loads > 0 ? bc.walk_loads : 2;
+    if (lw == 32) batched_scan_kernel<32><<<dp.num_sms * blocks_per_sm, 256, 0, st>>>(P);
+    else batched_scan_kernel<16><<<dp.num_sms * blocks_per_sm, 256, 0, st>>>(P);
     batched_tail_kernel<<<dp.num_sms * 4, 256, 0, st>>>(P);
     return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
 }
