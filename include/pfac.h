@@ -162,7 +162,8 @@ typedef struct {
     int32_t threads;         /* kernel 2: threads per CTA, 64..1024, multiple of 32: one
                                 producer warp plus consumer warps */
     int32_t ctas_per_sm;     /* kernel 2: resident CTAs per SM of the persistent grid */
-    int32_t stages;          /* kernel 2: text stages in the ring, 2..8 */
+    int32_t stages;          /* kernel 2: text stages in the ring, 2..8 (0 = 3 for packed
+                                text, 2 for ASCII) */
     int32_t rank_in_smem;    /* kernel 2: -1 = keep the filter's rank index in global
                                 memory, 0 = in shared memory when it fits */
     int32_t l2_persist;      /* 1 = keep the skip entries in L2 with an access-policy
@@ -172,8 +173,8 @@ typedef struct {
     int32_t walk_loads;      /* kernel 2: dependent table loads a walk may take before it
                                 is handed to the tail kernel (0 = 2) */
     int32_t lane_offsets;    /* kernel 2: consecutive offsets per consumer lane, 16 or 32
-                                (0 = 16); a tile is 32 x lane_offsets bases per consumer
-                                warp */
+                                (0 = 32 for packed text, 16 for ASCII and batched passes);
+                                a tile is 32 x lane_offsets bases per consumer warp */
 } pfac_config;
 
 /* Set (cfg != NULL) or reset (cfg == NULL) the launch configuration of a handle.

@@ -162,27 +162,45 @@ __device__ __forceinline__ uint32_t pack16(uint4 v, uint32_t *bad16)
 __global__ void pack_kernel(const uint8_t *__restrict__ text, int64_t len, uint32_t *__restrict__ packed,
                             int32_t *status, unsigned long long *bad)
 {
+    // Each thread packs four consecutive words (64 bases): four independent 16-byte
+    // loads in flight, one 16-byte store.
     const int64_t n_words = (len + 15) >> 4;
-    const bool aligned = ((uintptr_t)text & 15u) == 0;
-    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n_words;
-         w += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b0 = w << 4;
-        uint32_t word, badm;
-        if (aligned && b0 + 16 <= len) {
-            word = pack16(__ldg(reinterpret_cast<const uint4 *>(text + b0)), &badm);
+    const int64_t n_quads = (n_words + 3) >> 2;
+    const bool aligned = (((uintptr_t)text | (uintptr_t)packed) & 15u) == 0;
+    for (int64_t qd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qd < n_quads;
+         qd += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t w0 = qd << 2;
+        const int64_t b0 = w0 << 4;
+        uint32_t word[4], badm[4];
+        if (aligned && b0 + 64 <= len) {
+            uint4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) v[k] = __ldg(reinterpret_cast<const uint4 *>(text + b0) + k);
+#pragma unroll
+            for (int k = 0; k < 4; k++) word[k] = pack16(v[k], &badm[k]);
+            *reinterpret_cast<uint4 *>(packed + w0) = make_uint4(word[0], word[1], word[2], word[3]);
         } else {
-            word = 0;
-            badm = 0;
-            for (int i = 0; i < 16 && b0 + i < len; i++) {
-                const int c = base_code_or_neg(text[b0 + i]);
-                if (c < 0) badm |= 1u << i;
-                else word |= (uint32_t)c << (2 * i);
+            for (int k = 0; k < 4; k++) {
+                word[k] = 0;
+                badm[k] = 0;
+                const int64_t bk = b0 + 16 * k;
+                for (int i = 0; i < 16 && bk + i < len; i++) {
+                    const int c = base_code_or_neg(text[bk + i]);
+                    if (c < 0) badm[k] |= 1u << i;
+                    else word[k] |= (uint32_t)c << (2 * i);
+                }
+                if (w0 + k < n_words) packed[w0 + k] = word[k];
             }
         }
-        packed[w] = word;
-        if (badm) {
+        if (badm[0] | badm[1] | badm[2] | badm[3]) {
             if (status) *status = PFAC_ERR_BAD_SYMBOL;
-            if (bad) atomicMin(bad, (unsigned long long)(b0 + __ffs(badm) - 1));
+            if (bad) {
+                for (int k = 0; k < 4; k++)
+                    if (badm[k]) {
+                        atomicMin(bad, (unsigned long long)(b0 + 16 * k + __ffs(badm[k]) - 1));
+                        break;
+                    }
+            }
         }
     }
 }
@@ -195,7 +213,7 @@ int launch_pack(const uint8_t *text, int64_t len, uint32_t *packed, int32_t *sta
     const int64_t n_words = (len + 15) >> 4;
     if (n_words == 0) return PFAC_OK;
     const int threads = 256;
-    const int64_t want = (n_words + threads - 1) / threads;
+    const int64_t want = ((n_words + 3) / 4 + threads - 1) / threads;
     const int blocks = (int)std::min<int64_t>(want, (int64_t)dp.num_sms * 16);
     pack_kernel<<<blocks, threads, 0, st>>>(text, len, packed, status, (unsigned long long *)bad);
     return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
@@ -516,9 +534,12 @@ __device__ __forceinline__ uint32_t window_at(uint32_t x0, uint32_t x1, uint32_t
 // Prefix-filter bits of a lane's LW offsets: bit j is the filter bit of the b bases
 // from offset j (window bases j .. j+b-1; x0, x1, x2 hold window bases 0 .. 47). A
 // clear bit means the walk from offset j ends before depth b with no pattern on the
-// way. With the filter at shared-memory offset 0 and b >= 3, the byte address of a
-// filter word is the window shifted and masked, and the bit index is the window's low
-// five bits, which a rotate uses as they are.
+// way. The shared-memory copy of the filter (sf) holds each word bit-reversed: the bit of
+// b-mer w is bit 31 - (w mod 32) of word w / 32. With that copy at shared-memory offset 0
+// and b >= 3, the byte address of a filter word is the window shifted and masked, a
+// left rotate by the window (whose low five bits are w mod 32, taken as they are) brings
+// the bit to the top, and a funnel shift moves it into the result: two shifts per
+// offset after the load.
 template <bool FSMEM, int LW>
 __device__ __forceinline__ uint32_t filter_bits(const DeviceTable &T, const uint32_t *sf, uint32_t x0, uint32_t x1,
                                                 uint32_t x2, uint32_t bmask)
@@ -528,17 +549,17 @@ __device__ __forceinline__ uint32_t filter_bits(const DeviceTable &T, const uint
         const uint32_t amask = (bmask >> 3) & ~3u;
         const uint8_t *fb = reinterpret_cast<const uint8_t *>(sf);
 #pragma unroll
-        for (int j = 0; j < LW; j++) {
+        for (int j = LW - 1; j >= 0; j--) {
             const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
             const uint32_t word = *reinterpret_cast<const uint32_t *>(fb + ((win >> 3) & amask));
-            pend |= (__funnelshift_r(word, word, win) & 1u) << j;
+            pend = __funnelshift_l(__funnelshift_l(word, word, win), pend, 1);
         }
     } else {
 #pragma unroll
         for (int j = 0; j < LW; j++) {
             const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
             const uint32_t kmer = win & bmask;
-            const uint32_t word = FSMEM ? sf[kmer >> 5] : __ldg(T.filter + (kmer >> 5));
+            const uint32_t word = FSMEM ? __brev(sf[kmer >> 5]) : __ldg(T.filter + (kmer >> 5));
             pend |= ((word >> (kmer & 31u)) & 1u) << j;
         }
     }
@@ -594,7 +615,7 @@ __device__ __forceinline__ void walk_item(const DeviceTable &T, const Sink &K, c
     if (fast) {
         const uint32_t kmer = window_at(x0, x1, x2, x3, j) & bmask;
         const uint32_t widx = kmer >> 5;
-        const uint32_t word = FSMEM ? sf[widx] : __ldg(T.filter + widx);
+        const uint32_t word = FSMEM ? __brev(sf[widx]) : __ldg(T.filter + widx);
         uint32_t base_rank;
         if (srank) base_rank = (uint32_t)reinterpret_cast<const RankT *>(srank)[widx];
         else if (T.rank_wide) base_rank = __ldg(reinterpret_cast<const uint32_t *>(T.rank) + widx);
@@ -785,7 +806,15 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             for (int64_t i = (bytes & ~(int64_t)15) + tid; i < bytes; i += blockDim.x) dst[i] = src[i];
         };
         const int64_t words = B >= 3 ? ((int64_t)1 << (2 * B)) / 32 : 1;
-        if (FSMEM) copy_in(P.off_filter, T.filter, words * 4);
+        if (FSMEM) {
+            // the filter's words go in bit-reversed (see filter_bits)
+            uint32_t *dst = reinterpret_cast<uint32_t *>(smem + P.off_filter);
+            for (int64_t i = 4 * (int64_t)tid; i + 4 <= words; i += 4 * (int64_t)blockDim.x) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(T.filter + i));
+                *reinterpret_cast<uint4 *>(dst + i) = make_uint4(__brev(v.x), __brev(v.y), __brev(v.z), __brev(v.w));
+            }
+            for (int64_t i = (words & ~(int64_t)3) + tid; i < words; i += blockDim.x) dst[i] = __brev(__ldg(T.filter + i));
+        }
         if (P.rank_smem) copy_in(P.off_rank, T.rank, words * (int64_t)sizeof(RankT));
     }
     __syncthreads();
@@ -981,7 +1010,7 @@ static ScanLayout scan_layout(int consumers, int lw, int stages, int64_t filter_
 
 static int consumers_of(const TiledConfig &cfg) { return cfg.threads / 32 - 1; }
 static int lane_width_of(const TiledConfig &cfg) { return cfg.lane_offsets == 32 ? 32 : 16; }
-static int stages_of(const TiledConfig &cfg, bool packed) { return cfg.stages > 0 ? cfg.stages : (packed ? 4 : 2); }
+static int stages_of(const TiledConfig &cfg, bool packed) { return cfg.stages > 0 ? cfg.stages : (packed ? 3 : 2); }
 
 // Shared memory per CTA, by priority: the text stages, the prefix filter (read for
 // every offset), then the rank index (read for every walk the filter passes).

@@ -1,0 +1,50 @@
+"""Chunked scans of host-resident texts with overlapped copies (hoststream.py)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import first_diff, host_threads, require_cuda
+from paper_1811_10498_gb300 import _binding as b
+from paper_1811_10498_gb300 import datagen
+from paper_1811_10498_gb300.hoststream import HostScanner, scan_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def genome():
+    torch = require_cuda()
+    w = datagen.genome_scan(n_bases=(5 << 20) + 4321, n_patterns=4000)
+    t = b.Table((w.blob, w.offsets))
+    want = oracle.Trie((w.blob, w.offsets)).scan_threads(w.text, host_threads())
+    yield torch, w, t, want
+    t.close()
+
+
+@pytest.mark.parametrize("chunk", [1 << 16, (1 << 20) + 48, 1 << 26])
+def test_chunks_equal_the_oracle(genome, chunk):
+    """Walks that start near a chunk's end read into the next chunk's bases."""
+    torch, w, t, want = genome
+    h_text = torch.from_numpy(w.text).pin_memory()
+    got = scan_host(t, h_text, chunk_bases=chunk).numpy()
+    assert np.array_equal(got, want), first_diff(got, want)
+
+
+def test_scanner_reuse_and_short_texts(genome):
+    torch, w, t, want = genome
+    sc = HostScanner(t, chunk_bases=1 << 18)
+    for n in (w.text.size, 1, 99, (1 << 18) + 1):
+        h_text = torch.from_numpy(np.ascontiguousarray(w.text[:n])).pin_memory()
+        h_out = torch.full((n,), -3, dtype=torch.int32).pin_memory()
+        sc.scan(h_text, h_out)
+        assert sc.synchronize() == 0
+        ref = oracle.Trie((w.blob, w.offsets)).scan(w.text[:n])
+        assert np.array_equal(h_out.numpy(), ref), (n, first_diff(h_out.numpy(), ref))
+
+
+def test_bad_symbol_is_reported(genome):
+    torch, w, t, _ = genome
+    text = w.text[:300_000].copy()
+    text[250_000] = ord("N")
+    with pytest.raises(b.PfacError):
+        scan_host(t, torch.from_numpy(text), chunk_bases=1 << 16)

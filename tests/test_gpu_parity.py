@@ -67,6 +67,9 @@ def genome_small():
     dict(kernel=2, walk_loads=64),
     dict(kernel=2, lane_offsets=32),
     dict(kernel=2, lane_offsets=32, threads=64),
+    dict(kernel=2, lane_offsets=16),
+    dict(kernel=2, lane_offsets=16, stages=4),
+    dict(kernel=2, lane_offsets=32, stages=3, threads=1024),
 ], ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
 def test_genome_configs(genome_small, cfg, packed):
     w, want = genome_small
@@ -139,7 +142,7 @@ def test_empty_text():
     assert gpu_match(t, np.zeros(0, dtype=np.uint8)).size == 0
 
 
-@pytest.mark.parametrize("threads,lw", [(64, 16), (128, 32), (1024, 16)])
+@pytest.mark.parametrize("threads,lw", [(64, 16), (128, 32), (1024, 16), (1024, 32)])
 def test_matches_across_tile_edges(threads, lw):
     """Long patterns planted so they start just before, at and after tile edges (a tile
     is 1024 bases per consumer warp) and end exactly at a tile edge, at a 32-base lane
