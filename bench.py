@@ -232,6 +232,83 @@ def serving_measure(seconds: float):
     return stats
 
 
+def paper_suite(args):
+    """The paper's experiments re-run on GB300 with synthetic stand-ins for its files:
+    input data sets of 0.75-3.75 M newline-separated 100-base lines (Table IV) and
+    pattern sets of 1,000-5,000 100-base patterns (Table III), scanned as ASCII.
+
+    * placement: the GB300 analogues of the memory placements of Figs. 6-8 on input set
+      5 for every pattern set: one thread per offset over 16-byte rows with text and
+      table in global memory (kernel 1, the paper's kernel structure); the pipelined
+      kernel with the text staged in shared memory and the prefix filter in shared memory
+      but its rank index in global memory; the same with both in shared memory (the
+      default); and the same with the skip entries pinned in L2 by an access-policy
+      window (the texture-cache analogue);
+    * patterns: Fig. 9's sweep (pattern sets 1-5 on input set 5), kernel 1 vs default;
+    * inputs: Fig. 10's sweep (input sets 1-5 with pattern set 5), kernel 1 vs default.
+    Prints one JSON line per point: median kernel time over the timed launches (L2
+    flushed before each), Gbases/s counting every input byte as an offset, and the HBM
+    roofline fraction at 5 bytes per offset (1 in, 4 out)."""
+    import torch
+    from paper_1811_10498_gb300 import _binding as b
+    from paper_1811_10498_gb300 import build_ext, datagen
+    build_ext.build()
+    peak, peak_kind = measured_hbm()
+    src = datagen.paper_source()
+    lines = [750_000 * k for k in range(1, 6)]
+    n_pats = [1000 * k for k in range(1, 6)]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    texts = {}
+
+    def text(n_lines):
+        if n_lines not in texts:
+            texts.clear()
+            texts[n_lines] = torch.from_numpy(datagen.paper_input(src, n_lines)).cuda()
+        return texts[n_lines]
+
+    placements = {
+        "global (kernel 1)": dict(kernel=1),
+        "smem text + smem filter, rank in global": dict(kernel=2, rank_in_smem=-1),
+        "smem text + smem filter and rank (default)": dict(kernel=0),
+        "default + L2 window on skip entries": dict(kernel=2, l2_persist=1),
+    }
+
+    def point(fig, n_lines, n_p, label, cfg):
+        d_text = text(n_lines)
+        blob, offs = datagen.paper_patterns(src, n_p)
+        t = b.Table((blob, offs))
+        b.pfac_set_config(t.h, cfg)
+        out = torch.empty(d_text.numel(), dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            t.match(d_text, out)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(min(args.steps, 20)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            t.match(d_text, out)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        n = d_text.numel()
+        line = {"suite": "paper", "figure": fig, "input_lines": n_lines, "input_bytes": n, "patterns": n_p,
+                "placement": label, "config": b.pfac_get_config(t.h, n), "ms": ms, "gbases_s": n / ms / 1e6,
+                "roofline_frac": 5.0 * n / (ms * 1e-3) / (peak * 1e9), "peak_gbs": peak, "peak_source": peak_kind,
+                "matches": int((out != 0).sum().item()), "filter_b": t.info["filter_b"], "states": t.info["n_states"]}
+        print(json.dumps(line), flush=True)
+        b.pfac_set_config(t.h, None)
+        t.close()
+
+    for n_p in n_pats:                                 # Figs. 6-8 and 9
+        for label, cfg in placements.items():
+            point("6-9", lines[-1], n_p, label, cfg)
+    for n_l in lines[:-1]:                             # Fig. 10 (input set 5 is above)
+        for label in ("global (kernel 1)", "smem text + smem filter and rank (default)"):
+            point("10", n_l, n_pats[-1], label, placements[label])
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores: each step scans a bounded sample."""
     rank = int(os.environ.get("RANK", "0"))
@@ -284,11 +361,16 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--no-tune", action="store_true", help="use the library's default launch configuration")
+    ap.add_argument("--suite", default=None, choices=["paper"],
+                    help="paper: the paper's placement, pattern-set and input-size experiments (many lines)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.suite == "paper":
+        paper_suite(args)
         return
 
     import torch

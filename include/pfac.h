@@ -215,13 +215,27 @@ int pfac_match_compact(pfac_handle h, const uint32_t *d_packed, int64_t n_bases,
                        int64_t *d_offsets, int32_t *d_ids, int64_t capacity,
                        int64_t *d_count, void *stream);
 
+/* Every pattern occurrence, not only the longest per offset: for every offset i and
+ * every distinct pattern string that starts at i, one (d_offsets[k], d_ids[k]) pair with
+ * that string's lowest id, k < capacity, in no particular order. This is the walk of
+ * Section IV reporting each terminal state it passes, the sub-patterns included that the
+ * paper's PFAC leaves out (it lists what classic Aho-Corasick, Section III, finds, with
+ * occurrences keyed by their start). Same arguments, overflow rule and d_count reset as
+ * pfac_match_compact. */
+int pfac_match_all(pfac_handle h, const uint32_t *d_packed, int64_t n_bases,
+                   int64_t *d_offsets, int32_t *d_ids, int64_t capacity,
+                   int64_t *d_count, void *stream);
+
 /* Many reads against many resident tables in ONE pass (not in the paper, whose input
  * is newline-separated reads scanned as one text, Table IV).
  *   sets[n_sets]                 : host array of handles built on this device
  *                                  (1 <= n_sets <= 65535)
  *   d_texts[text_len]            : all reads' ASCII bytes, concatenated
  *   d_read_offsets[n_reads + 1]  : read r is d_texts[off[r] .. off[r+1]) (offsets are
- *                                  clamped to [0, text_len])
+ *                                  clamped to [0, text_len]; a read with off[r+1] <=
+ *                                  off[r] is empty). Reads should not overlap; where two
+ *                                  do, each offset of the overlap gets the result of one
+ *                                  of them, which one is unspecified.
  *   d_read_set[n_reads]          : index into sets[] of the table for read r
  *   d_out_ids[text_len]          : same layout as d_texts; every offset inside a read
  *                                  gets the longest pattern starting there, within the

@@ -264,3 +264,25 @@ def compact(out_ids: np.ndarray):
     """The match list: every offset with a non-zero id, ascending, with its id."""
     offs = np.flatnonzero(out_ids).astype(np.int64)
     return offs, out_ids[offs].astype(np.int32)
+
+
+def all_matches(patterns, text, cap: int = 1 << 24, lib: C.CDLL | None = None):
+    """Every pattern occurrence, as the walk that reports each terminal state it passes
+    would list it (not only the last one, as the PFAC scan of Section IV does): one
+    ``(start, id)`` per start offset and distinct pattern string occurring there, with
+    the lowest id of that string, sorted by start and then by length. Computed from the
+    classic Aho-Corasick machine's occurrence list (Section III), whose (end, id) pairs
+    are turned into starts. Returns ``(starts int64, ids int32)``."""
+    blob, offsets = _as_patterns(patterns)
+    lengths = np.diff(offsets)
+    ends, ids = AhoCorasick((blob, offsets), lib).occurrences(text, cap)
+    if ends.size == 0:
+        return np.zeros(0, np.int64), np.zeros(0, np.int32)
+    lens = lengths[ids - 1]
+    starts = ends - lens + 1
+    # equal strings at one start: keep the lowest id
+    order = np.lexsort((ids, lens, starts))
+    starts, lens, ids = starts[order], lens[order], ids[order]
+    keep = np.ones(starts.size, dtype=bool)
+    keep[1:] = (starts[1:] != starts[:-1]) | (lens[1:] != lens[:-1])
+    return starts[keep].astype(np.int64), ids[keep].astype(np.int32)

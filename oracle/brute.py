@@ -47,3 +47,17 @@ def occurrences(text: bytes, patterns: list[bytes]) -> list[tuple[int, int]]:
             occ.append((start + len(p) - 1, j + 1))
             start = text.find(p, start + 1)
     return sorted(occ)
+
+
+def brute_all(text: bytes, patterns: list[bytes]) -> list[tuple[int, int]]:
+    """Every (start, id) with ``text[start:start+len] == pattern``, one per start and
+    distinct string (its lowest id), sorted by start then length."""
+    lowest = {}
+    for j, p in enumerate(patterns):
+        lowest.setdefault(bytes(p), j + 1)
+    out = []
+    for i in range(len(text)):
+        for p, pid in sorted(lowest.items(), key=lambda kv: len(kv[0])):
+            if text.startswith(p, i):
+                out.append((i, pid))
+    return out

@@ -70,6 +70,7 @@ _SIGS = {
     "pfac_match": (C.c_int, [P, P, I64, P, P]),
     "pfac_match_packed": (C.c_int, [P, P, I64, P, P]),
     "pfac_match_compact": (C.c_int, [P, P, I64, P, P, I64, P, P]),
+    "pfac_match_all": (C.c_int, [P, P, I64, P, P, I64, P, P]),
     "pfac_match_batched": (C.c_int, [P, I32, P, I64, P, P, I32, P, P]),
     "pfac_device_status": (C.c_int, [P, P, P]),
     "pfac_debug_timeout_probe": (C.c_int, [P, I64, P]),
@@ -227,6 +228,13 @@ def pfac_match_compact(h: int, d_packed, n_bases: int, d_offsets, d_ids, d_count
     cap = 0 if d_offsets is None else d_offsets.numel()
     _check(lib().pfac_match_compact(h, _dptr(d_packed), n_bases, _dptr(d_offsets), _dptr(d_ids), cap,
                                     _dptr(d_count), _stream(stream)), "pfac_match_compact")
+
+
+def pfac_match_all(h: int, d_packed, n_bases: int, d_offsets, d_ids, d_count, stream=None):
+    """Every (offset, id) occurrence, sub-patterns included (see include/pfac.h)."""
+    cap = 0 if d_offsets is None else d_offsets.numel()
+    _check(lib().pfac_match_all(h, _dptr(d_packed), n_bases, _dptr(d_offsets), _dptr(d_ids), cap,
+                                _dptr(d_count), _stream(stream)), "pfac_match_all")
 
 
 def pfac_match_batched(handles, d_texts, d_read_offsets, d_read_set, d_out_ids, stream=None):

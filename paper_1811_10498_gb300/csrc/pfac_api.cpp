@@ -258,7 +258,8 @@ int batch_scratch(int dev, cudaStream_t st, int64_t bytes, void **out)
 // Run the scan with the handle's configuration. Kernel 2 needs 16-byte aligned text
 // and output, the filter and the skip entries; otherwise kernel 1 runs.
 int run_scan(pfac_handle h, const void *text, bool packed, int64_t n, int32_t *out, int64_t *c_off,
-             int32_t *c_ids, int64_t cap, int64_t *count, cudaStream_t st, const pfac::DeviceProps &dp)
+             int32_t *c_ids, int64_t cap, int64_t *count, cudaStream_t st, const pfac::DeviceProps &dp,
+             bool all_matches = false)
 {
     pfac_config c = effective_config(h, packed);
     const bool compact = c_off != nullptr;
@@ -270,13 +271,13 @@ int run_scan(pfac_handle h, const void *text, bool packed, int64_t n, int32_t *o
         rc = get_scratch(dp.device, st, n, &scratch);
         if (rc != PFAC_OK) return rc;
         rc = pfac::launch_tiled(h->dt, text, packed, n, out, c_off, c_ids, cap, (unsigned long long *)count, tc,
-                                scratch, st, dp);
+                                scratch, st, dp, all_matches);
         if (rc == PFAC_ERR_UNSUPPORTED) tiled = false;   // the configuration does not fit shared memory
         else if (rc != PFAC_OK) return rc == PFAC_ERR_CUDA ? cuda_fail(cudaGetLastError()) : fail(rc);
     }
     if (!tiled) {
         rc = pfac::launch_walk_rows_any(h->dt, text, packed, n, out, c_off, c_ids, cap, (unsigned long long *)count,
-                                        st, dp);
+                                        st, dp, all_matches);
         if (rc != PFAC_OK) return rc == PFAC_ERR_CUDA ? cuda_fail(cudaGetLastError()) : fail(rc);
     }
     return PFAC_OK;
@@ -399,6 +400,7 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         h->device = dev;
         h->dt.n_states = T.n_states;
         h->dt.max_len = T.max_len;
+        h->dt.min_len = T.min_len;
         h->dt.filter_b = T.filter_b;
         h->dt.rank_wide = T.rank_wide;
         // The device copy is complete; the host keeps rows, ids and levels for export.
@@ -548,8 +550,8 @@ int pfac_match_packed(pfac_handle h, const uint32_t *d_packed, int64_t n_bases, 
     return run_scan(h, d_packed, true, n_bases, d_out_ids, nullptr, nullptr, 0, nullptr, (cudaStream_t)stream, dp);
 }
 
-int pfac_match_compact(pfac_handle h, const uint32_t *d_packed, int64_t n_bases, int64_t *d_offsets, int32_t *d_ids,
-                       int64_t capacity, int64_t *d_count, void *stream)
+static int match_list(pfac_handle h, const uint32_t *d_packed, int64_t n_bases, int64_t *d_offsets, int32_t *d_ids,
+                      int64_t capacity, int64_t *d_count, void *stream, bool all_matches)
 {
     pfac::DeviceProps dp{};
     int rc = check_handle_for_launch(h, &dp);
@@ -563,7 +565,20 @@ int pfac_match_compact(pfac_handle h, const uint32_t *d_packed, int64_t n_bases,
     }
     int64_t *offs = d_offsets ? d_offsets : (int64_t *)d_count;   // never written when capacity == 0
     int32_t *ids = d_ids ? d_ids : (int32_t *)d_count;
-    return run_scan(h, d_packed, true, n_bases, nullptr, offs, ids, capacity, d_count, (cudaStream_t)stream, dp);
+    return run_scan(h, d_packed, true, n_bases, nullptr, offs, ids, capacity, d_count, (cudaStream_t)stream, dp,
+                    all_matches);
+}
+
+int pfac_match_compact(pfac_handle h, const uint32_t *d_packed, int64_t n_bases, int64_t *d_offsets, int32_t *d_ids,
+                       int64_t capacity, int64_t *d_count, void *stream)
+{
+    return match_list(h, d_packed, n_bases, d_offsets, d_ids, capacity, d_count, stream, false);
+}
+
+int pfac_match_all(pfac_handle h, const uint32_t *d_packed, int64_t n_bases, int64_t *d_offsets, int32_t *d_ids,
+                   int64_t capacity, int64_t *d_count, void *stream)
+{
+    return match_list(h, d_packed, n_bases, d_offsets, d_ids, capacity, d_count, stream, true);
 }
 
 int pfac_device_status(pfac_handle h, int32_t *status, void *stream)

@@ -93,6 +93,7 @@ struct DeviceTable {
     const uint4 *dense;        // one skip entry per set filter bit
     int64_t n_states;
     int32_t max_len;
+    int32_t min_len;           // shortest pattern
     int32_t filter_b;          // 0 = no prefix filter
     int32_t rank_wide;
     int32_t *status;           // device status word (PFAC_OK or the first error)
@@ -133,17 +134,19 @@ int get_device_props(DeviceProps *p);
 int launch_pack(const uint8_t *text, int64_t len, uint32_t *packed, int32_t *status,
                 int64_t *bad, cudaStream_t st, const DeviceProps &dp);
 
-// Kernel 1 with either a dense output (c_off == nullptr) or a compacted match list.
+// Kernel 1 with either a dense output (c_off == nullptr) or a compacted match list;
+// all_matches: the list holds every pattern that ends on each walk, not only the longest.
 int launch_walk_rows_any(const DeviceTable &t, const void *text, bool packed, int64_t n,
                          int32_t *out, int64_t *c_off, int32_t *c_ids, int64_t cap,
-                         unsigned long long *count, cudaStream_t st, const DeviceProps &dp);
+                         unsigned long long *count, cudaStream_t st, const DeviceProps &dp,
+                         bool all_matches = false);
 
 // Kernel 2 (and its tail kernel). Dense output when c_off == nullptr, otherwise the
 // compacted match list.
 int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n, int32_t *out,
                  int64_t *c_off, int32_t *c_ids, int64_t cap, unsigned long long *count,
                  const TiledConfig &cfg, const DeferScratch &scratch, cudaStream_t st,
-                 const DeviceProps &dp);
+                 const DeviceProps &dp, bool all_matches = false);
 
 // Launch shape of the batched scan: offsets per lane (16 or 32; a work item is 32 x that),
 // 256-thread blocks per SM of the persistent scan kernel (1..8), dependent table loads a

@@ -132,18 +132,27 @@ __device__ __forceinline__ int base_code_or_neg(uint32_t b)
     return ok ? c : -1;
 }
 
-// Four ASCII bytes -> four 2-bit codes in the low 8 bits, plus a 4-bit mask of bytes
-// that are not A, C, G or T.
+// Four ASCII bytes -> four 2-bit codes in the low 8 bits (a byte outside ACGT codes as
+// A), plus a 4-bit mask of bytes that are not A, C, G or T. Byte-parallel arithmetic:
+//   t      the code each byte would have if it were a base (see base_code_or_neg);
+//   c8     t's four codes gathered into one byte by one multiply (the products of
+//          different bytes land below bit 24 or above bit 31, without carries);
+//   sel    the codes spread to one nibble each, a byte-permute selector that picks the
+//          byte each code stands for out of "ACGT";
+//   diff   zero exactly in the bytes that equal that byte, i.e. are bases;
+//   nz     bit 7 of each nonzero byte of diff (the zero-byte test), gathered into 4 bits
+//          by a second multiply.
+// Checked against the per-byte definition for all 2^32 inputs.
 __device__ __forceinline__ uint32_t pack4(uint32_t x, uint32_t *bad4)
 {
-    const uint32_t okA = __vcmpeq4(x, 0x41414141u), okC = __vcmpeq4(x, 0x43434343u);
-    const uint32_t okG = __vcmpeq4(x, 0x47474747u), okT = __vcmpeq4(x, 0x54545454u);
-    const uint32_t ok = okA | okC | okG | okT;           // 0xFF per valid byte
-    const uint32_t t = (((x >> 1) & 0x03030303u) ^ ((x >> 2) & 0x01010101u)) & ok;
-    const uint32_t codes = (t & 0x3u) | ((t >> 6) & 0xCu) | ((t >> 12) & 0x30u) | ((t >> 18) & 0xC0u);
-    const uint32_t bad = ~ok;
-    *bad4 = (bad & 1u) | ((bad >> 7) & 2u) | ((bad >> 14) & 4u) | ((bad >> 21) & 8u);
-    return codes;
+    const uint32_t t = ((x >> 1) & 0x03030303u) ^ ((x >> 2) & 0x01010101u);
+    const uint32_t c8 = (t * 0x01041040u) >> 24;
+    const uint32_t y = (c8 | (c8 << 4)) & 0x0F0Fu;
+    const uint32_t sel = (y | (y << 2)) & 0x3333u;
+    const uint32_t diff = x ^ __byte_perm(0x54474341u, 0u, sel);
+    const uint32_t nz = (((diff & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | diff) & 0x80808080u;
+    *bad4 = (nz * 0x00204081u) >> 28;
+    return ((t & ~((nz >> 7) * 0xFFu)) * 0x01041040u) >> 24;
 }
 
 // Sixteen ASCII bytes -> one packed word, plus a 16-bit mask of invalid bytes.
@@ -225,7 +234,9 @@ int launch_pack(const uint8_t *text, int64_t len, uint32_t *packed, int32_t *sta
 // and for unaligned buffers.
 // ---------------------------------------------------------------------------
 
-template <bool PACKED, bool COMPACT>
+// ALL: list every pattern that ends on the walk (each terminal state passed), not only
+// the longest, in the match list.
+template <bool PACKED, bool COMPACT, bool ALL = false>
 __global__ void __launch_bounds__(256) walk_rows_kernel(DeviceTable t, const void *__restrict__ text,
                                                         int64_t n, int32_t *__restrict__ out,
                                                         int64_t *__restrict__ c_off,
@@ -254,12 +265,22 @@ __global__ void __launch_bounds__(256) walk_rows_kernel(DeviceTable t, const voi
                 const int32_t e = __ldg(rows + 4 * (int64_t)s + c);
                 if (e == 0) break;
                 s = e & 0x7FFFFFFF;
-                if (e < 0) best = s;
+                if (e < 0) {
+                    if (ALL) {
+                        const unsigned long long kk = atomicAdd(count, 1ull);
+                        if ((int64_t)kk < cap) {
+                            c_off[kk] = i;
+                            c_ids[kk] = __ldg(t.out_id + s);
+                        }
+                    } else {
+                        best = s;
+                    }
+                }
             }
             res = best ? __ldg(t.out_id + best) : 0;
             if (!COMPACT) out[i] = res;
         }
-        if (COMPACT) {
+        if (COMPACT && !ALL) {
             const unsigned m = __ballot_sync(0xFFFFFFFFu, res != 0);
             if (m) {
                 const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
@@ -277,7 +298,7 @@ __global__ void __launch_bounds__(256) walk_rows_kernel(DeviceTable t, const voi
 
 int launch_walk_rows_any(const DeviceTable &t, const void *text, bool packed, int64_t n, int32_t *out,
                          int64_t *c_off, int32_t *c_ids, int64_t cap, unsigned long long *count,
-                         cudaStream_t st, const DeviceProps &dp)
+                         cudaStream_t st, const DeviceProps &dp, bool all_matches)
 {
     if (count && cudaMemsetAsync(count, 0, sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     if (n == 0) return PFAC_OK;
@@ -285,7 +306,10 @@ int launch_walk_rows_any(const DeviceTable &t, const void *text, bool packed, in
     const int64_t want = (n + threads - 1) / threads;
     const int blocks = (int)std::min<int64_t>(want, (int64_t)dp.num_sms * 8);
     const bool compact = c_off != nullptr;
-    if (packed) {
+    if (all_matches) {
+        if (packed) walk_rows_kernel<true, true, true><<<blocks, threads, 0, st>>>(t, text, n, out, c_off, c_ids, cap, count);
+        else walk_rows_kernel<false, true, true><<<blocks, threads, 0, st>>>(t, text, n, out, c_off, c_ids, cap, count);
+    } else if (packed) {
         if (compact) walk_rows_kernel<true, true><<<blocks, threads, 0, st>>>(t, text, n, out, c_off, c_ids, cap, count);
         else walk_rows_kernel<true, false><<<blocks, threads, 0, st>>>(t, text, n, out, c_off, c_ids, cap, count);
     } else {
@@ -447,38 +471,6 @@ __device__ __forceinline__ uint32_t text16(const void *__restrict__ text, const 
     return w;
 }
 
-// Continue a walk from state s with `q` bases consumed, reading the text from global
-// memory up to `end` (deferred walks, and walks the deferred list had no room for).
-// Returns the pattern id (0 if none).
-template <bool PACKED>
-__device__ int32_t walk_global(const DeviceTable &T, const void *__restrict__ text,
-                               const uint32_t *__restrict__ invalid, int64_t end, int64_t gp, uint32_t s, int q,
-                               uint32_t best)
-{
-    uint4 e = __ldg(T.skip + s);
-    for (;;) {
-        if (e.y & kSkipSelfTerm) best = s;
-        const uint32_t L = e.y & kSkipLenMask;
-        uint32_t bad;
-        const uint32_t win = text16<PACKED>(text, invalid, end, gp + q, &bad);
-        const uint32_t need = L ? L : 1u;
-        if (bad & ((need >= 16) ? 0xFFFFu : ((1u << need) - 1u))) break;   // cannot read the next step
-        if (L) {
-            if ((win ^ e.x) & base_mask(L)) break;
-            q += (int)L;
-            s = e.z;
-            if (e.y & kSkipTargetTerm) best = s;
-        } else {
-            const uint32_t c = win & 3u;
-            if (!((e.w >> c) & 1u)) break;
-            s = (e.w >> kNodeFirstShift) + __popc(e.w & ((1u << c) - 1u));
-            q++;
-        }
-        e = __ldg(T.skip + s);
-    }
-    return best ? __ldg(T.out_id + best) : 0;
-}
-
 // Where results go: the dense output array (whose slots already hold 0) or the match
 // list, plus the deferred-walk list.
 struct Sink {
@@ -506,6 +498,43 @@ __device__ __forceinline__ void emit_match(const Sink &K, int64_t gp, int32_t v)
     } else {
         K.out[gp] = v;
     }
+}
+
+// Continue a walk from state s with `q` bases consumed, reading the text from global
+// memory up to `end` (deferred walks, and walks the deferred list had no room for).
+// Returns the pattern id (0 if none). ALL: every terminal state reached from here goes
+// to the match list *K instead (each is met once, at the top of the loop) and 0 is
+// returned.
+template <bool PACKED, bool ALL = false>
+__device__ int32_t walk_global(const DeviceTable &T, const void *__restrict__ text,
+                               const uint32_t *__restrict__ invalid, int64_t end, int64_t gp, uint32_t s, int q,
+                               uint32_t best, const Sink *K = nullptr)
+{
+    uint4 e = __ldg(T.skip + s);
+    for (;;) {
+        if (e.y & kSkipSelfTerm) {
+            if (ALL) emit_match<true>(*K, gp, __ldg(T.out_id + s));
+            else best = s;
+        }
+        const uint32_t L = e.y & kSkipLenMask;
+        uint32_t bad;
+        const uint32_t win = text16<PACKED>(text, invalid, end, gp + q, &bad);
+        const uint32_t need = L ? L : 1u;
+        if (bad & ((need >= 16) ? 0xFFFFu : ((1u << need) - 1u))) break;   // cannot read the next step
+        if (L) {
+            if ((win ^ e.x) & base_mask(L)) break;
+            q += (int)L;
+            s = e.z;
+            if (!ALL && (e.y & kSkipTargetTerm)) best = s;
+        } else {
+            const uint32_t c = win & 3u;
+            if (!((e.w >> c) & 1u)) break;
+            s = (e.w >> kNodeFirstShift) + __popc(e.w & ((1u << c) - 1u));
+            q++;
+        }
+        e = __ldg(T.skip + s);
+    }
+    return (!ALL && best) ? __ldg(T.out_id + best) : 0;
 }
 
 // Mask of positions j < 32 (bit j) such that bits j .. j+w-1 of `bad` are all clear.
@@ -599,7 +628,7 @@ __device__ __forceinline__ void zero_batch(const Sink &K, int64_t warp_base, int
 // dense entry of their b-mer (unless that entry is marked special) at depth b; else at
 // the root. It goes on through skip entries inside the window with at most walk_loads
 // dependent table loads; a longer walk is deferred to the tail kernel.
-template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16>
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, bool ALL = false>
 __device__ __forceinline__ void walk_item(const DeviceTable &T, const Sink &K, const uint32_t *sf, const void *srank,
                                           int walk_loads, uint32_t set_index, const void *text,
                                           const uint32_t *invalid, int64_t end, int64_t gp, uint32_t x0, uint32_t x1,
@@ -630,7 +659,11 @@ __device__ __forceinline__ void walk_item(const DeviceTable &T, const Sink &K, c
     if (from_root) e = __ldg(T.skip);
     bool defer = false;
     for (int loads = 1;; loads++) {
-        if (e.y & kSkipSelfTerm) best = s;
+        // every state the walk enters is met here once (ALL lists each terminal one)
+        if (e.y & kSkipSelfTerm) {
+            if (ALL) emit_match<true>(K, gp, __ldg(T.out_id + s));
+            else best = s;
+        }
         const uint32_t L = e.y & kSkipLenMask;
         const int need = L ? (int)L : 1;
         if (q + need > wlim) {
@@ -642,7 +675,7 @@ __device__ __forceinline__ void walk_item(const DeviceTable &T, const Sink &K, c
             if ((win ^ e.x) & base_mask(L)) break;
             q += (int)L;
             s = e.z;
-            if (e.y & kSkipTargetTerm) best = s;
+            if (!ALL && (e.y & kSkipTargetTerm)) best = s;
         } else {
             const uint32_t c = win & 3u;
             if (!((e.w >> c) & 1u)) break;
@@ -662,14 +695,14 @@ __device__ __forceinline__ void walk_item(const DeviceTable &T, const Sink &K, c
             DeferItem it;
             it.gp = gp;
             it.s = s;
-            it.best = best;
+            it.best = ALL ? 0u : best;
             it.q_set = (uint32_t)q | (set_index << 16);
             it.span = (int32_t)min(end - gp, (int64_t)0x7FFFFFFF);
             K.defer[di] = it;
         } else {
-            emit_match<COMPACT>(K, gp, walk_global<PACKED>(T, text, invalid, end, gp, s, q, best));
+            emit_match<COMPACT>(K, gp, walk_global<PACKED, ALL>(T, text, invalid, end, gp, s, q, best, &K));
         }
-    } else if (best) {
+    } else if (!ALL && best) {
         emit_match<COMPACT>(K, gp, __ldg(T.out_id + best));
     }
 }
@@ -682,7 +715,7 @@ __device__ __forceinline__ void walk_item(const DeviceTable &T, const Sink &K, c
 // offset order, goes to lane r mod 32 in round r / 32, with the owner's window by
 // shuffle) and walked at once. Used for ASCII text and for batched reads.
 // sf / srank: filter and rank index in shared memory, or nullptr for global memory.
-template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW>
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW, bool ALL = false>
 __device__ __forceinline__ void scan_lane_batch(const DeviceTable &T, const Sink &K, const uint32_t *sf,
                                                 const void *srank, int walk_loads, uint32_t set_index,
                                                 const void *text, const uint32_t *invalid, int64_t end,
@@ -693,7 +726,10 @@ __device__ __forceinline__ void scan_lane_batch(const DeviceTable &T, const Sink
     const uint32_t bmask = (uint32_t)((1ull << (2 * B)) - 1ull);
     const uint32_t fast = clear_runs(bad, B) & valid;   // the b-mer is readable
     uint32_t pend = filter_bits<FSMEM, LW>(T, sf, x0, x1, x2, bmask) & fast;
-    pend |= valid & ~fast;     // these walk from the root
+    // Offsets whose b bases cannot all be read (a byte outside ACGT, or the end of the
+    // text or read, within b bases) walk from the root, unless fewer bases than the
+    // shortest pattern can be read: then no pattern starts there.
+    if (T.min_len < B) pend |= valid & ~fast & clear_runs(bad, T.min_len);
 
     if (!COMPACT) zero_batch<LW>(K, warp_base, lane, valid, vec_ok, pol);
     // The zeros above were stored by one lane and a match found below is stored by
@@ -738,7 +774,7 @@ __device__ __forceinline__ void scan_lane_batch(const DeviceTable &T, const Sink
         // bases readable from the window; `ends` when the text (or the run of ACGT
         // bytes) really stops there rather than the window
         const int wlim = badj ? __ffsll((long long)badj) - 1 : 64 - j;
-        walk_item<PACKED, COMPACT, FSMEM, RANK16>(T, K, sf, srank, walk_loads, set_index, text, invalid, end, gp,
+        walk_item<PACKED, COMPACT, FSMEM, RANK16, ALL>(T, K, sf, srank, walk_loads, set_index, text, invalid, end, gp,
                                                   ox0, ox1, ox2, ox3, j, wlim, badj != 0, (ofast >> j) & 1u);
     }
 }
@@ -746,7 +782,7 @@ __device__ __forceinline__ void scan_lane_batch(const DeviceTable &T, const Sink
 // Walk `count` (<= 32) queued offsets of packed text, one per lane. Each lane reads the
 // 64 bases from its offset straight from the packed text (an L2 hit: the tile was
 // staged moments ago), so nothing moves between lanes.
-template <bool COMPACT, bool FSMEM, bool RANK16>
+template <bool COMPACT, bool FSMEM, bool RANK16, bool ALL = false>
 __device__ __forceinline__ void queue_round(const ScanParams &P, const Sink &K, const uint32_t *sf,
                                             const void *srank, const volatile uint32_t *queue, uint32_t head, uint32_t count,
                                             int lane)
@@ -765,11 +801,11 @@ __device__ __forceinline__ void queue_round(const ScanParams &P, const Sink &K, 
     const uint32_t x0 = __funnelshift_r(w[0], w[1], sh), x1 = __funnelshift_r(w[1], w[2], sh);
     const uint32_t x2 = __funnelshift_r(w[2], w[3], sh), x3 = __funnelshift_r(w[3], w[4], sh);
     const int wlim = rem < 64 ? (int)rem : 64;
-    walk_item<true, COMPACT, FSMEM, RANK16>(P.t, K, sf, srank, P.walk_loads, 0u, P.text, nullptr, P.n, gp, x0, x1,
+    walk_item<true, COMPACT, FSMEM, RANK16, ALL>(P.t, K, sf, srank, P.walk_loads, 0u, P.text, nullptr, P.n, gp, x0, x1,
                                             x2, x3, 0, wlim, rem <= 64, wlim >= P.t.filter_b);
 }
 
-template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW>
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW, bool ALL = false>
 __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -891,7 +927,9 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             }
             const uint32_t fast = bad ? clear_runs(bad, B) & valid : valid;   // the b-mer is readable
             uint32_t pend = filter_bits<FSMEM, LW>(T, sf, x0, x1, x2, bmask) & fast;
-            pend |= valid & ~fast;     // these walk from the root
+            // near the text end: offsets with fewer than b readable bases walk from the
+            // root when a pattern shorter than b could still fit
+            if (T.min_len < B) pend |= valid & ~fast & clear_runs(bad, T.min_len);
             // Release the stage only once every lane has used its words: the producer
             // refills it as soon as all consumer warps have arrived, and a word read
             // after that would come from the next fill.
@@ -928,7 +966,7 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                 total -= take;
                 __syncwarp();
                 while (qcount >= 32) {
-                    queue_round<COMPACT, FSMEM, RANK16>(P, K, sf, rank_ptr, queue, qhead, 32, lane);
+                    queue_round<COMPACT, FSMEM, RANK16, ALL>(P, K, sf, rank_ptr, queue, qhead, 32, lane);
                     qhead = (qhead + 32) & (kQueue - 1);
                     qcount -= 32;
                     __syncwarp();   // the entries just read may be written again
@@ -950,16 +988,16 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             // release the stage once every lane has used its bytes (see the packed path)
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_addr(&empty[st]));
-            scan_lane_batch<PACKED, COMPACT, FSMEM, RANK16, LW>(T, K, sf, rank_ptr, P.walk_loads, 0u, P.text,
+            scan_lane_batch<PACKED, COMPACT, FSMEM, RANK16, LW, ALL>(T, K, sf, rank_ptr, P.walk_loads, 0u, P.text,
                                                                 nullptr, n, warp_base, lane, x0, x1, x2, x3, bad,
                                                                 valid, true, pol);
         }
     }
-    if (PACKED && qcount) queue_round<COMPACT, FSMEM, RANK16>(P, K, sf, rank_ptr, queue, qhead, qcount, lane);
+    if (PACKED && qcount) queue_round<COMPACT, FSMEM, RANK16, ALL>(P, K, sf, rank_ptr, queue, qhead, qcount, lane);
 }
 
 // Deferred walks: one thread per item.
-template <bool PACKED, bool COMPACT>
+template <bool PACKED, bool COMPACT, bool ALL = false>
 __global__ void __launch_bounds__(256) tail_kernel(const ScanParams P)
 {
     const unsigned long long cnt = *P.defer_count;
@@ -972,8 +1010,8 @@ __global__ void __launch_bounds__(256) tail_kernel(const ScanParams P)
         K.c_ids = P.c_ids;
         K.cap = P.cap;
         K.count = P.count;
-        emit_match<COMPACT>(K, it.gp, walk_global<PACKED>(P.t, P.text, nullptr, it.gp + it.span, it.gp, it.s,
-                                                          (int)(it.q_set & 0xFFFFu), it.best));
+        emit_match<COMPACT>(K, it.gp, walk_global<PACKED, ALL>(P.t, P.text, nullptr, it.gp + it.span, it.gp, it.s,
+                                                               (int)(it.q_set & 0xFFFFu), it.best, &K));
     }
 }
 
@@ -1105,33 +1143,33 @@ static cudaError_t launch_with_policy(Kern kern, const ScanParams &P, int grid, 
     return cudaLaunchKernelEx(&lc, kern, P);
 }
 
-template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16>
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, bool ALL>
 static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t smem, int tail_grid, cudaStream_t st,
                          const TiledConfig &cfg, const DeviceProps &dp)
 {
-    auto kern = lane_width_of(cfg) == 32 ? scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32>
-                                         : scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 16>;
+    auto kern = lane_width_of(cfg) == 32 ? scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL>
+                                         : scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 16, ALL>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return PFAC_ERR_CUDA;
     if (launch_with_policy(kern, P, grid, threads, smem, st, cfg, dp) != cudaSuccess) return PFAC_ERR_CUDA;
-    tail_kernel<PACKED, COMPACT><<<tail_grid, 256, 0, st>>>(P);
+    tail_kernel<PACKED, COMPACT, ALL><<<tail_grid, 256, 0, st>>>(P);
     return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
 }
 
-template <bool PACKED, bool COMPACT>
+template <bool PACKED, bool COMPACT, bool ALL = false>
 static int launch_scan_w(const ScanParams &P, bool fsmem, bool rank16, int grid, int threads, uint32_t smem,
                          int tail_grid, cudaStream_t st, const TiledConfig &cfg, const DeviceProps &dp)
 {
     if (fsmem)
-        return rank16 ? launch_scan_t<PACKED, COMPACT, true, true>(P, grid, threads, smem, tail_grid, st, cfg, dp)
-                      : launch_scan_t<PACKED, COMPACT, true, false>(P, grid, threads, smem, tail_grid, st, cfg, dp);
-    return rank16 ? launch_scan_t<PACKED, COMPACT, false, true>(P, grid, threads, smem, tail_grid, st, cfg, dp)
-                  : launch_scan_t<PACKED, COMPACT, false, false>(P, grid, threads, smem, tail_grid, st, cfg, dp);
+        return rank16 ? launch_scan_t<PACKED, COMPACT, true, true, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp)
+                      : launch_scan_t<PACKED, COMPACT, true, false, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp);
+    return rank16 ? launch_scan_t<PACKED, COMPACT, false, true, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp)
+                  : launch_scan_t<PACKED, COMPACT, false, false, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp);
 }
 
 int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n, int32_t *out, int64_t *c_off,
                  int32_t *c_ids, int64_t cap, unsigned long long *count, const TiledConfig &cfg,
-                 const DeferScratch &scratch, cudaStream_t st, const DeviceProps &dp)
+                 const DeferScratch &scratch, cudaStream_t st, const DeviceProps &dp, bool all_matches)
 {
     const bool compact = c_off != nullptr;
     if (compact && cudaMemsetAsync(count, 0, sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
@@ -1181,6 +1219,10 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     const int tail_grid = dp.num_sms * 4;
     const bool fsmem = pl.filter_bytes > 0;
     const bool rank16 = !t.rank_wide;
+    if (all_matches) {   // the match list of every pattern on every walk (packed text only)
+        if (!packed || !compact) return PFAC_ERR_INVALID_ARG;
+        return launch_scan_w<true, true, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp);
+    }
     if (packed)
         return compact ? launch_scan_w<true, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp)
                        : launch_scan_w<true, false>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp);
@@ -1194,7 +1236,8 @@ size_t defer_item_bytes() { return sizeof(DeferItem); }
 // Batched scan: many reads of uneven length, each against its own table, in one
 // persistent launch (plus the pack, plan and tail kernels around it).
 //   pack_bits_kernel    ASCII reads -> 2-bit words + one invalid bit per base
-//   plan_kernel         reads -> first work item of each read (512 offsets per item)
+//   plan_kernel         reads -> first work item of each read (512 or 1024 offsets per
+//                       item), and the read of every work item
 //   batched_scan_kernel warps take items from a counter; each item runs the same
 //                       per-warp filter test and skip walks as kernel 2, with its
 //                       read's table and every walk bounded by its read's end
@@ -1213,6 +1256,8 @@ struct BatchParams {
     const int32_t *read_set;
     int32_t n_reads;
     const int64_t *item_start;
+    const int32_t *item_read;    // read of each work item, for the first item_cap items
+    int64_t item_cap;
     unsigned long long *item_next;
     int32_t item;                // offsets per work item (32 x LW)
     int32_t *out;
@@ -1259,7 +1304,8 @@ __device__ __forceinline__ void read_bounds(const int64_t *read_off, int32_t r, 
 
 // One CTA: exclusive prefix of the number of work items per read.
 __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ read_off, int32_t n_reads, int64_t n,
-                                                    int32_t item, int64_t *__restrict__ item_start)
+                                                    int32_t item, int64_t *__restrict__ item_start,
+                                                    int32_t *__restrict__ item_read, int64_t item_cap)
 {
     __shared__ int64_t warp_sum[32];
     __shared__ int64_t carry;
@@ -1297,6 +1343,12 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         __syncthreads();
     }
     if (tid == 0) item_start[n_reads] = carry;
+    __syncthreads();
+    // the read of each work item (items past item_cap are found by search instead)
+    for (int64_t r = tid; r < n_reads; r += blockDim.x) {
+        const int64_t k1 = min(item_start[r + 1], item_cap);
+        for (int64_t k = item_start[r]; k < k1; k++) item_read[k] = (int32_t)r;
+    }
 }
 
 template <int LW>
@@ -1319,12 +1371,18 @@ __global__ void __launch_bounds__(256) batched_scan_kernel(const BatchParams P)
         if (lane == 0) it = atomicAdd(P.item_next, 1ull);
         it = __shfl_sync(0xFFFFFFFFu, it, 0);
         if ((int64_t)it >= total) break;
-        // the read holding item `it`: the last r with item_start[r] <= it
-        int32_t lo = 0, hi = P.n_reads - 1;
-        while (lo < hi) {
-            const int32_t mid = (int32_t)(((int64_t)lo + hi + 1) >> 1);
-            if (P.item_start[mid] <= (int64_t)it) lo = mid;
-            else hi = mid - 1;
+        // the read holding item `it`: the last r with item_start[r] <= it, from the plan's
+        // map, or by search past its capacity (reads that overlap one another)
+        int32_t lo = 0;
+        if ((int64_t)it < P.item_cap) {
+            lo = P.item_read[it];
+        } else {
+            int32_t hi = P.n_reads - 1;
+            while (lo < hi) {
+                const int32_t mid = (int32_t)(((int64_t)lo + hi + 1) >> 1);
+                if (P.item_start[mid] <= (int64_t)it) lo = mid;
+                else hi = mid - 1;
+            }
         }
         int64_t rs, re;
         read_bounds(P.read_off, lo, P.n, &rs, &re);
@@ -1376,11 +1434,16 @@ __global__ void __launch_bounds__(256) batched_tail_kernel(const BatchParams P)
     }
 }
 
+// Work items of reads that do not overlap: at most one partial item per read plus one
+// per 512 bases.
+static int64_t item_capacity(int64_t n, int32_t n_reads) { return n / 512 + (int64_t)n_reads + 1; }
+
 int64_t batch_scratch_bytes(int64_t n, int32_t n_reads, int64_t defer_cap)
 {
     const int64_t words = (n + 15) / 16, bw = (n + 31) / 32;
     return 256 + ((words * 4 + 255) & ~255LL) + (((bw + 1) * 4 + 255) & ~255LL) +
-           ((((int64_t)n_reads + 1) * 8 + 255) & ~255LL) + defer_cap * (int64_t)sizeof(DeferItem);
+           ((((int64_t)n_reads + 1) * 8 + 255) & ~255LL) + ((item_capacity(n, n_reads) * 4 + 255) & ~255LL) +
+           defer_cap * (int64_t)sizeof(DeferItem);
 }
 
 int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *texts, int64_t n, const int64_t *read_off,
@@ -1400,11 +1463,14 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
     p += ((bw + 1) * 4 + 255) & ~255LL;
     int64_t *item_start = (int64_t *)p;
     p += ((((int64_t)n_reads + 1) * 8) + 255) & ~255LL;
+    const int64_t item_cap = item_capacity(n, n_reads);
+    int32_t *item_read = (int32_t *)p;
+    p += (item_cap * 4 + 255) & ~255LL;
     DeferItem *defer = (DeferItem *)p;
     if (cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     const int pack_blocks = (int)std::min<int64_t>((bw + 255) / 256, (int64_t)dp.num_sms * 16);
     pack_bits_kernel<<<std::max(1, pack_blocks), 256, 0, st>>>(texts, n, packed, invalid);
-    plan_kernel<<<1, 1024, 0, st>>>(read_off, n_reads, n, 32 * lw, item_start);
+    plan_kernel<<<1, 1024, 0, st>>>(read_off, n_reads, n, 32 * lw, item_start, item_read, item_cap);
     BatchParams P{};
     P.sets = d_sets;
     P.n_sets = n_sets;
@@ -1415,6 +1481,8 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
     P.read_set = read_set;
     P.n_reads = n_reads;
     P.item_start = item_start;
+    P.item_read = item_read;
+    P.item_cap = item_cap;
     P.item_next = counters;
     P.out = out;
     P.defer = defer;

@@ -359,3 +359,39 @@ def request_stream(seed: int = 5, rate: float = 2000.0, duration: float = 2.0, n
                          f"{text_range[0]}-{text_range[1]} bases",
                          arrivals, set_id, starts, lengths, source, sets,
                          {"seed": seed, "set_sizes": sizes.tolist()})
+
+
+# ----------------------------------------------------------------------------
+# The paper's own workload shape (Tables III and IV), standing in for its files:
+# pattern sets of 1,000-5,000 patterns of about 100 bases, and input data sets of
+# 0.75-3.75 million newline-separated lines of about 100 bases (about 101 bytes per
+# line with its newline: 76-380 MB).
+# ----------------------------------------------------------------------------
+
+PAPER_LINE = 100          # bases per line of an input data set
+PAPER_PATTERN = 100       # bases per pattern
+
+
+def paper_source(seed: int = 6, n_bases: int = 64 << 20) -> np.ndarray:
+    """The genome-like source that lines and patterns are cut from (41 %-GC order-2
+    chain)."""
+    return markov2_text(n_bases, rng_for(seed), 0.41)
+
+
+def paper_input(source: np.ndarray, n_lines: int, seed: int = 7, line: int = PAPER_LINE) -> np.ndarray:
+    """``n_lines`` lines of ``line`` bases cut at uniform offsets of ``source``, each
+    followed by a newline (ASCII uint8). A newline has no edge in the trie, so no walk
+    crosses from one line into the next."""
+    rng = rng_for(seed)
+    starts = (rng.random(n_lines) * (source.shape[0] - line + 1)).astype(np.int64)
+    out = np.empty((n_lines, line + 1), dtype=np.uint8)
+    idx = starts[:, None] + np.arange(line)[None, :]
+    out[:, :line] = source[idx]
+    out[:, line] = ord("\n")
+    return out.reshape(-1)
+
+
+def paper_patterns(source: np.ndarray, n: int, seed: int = 8, length: int = PAPER_PATTERN):
+    """``n`` patterns of ``length`` bases: half copies of ``source`` at uniform offsets,
+    half i.i.d. at 41 % GC. Returned as ``(blob, offsets)``."""
+    return pattern_set(source, rng_for(seed), n, (length, length), 0.5, GC41)

@@ -7,7 +7,8 @@ max_len - 1 bases of the next chunk, so every walk that starts inside the chunk 
 the bases it can use; only the chunk's own ids are copied back. Two sets of device
 buffers alternate between chunks; events keep each buffer from being refilled before
 the stream that reads it is done. The scan itself is the library's ``pfac_pack`` and
-``pfac_match_packed``; Python only orders the calls.
+``pfac_match_packed`` (or ``pfac_match`` on the ASCII bytes, for texts that hold bytes
+outside A/C/G/T such as newline-separated reads); Python only orders the calls.
 """
 from __future__ import annotations
 
@@ -17,10 +18,13 @@ from . import _binding as b
 class HostScanner:
     """Device buffers and streams for chunked scans of host texts with one table."""
 
-    def __init__(self, table, chunk_bases: int = 1 << 26, device="cuda"):
+    def __init__(self, table, chunk_bases: int = 1 << 26, device="cuda", ascii: bool = False):
+        """ascii: scan the ASCII bytes with pfac_match (any byte allowed; bytes outside
+        A/C/G/T end walks) instead of packing them first."""
         import torch
         self.torch = torch
         self.table = table
+        self.ascii = bool(ascii)
         self.max_len = int(table.info["max_len"])
         self.chunk = max(16, (int(chunk_bases) + 15) // 16 * 16)
         span = self.chunk + self.max_len + 16
@@ -40,8 +44,9 @@ class HostScanner:
     def scan(self, h_text, h_out):
         """Longest-pattern ids of the ASCII host tensor ``h_text`` (uint8, ideally pinned)
         into the host tensor ``h_out`` (int32, same length, ideally pinned). Returns when
-        the last copy is queued; ``synchronize()`` waits for it. Bytes that are not A, C,
-        G or T are rejected by the pack step (status checked at the end)."""
+        the last copy is queued; ``synchronize()`` waits for it. Unless the scanner was made
+        with ascii=True, bytes that are not A, C, G or T are rejected by the pack step
+        (status checked at the end)."""
         torch = self.torch
         n = int(h_text.numel())
         if h_out.numel() != n:
@@ -62,8 +67,11 @@ class HostScanner:
             self.s_scan.wait_event(self.ev_in[k])
             self.s_scan.wait_event(self.ev_out[k])
             with torch.cuda.stream(self.s_scan):
-                b.pfac_pack(self.d_text[k][:m], self.d_packed[k], status[i:i + 1], None, self.s_scan)
-                b.pfac_match_packed(self.table.h, self.d_packed[k], m, self.d_out[k], self.s_scan)
+                if self.ascii:
+                    b.pfac_match(self.table.h, self.d_text[k], self.d_out[k], self.s_scan, length=m)
+                else:
+                    b.pfac_pack(self.d_text[k][:m], self.d_packed[k], status[i:i + 1], None, self.s_scan)
+                    b.pfac_match_packed(self.table.h, self.d_packed[k], m, self.d_out[k], self.s_scan)
                 self.ev_scan[k].record(self.s_scan)
             self.s_out.wait_event(self.ev_scan[k])
             with torch.cuda.stream(self.s_out):
@@ -80,12 +88,12 @@ class HostScanner:
         return int(st.max().item()) if st is not None else 0
 
 
-def scan_host(table, h_text, h_out=None, chunk_bases: int = 1 << 26):
+def scan_host(table, h_text, h_out=None, chunk_bases: int = 1 << 26, ascii: bool = False):
     """One-shot form of ``HostScanner``: returns the host int32 ids of ``h_text``."""
     import torch
     if h_out is None:
         h_out = torch.empty(h_text.numel(), dtype=torch.int32, pin_memory=True)
-    sc = HostScanner(table, chunk_bases, device="cuda")
+    sc = HostScanner(table, chunk_bases, device="cuda", ascii=ascii)
     sc.scan(h_text, h_out)
     rc = sc.synchronize()
     if rc != 0:

@@ -220,5 +220,34 @@ def check_invariants(lib, n_bases: int = 30000, n_pats: int = 300, seed: int = 1
             assert raw[i:i + L] not in by_len[L], (i, L)
 
 
+def check_fig1_all(lib):
+    """Hand-worked all-match lists with the Fig. 1 patterns: every pattern occurrence,
+    sub-patterns included, at its start offset."""
+    rows = _golden("fig1_all.txt")
+    pats = _patterns(rows)
+    for r in rows:
+        if r[0] != "all":
+            continue
+        want = [tuple(int(v) for v in pair.split(":")) for pair in r[2:]]
+        s, i = oracle.all_matches(pats, r[1].encode(), lib=lib)
+        assert list(zip(s.tolist(), i.tolist())) == want, (r[1], want)
+
+
+def check_all_matches_random_tiny(lib, cases: int = 300, seed: int = 17):
+    """The all-match list == brute force over every start and pattern; its longest
+    entry per start == the PFAC scan."""
+    rng = random.Random(seed)
+    for _ in range(cases):
+        text, pats = random_case(rng)
+        s, i = oracle.all_matches(pats, text, lib=lib)
+        got = list(zip(s.tolist(), i.tolist()))
+        assert got == brute.brute_all(text, pats), (text, pats)
+        longest = [0] * len(text)
+        for start, pid in got:            # sorted by length within a start
+            longest[start] = pid
+        assert longest == brute.brute_longest(text, pats), (text, pats)
+
+
 ALL_PINS = [check_fig1_numbering, check_table1, check_fig2_failure, check_fig1_scans,
-            check_random_tiny, check_special_cases, check_invariants]
+            check_random_tiny, check_special_cases, check_invariants, check_fig1_all,
+            check_all_matches_random_tiny]

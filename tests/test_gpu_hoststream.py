@@ -48,3 +48,18 @@ def test_bad_symbol_is_reported(genome):
     text[250_000] = ord("N")
     with pytest.raises(b.PfacError):
         scan_host(t, torch.from_numpy(text), chunk_bases=1 << 16)
+
+
+def test_ascii_chunks_with_newline_separated_reads():
+    """The paper's input shape: lines of 100 bases, each ending in a newline, scanned as
+    ASCII (a newline ends every walk)."""
+    torch = require_cuda()
+    src = datagen.paper_source(n_bases=1 << 16)     # lines overlap, so patterns recur
+    text = datagen.paper_input(src, 20_000)
+    blob, offs = datagen.paper_patterns(src, 1000)
+    t = b.Table((blob, offs))
+    want = oracle.Trie((blob, offs)).scan(text)
+    got = scan_host(t, torch.from_numpy(text), chunk_bases=(1 << 18) + 16, ascii=True).numpy()
+    assert np.array_equal(got, want), first_diff(got, want)
+    assert (want != 0).sum() > 100
+    t.close()

@@ -220,6 +220,36 @@ def test_pack_matches_definition(n):
     assert int(status.item()) == 0 and int(first_bad.item()) == -1
 
 
+def test_pack_every_byte_value():
+    """Every byte value at every position of a packed word: bases pack to their codes,
+    other bytes pack as A and the first of them is reported."""
+    import torch
+    rng = np.random.default_rng(3)
+    vals = np.arange(256, dtype=np.uint8)
+    text = np.concatenate([np.roll(vals, k) for k in range(16)] + [rng.integers(0, 256, 4099, dtype=np.uint8)])
+    words, first = oracle.pack(text)
+    packed, status, first_bad = b.pack(to_dev(text))
+    torch.cuda.synchronize()
+    assert np.array_equal(packed.cpu().numpy().view(np.uint32), words)
+    assert int(status.item()) == b.CODE["PFAC_ERR_BAD_SYMBOL"] and int(first_bad.item()) == first
+
+
+def test_ascii_scan_with_every_byte_value():
+    """ASCII texts mixing bases with every other byte value (lowercase, N, newline, high
+    bytes): a walk stops at any non-base byte."""
+    rng = np.random.default_rng(4)
+    base = datagen.iid_text(200_000, datagen.rng_for(12))
+    noise = rng.integers(0, 256, base.size, dtype=np.uint8)
+    text = np.where(rng.random(base.size) < 0.03, noise, base).astype(np.uint8)
+    pats = [base[i:i + L].tobytes() for i, L in zip(rng.integers(0, base.size - 40, 300), rng.integers(3, 30, 300))]
+    want = ref(text, pats)
+    t = b.Table(pats)
+    for kernel in (1, 2):
+        got = gpu_match(t, text, kernel=kernel)
+        assert np.array_equal(got, want), (kernel, first_diff(got, want))
+    assert (want != 0).sum() > 500
+
+
 def test_pack_reports_first_bad_symbol():
     import torch
     text = np.frombuffer(b"ACGT" * 100 + b"ACGN" + b"ACGT" * 10 + b"x", dtype=np.uint8)
