@@ -105,8 +105,12 @@ class ClockSampler:
 
 
 def kernel_source_hash():
-    p = os.path.join(ROOT, "paper_1811_10498_gb300", "csrc", "pfac_kernels.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """SHA-256 (first 16 hex digits) of the scan kernels' sources: pfac_kernels.cu, then
+    pfac_device.cuh."""
+    h = hashlib.sha256()
+    for f in ("pfac_kernels.cu", "pfac_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1811_10498_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic():
@@ -212,6 +216,62 @@ def batched_measure(steps: int):
             "autotune": {k: tuned.get(k) for k in ("lane_offsets", "threads", "ctas_per_sm", "walk_loads",
                                                    "ms", "default_ms", "candidates")},
             "launches_per_batch": 4, "launches_per_read_pass": 2 * int(len(w.read_set))}
+
+
+def large_dict_measure(steps: int):
+    """The large-dictionary workload: 2^30 i.i.d. bases at 41 % GC against 10^6 patterns
+    of 16-64 bases (a trie of tens of millions of states, held in HBM); dense ids and
+    the compacted (offset, id) list, each timed over `steps` launches with the L2
+    flushed before each."""
+    import torch
+    from paper_1811_10498_gb300 import _binding as b
+    from paper_1811_10498_gb300 import datagen
+    w = datagen.large_dict_scan(seed=3)
+    n = int(w.text.size)
+    t0 = time.perf_counter()
+    table = b.Table((w.blob, w.offsets))
+    build_s = time.perf_counter() - t0
+    info = table.info
+    d_text = torch.from_numpy(w.text).cuda()
+    packed, status, _ = b.pack(d_text)
+    del d_text
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    cap = 1 << 24
+    d_off = torch.empty(cap, dtype=torch.int64, device="cuda")
+    d_ids = torch.empty(cap, dtype=torch.int32, device="cuda")
+    d_cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    dense_ms = timed(lambda: b.pfac_match_packed(table.h, packed, n, out))
+    compact_ms = timed(lambda: b.pfac_match_compact(table.h, packed, n, d_off, d_ids, d_cnt))
+    matches = int(d_cnt.item())
+    same = matches <= cap and int((out != 0).sum().item()) == matches
+    peak, _ = measured_hbm()
+    res = {"workload": w.name, "bases": n, "n_states": info["n_states"], "filter_b": info["filter_b"],
+           "table_bytes": info["table_bytes"], "table_build_s": build_s,
+           "dense_ms": dense_ms, "dense_gbases_s": n / dense_ms / 1e6,
+           "dense_roofline_frac": BYTES_PER_BASE * n / (dense_ms * 1e-3) / (peak * 1e9),
+           "compact_ms": compact_ms, "compact_gbases_s": n / compact_ms / 1e6, "matches": matches,
+           "compact_count_equals_dense_nonzeros": same,
+           "config": b.pfac_get_config(table.h, n)}
+    table.close()
+    return res
 
 
 def serving_measure(seconds: float):
@@ -359,6 +419,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the large-dictionary (10^6 patterns) leg")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--no-tune", action="store_true", help="use the library's default launch configuration")
     ap.add_argument("--suite", default=None, choices=["paper"],
@@ -510,6 +571,8 @@ def main():
             "extra": {"pack_gbases_s": pack_gbs, "build_s": build_s,
                       "frac_of_roofline_gbases": value / world / (peak / BYTES_PER_BASE)},
         }
+        if not args.no_large:
+            line["large_dictionary"] = large_dict_measure(10)
         if not args.no_batched:
             line["batched"] = batched_measure(20)
         if not args.no_serving:
