@@ -133,3 +133,28 @@ def test_bad_table_index_is_reported():
     torch.cuda.synchronize()
     assert out[:4].cpu().numpy().tolist() == [1, 0, 0, 0]
     assert b.pfac_device_status(tables[0].h) == b.CODE["PFAC_ERR_INVALID_ARG"]
+
+
+def test_many_tables_and_filters_of_every_size():
+    """300 tables with filters of orders 1-12 next to one another in one batch."""
+    rng = np.random.default_rng(31)
+    src = datagen.markov2_text(1 << 20, datagen.rng_for(31))
+    sets, tables = [], []
+    for k in range(300):
+        size = int(rng.integers(1, 400))
+        blob, offs = datagen.pattern_set(src, datagen.rng_for(100 + k), size, (4, 40), 0.7)
+        sets.append((blob, offs))
+        fb = 12 if k % 50 == 0 else (int(rng.integers(1, 10)) if k % 7 == 0 else 0)
+        tables.append(b.Table((blob, offs), filter_b=fb))
+    lens = rng.integers(0, 3000, 900)
+    offs = np.zeros(lens.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=offs[1:])
+    starts = rng.integers(0, src.size - 3000, lens.size)
+    reads = np.concatenate([src[s0:s0 + L] for s0, L in zip(starts, lens)]).astype(np.uint8)
+    read_set = rng.integers(0, len(sets), lens.size).astype(np.int32)
+    want = oracle.pfac_scan_reads(reads, offs, read_set, sets)
+    got = run_batched(tables, reads, offs, read_set)
+    assert np.array_equal(got, want), first_diff(got, want)
+    assert (want != 0).sum() > 1000
+    for t in tables:
+        t.close()
