@@ -134,6 +134,21 @@ def profiled_traffic():
         return None
 
 
+def job_throughput(local_s: float, n_per_rank: int, steps: int, world: int, device=None):
+    """Whole-job Gbases/s under weak scaling: every rank scans its own text of
+    `n_per_rank` bases `steps` times; the job takes as long as its slowest rank (max of
+    the ranks' timed totals over the process group, which must be initialised when
+    world > 1). Returns (slowest total seconds, Gbases/s)."""
+    total_s = local_s
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([local_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return total_s, world * n_per_rank * steps / total_s / 1e9
+
+
 def make_workload(rank: int, n_bases: int, n_patterns: int):
     from paper_1811_10498_gb300 import datagen
     return datagen.genome_scan(seed=2 + rank, n_bases=n_bases, n_patterns=n_patterns)
@@ -504,12 +519,7 @@ def main():
         if world > 1:
             dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = sum(step_ms) * 1e-3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * n * args.steps / total_s / 1e9
+    total_s, value = job_throughput(sum(step_ms) * 1e-3, n, args.steps, world, dev)
     ms_per_step = 1e3 * total_s / args.steps
 
     # roofline of the scan kernel (the only kernel of a step)

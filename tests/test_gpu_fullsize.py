@@ -109,3 +109,25 @@ def test_serving_workload_full_sampled():
             tries[r.set_id] = oracle.Trie(st.sets[r.set_id])
         want = tries[r.set_id].scan_threads(r.text, host_threads())
         assert np.array_equal(results[rid], want), rid
+
+
+def test_text_beyond_two_gigabases():
+    """2^31 + 4,099 bases: offsets past 2^31 (64-bit indexing all the way), with
+    patterns planted on both sides of 2^31 and at the very end of the text."""
+    import torch
+    n = (1 << 31) + 4099
+    rng = datagen.rng_for(77)
+    text = datagen.iid_text(n, rng, datagen.GC41)
+    pats = []
+    for pos in ((1 << 31) - 40, (1 << 31) - 7, 1 << 31, (1 << 31) + 1, n - 64, n - 30):
+        pats.append(text[pos:pos + 30].tobytes())
+    blob, offs = datagen.pattern_set(text[:1 << 24], rng, 2000, (16, 40), 0.5, datagen.GC41)
+    pats += datagen.pattern_list(blob, offs)
+    t = b.Table(pats)
+    packed, out = scan_packed(t, text)
+    got = out.cpu().numpy()
+    del out, packed
+    torch.cuda.empty_cache()
+    want = oracle.Trie(pats).scan_threads(text, host_threads())
+    assert np.array_equal(got, want), first_diff(got, want)
+    assert (want[1 << 31:] != 0).sum() >= 3
