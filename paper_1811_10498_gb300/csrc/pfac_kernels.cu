@@ -433,18 +433,53 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                 }
             }
         } else {
-            // ASCII: the lane packs its 64-base window from the stage and walks what
-            // passes at once, through scan_lane_batch.
+            // ASCII: each lane packs only its own LW bytes from the stage; the rest of its
+            // 64-base window comes from the next lanes by shuffles, and the window of the
+            // last lanes from the bytes right after the warp's span (the next warp's
+            // first bytes or the stage's halo), which the first lanes pack. Then the lane
+            // walks what passes at once, through scan_lane_batch.
+            constexpr uint32_t kFull = 0xFFFFFFFFu;
+            const uint8_t *r = stage + p_rel;
             uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
-            if (rem > 0) {
-                const uint8_t *r = stage + p_rel;
-                uint32_t b0, b1, b2, b3;
-                x0 = pack16(lds_v4(r), &b0);
-                x1 = pack16(lds_v4(r + 16), &b1);
-                x2 = pack16(lds_v4(r + 32), &b2);
-                x3 = pack16(lds_v4(r + 48), &b3);
-                bad |= (uint64_t)b0 | ((uint64_t)b1 << 16) | ((uint64_t)b2 << 32) | ((uint64_t)b3 << 48);
+            uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+            if constexpr (LW == 16) {
+                uint32_t h = 0, hb = 0;
+                if (rem > 0) x0 = pack16(lds_v4(r), &b0);
+                if (lane < 3) h = pack16(lds_v4(r + 512), &hb);          // words 32..34 of the warp
+                // window word k of this lane: word lane + k of the warp
+                const uint32_t d1 = __shfl_down_sync(kFull, x0, 1), e1 = __shfl_down_sync(kFull, b0, 1);
+                const uint32_t d2 = __shfl_down_sync(kFull, x0, 2), e2 = __shfl_down_sync(kFull, b0, 2);
+                const uint32_t d3 = __shfl_down_sync(kFull, x0, 3), e3 = __shfl_down_sync(kFull, b0, 3);
+                const uint32_t g1 = __shfl_sync(kFull, h, (lane + 1) & 31), f1 = __shfl_sync(kFull, hb, (lane + 1) & 31);
+                const uint32_t g2 = __shfl_sync(kFull, h, (lane + 2) & 31), f2 = __shfl_sync(kFull, hb, (lane + 2) & 31);
+                const uint32_t g3 = __shfl_sync(kFull, h, (lane + 3) & 31), f3 = __shfl_sync(kFull, hb, (lane + 3) & 31);
+                x1 = lane < 31 ? d1 : g1;
+                b1 = lane < 31 ? e1 : f1;
+                x2 = lane < 30 ? d2 : g2;
+                b2 = lane < 30 ? e2 : f2;
+                x3 = lane < 29 ? d3 : g3;
+                b3 = lane < 29 ? e3 : f3;
+            } else {
+                uint32_t h0 = 0, h1 = 0, hb0 = 0, hb1 = 0;
+                if (rem > 0) {
+                    x0 = pack16(lds_v4(r), &b0);
+                    x1 = pack16(lds_v4(r + 16), &b1);
+                }
+                if (lane == 0) {                                          // words 64, 65 of the warp
+                    h0 = pack16(lds_v4(r + 1024), &hb0);
+                    h1 = pack16(lds_v4(r + 1040), &hb1);
+                }
+                const uint32_t d2 = __shfl_down_sync(kFull, x0, 1), e2 = __shfl_down_sync(kFull, b0, 1);
+                const uint32_t d3 = __shfl_down_sync(kFull, x1, 1), e3 = __shfl_down_sync(kFull, b1, 1);
+                const uint32_t g2 = __shfl_sync(kFull, h0, 0), f2 = __shfl_sync(kFull, hb0, 0);
+                const uint32_t g3 = __shfl_sync(kFull, h1, 0), f3 = __shfl_sync(kFull, hb1, 0);
+                x2 = lane < 31 ? d2 : g2;
+                b2 = lane < 31 ? e2 : f2;
+                x3 = lane < 31 ? d3 : g3;
+                b3 = lane < 31 ? e3 : f3;
             }
+            // bytes past the text are already marked in `bad` from `rem`
+            bad |= (uint64_t)b0 | ((uint64_t)b1 << 16) | ((uint64_t)b2 << 32) | ((uint64_t)b3 << 48);
             // release the stage once every lane has used its bytes (see the packed path)
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_addr(&empty[st]));
