@@ -18,9 +18,11 @@ namespace pfac {
 //   pack_bits_kernel    ASCII reads -> 2-bit words + one invalid bit per base
 //   plan_kernel         reads -> first work item of each read (512 or 1024 offsets per
 //                       item), and the read of every work item
-//   batched_scan_kernel warps take items from a counter; each item runs the same
-//                       per-warp filter test and skip walks as kernel 2, with its
-//                       read's table and every walk bounded by its read's end
+//   batched_scan_kernel each warp takes every W-th item (W warps in the grid), with the
+//                       next item's read and bounds loaded while it scans the current
+//                       one; each item runs the same per-warp filter test and skip walks
+//                       as kernel 2, with its read's table and every walk bounded by its
+//                       read's end
 //   batched_tail_kernel deferred long walks, with the table recorded in each item
 // ---------------------------------------------------------------------------
 
@@ -38,7 +40,6 @@ struct BatchParams {
     const int64_t *item_start;
     const int32_t *item_read;    // read of each work item, for the first item_cap items
     int64_t item_cap;
-    unsigned long long *item_next;
     int32_t item;                // offsets per work item (32 x LW)
     int32_t *out;
     DeferItem *defer;
@@ -132,8 +133,40 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     if (tid == 0) item_start[n_reads] = carry;
 }
 
+// Where a work item lies: its read, the read's bounds and table, the item's first offset.
+struct ItemMeta {
+    int64_t rs, re, base;
+    int32_t set;
+};
+
+// The metadata of work item `it` (the read from the plan's map, or by search past its
+// capacity: the last r with item_start[r] <= it).
 template <int LW>
-__global__ void __launch_bounds__(256) batched_scan_kernel(const BatchParams P)
+__device__ __forceinline__ ItemMeta item_meta(const BatchParams &P, int64_t it)
+{
+    int32_t r = 0;
+    if (it < P.item_cap) {
+        r = P.item_read[it];
+    } else {
+        int32_t hi = P.n_reads - 1;
+        while (r < hi) {
+            const int32_t mid = (int32_t)(((int64_t)r + hi + 1) >> 1);
+            if (P.item_start[mid] <= it) r = mid;
+            else hi = mid - 1;
+        }
+    }
+    ItemMeta m;
+    read_bounds(P.read_off, r, P.n, &m.rs, &m.re);
+    m.set = P.read_set[r];
+    m.base = m.rs + (it - P.item_start[r]) * (32 * LW);
+    return m;
+}
+
+// Warp w takes work items w, w + W, w + 2W, ... (W warps in the grid); the metadata of
+// its next item is loaded before the current one is scanned, so those dependent loads
+// overlap the scan instead of preceding it.
+template <int LW>
+__global__ void __launch_bounds__(256, 4) batched_scan_kernel(const BatchParams P)
 {
     constexpr int kItem = 32 * LW;
     constexpr uint32_t kAll = LW == 32 ? 0xFFFFFFFFu : ((1u << LW) - 1u);
@@ -147,57 +180,47 @@ __global__ void __launch_bounds__(256) batched_scan_kernel(const BatchParams P)
     K.defer_count = P.defer_count;
     const int64_t n_words = (P.n + 15) >> 4;
     const int64_t n_bw = (P.n + 31) >> 5;
-    for (;;) {
-        unsigned long long it = 0;
-        if (lane == 0) it = atomicAdd(P.item_next, 1ull);
-        it = __shfl_sync(0xFFFFFFFFu, it, 0);
-        if ((int64_t)it >= total) break;
-        // the read holding item `it`: the last r with item_start[r] <= it, from the plan's
-        // map, or by search past its capacity (reads that overlap one another)
-        int32_t lo = 0;
-        if ((int64_t)it < P.item_cap) {
-            lo = P.item_read[it];
-        } else {
-            int32_t hi = P.n_reads - 1;
-            while (lo < hi) {
-                const int32_t mid = (int32_t)(((int64_t)lo + hi + 1) >> 1);
-                if (P.item_start[mid] <= (int64_t)it) lo = mid;
-                else hi = mid - 1;
-            }
-        }
-        int64_t rs, re;
-        read_bounds(P.read_off, lo, P.n, &rs, &re);
-        const int64_t base = rs + ((int64_t)it - P.item_start[lo]) * kItem;
-        const int64_t item_end = min(base + kItem, re);
-        const int32_t set = P.read_set[lo];
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    ItemMeta m{};
+    if (it < total) m = item_meta<LW>(P, it);
+    while (it < total) {
+        const int64_t nxt = it + stride;
+        ItemMeta mn{};
+        if (nxt < total) mn = item_meta<LW>(P, nxt);
+        const int32_t set = m.set;
         if (set < 0 || set >= P.n_sets) {
             if (lane == 0) record_error(P.sets[0].status, PFAC_ERR_INVALID_ARG);
-            continue;
+        } else {
+            const DeviceTable T = P.sets[set];
+            const int64_t base = m.base, re = m.re;
+            const int64_t item_end = min(base + kItem, re);
+            // this lane's LW offsets and the 64 bases from its first one
+            const int64_t p0 = base + LW * lane;
+            const int64_t wi = p0 >> 4;
+            const uint32_t sh = (uint32_t)(p0 & 15) * 2;
+            uint32_t w[5];
+#pragma unroll
+            for (int k = 0; k < 5; k++) w[k] = (wi + k < n_words) ? __ldg(P.packed + wi + k) : 0u;
+            const uint32_t x0 = __funnelshift_r(w[0], w[1], sh), x1 = __funnelshift_r(w[1], w[2], sh);
+            const uint32_t x2 = __funnelshift_r(w[2], w[3], sh), x3 = __funnelshift_r(w[3], w[4], sh);
+            const int64_t bi = p0 >> 5;
+            const uint32_t sb = (uint32_t)(p0 & 31);
+            uint32_t iv[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) iv[k] = (bi + k < n_bw) ? __ldg(P.invalid + bi + k) : 0xFFFFFFFFu;
+            uint64_t bad = ((uint64_t)__funnelshift_r(iv[1], iv[2], sb) << 32) | __funnelshift_r(iv[0], iv[1], sb);
+            const int64_t rem_read = re - p0;   // walks stop at the read's end
+            if (rem_read < 64) bad |= rem_read > 0 ? (~0ull << rem_read) : ~0ull;
+            const int64_t rem_item = item_end - p0;
+            const uint32_t valid = rem_item >= LW ? kAll : (rem_item > 0 ? ((1u << rem_item) - 1u) : 0u);
+            const bool vec_ok = (((uintptr_t)(P.out + base)) & 15u) == 0;
+            scan_lane_batch<true, false, false, true, LW>(T, K, nullptr, nullptr, P.walk_loads, (uint32_t)set,
+                                                          P.packed, P.invalid, re, base, lane, x0, x1, x2, x3, bad,
+                                                          valid, vec_ok, pol);
         }
-        const DeviceTable T = P.sets[set];
-        // this lane's LW offsets and the 64 bases from its first one
-        const int64_t p0 = base + LW * lane;
-        const int64_t wi = p0 >> 4;
-        const uint32_t sh = (uint32_t)(p0 & 15) * 2;
-        uint32_t w[5];
-#pragma unroll
-        for (int k = 0; k < 5; k++) w[k] = (wi + k < n_words) ? __ldg(P.packed + wi + k) : 0u;
-        const uint32_t x0 = __funnelshift_r(w[0], w[1], sh), x1 = __funnelshift_r(w[1], w[2], sh);
-        const uint32_t x2 = __funnelshift_r(w[2], w[3], sh), x3 = __funnelshift_r(w[3], w[4], sh);
-        const int64_t bi = p0 >> 5;
-        const uint32_t sb = (uint32_t)(p0 & 31);
-        uint32_t iv[3];
-#pragma unroll
-        for (int k = 0; k < 3; k++) iv[k] = (bi + k < n_bw) ? __ldg(P.invalid + bi + k) : 0xFFFFFFFFu;
-        uint64_t bad = ((uint64_t)__funnelshift_r(iv[1], iv[2], sb) << 32) | __funnelshift_r(iv[0], iv[1], sb);
-        const int64_t rem_read = re - p0;   // walks stop at the read's end
-        if (rem_read < 64) bad |= rem_read > 0 ? (~0ull << rem_read) : ~0ull;
-        const int64_t rem_item = item_end - p0;
-        const uint32_t valid = rem_item >= LW ? kAll : (rem_item > 0 ? ((1u << rem_item) - 1u) : 0u);
-        const bool vec_ok = (((uintptr_t)(P.out + base)) & 15u) == 0;
-        scan_lane_batch<true, false, false, true, LW>(T, K, nullptr, nullptr, P.walk_loads, (uint32_t)set, P.packed,
-                                                      P.invalid, re, base, lane, x0, x1, x2, x3, bad, valid, vec_ok,
-                                                      pol);
+        it = nxt;
+        m = mn;
     }
 }
 
@@ -235,7 +258,7 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
     const int blocks_per_sm = std::min(8, std::max(1, bc.blocks_per_sm));
     if (n == 0 || n_reads == 0) return PFAC_OK;
     uint8_t *p = (uint8_t *)scratch;
-    unsigned long long *counters = (unsigned long long *)p;       // [0] next item, [1] deferred walks
+    unsigned long long *counters = (unsigned long long *)p;       // [1]: deferred walks
     p += 256;
     const int64_t words = (n + 15) / 16, bw = (n + 31) / 32;
     uint32_t *packed = (uint32_t *)p;
@@ -264,7 +287,6 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
     P.item_start = item_start;
     P.item_read = item_read;
     P.item_cap = item_cap;
-    P.item_next = counters;
     P.out = out;
     P.defer = defer;
     P.defer_cap = defer_cap;
