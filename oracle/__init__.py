@@ -12,7 +12,9 @@ Contents:
   * ``brute.py``: pure-Python brute force and a regular-expression restatement for
     tiny inputs;
   * ``pack`` and ``compact`` below: the plain definitions of the 2-bit text packing
-    and of the (offset, id) match list that the CUDA library produces.
+    and of the (offset, id) match list that the CUDA library produces;
+  * ``all_matches``: every pattern occurrence keyed by its start, from the classic
+    Aho-Corasick machine's occurrence list (the reference for the all-matches scan).
 """
 from __future__ import annotations
 
