@@ -383,6 +383,38 @@ def paper_suite(args):
         for label in ("global (kernel 1)", "smem text + smem filter and rank (default)"):
             point("10", n_l, n_pats[-1], label, placements[label])
 
+    # the paper's host program from files (Figs. 4-5): pattern set 5 and input set 5 written
+    # to files, read back, the table built from its file, the text scanned from host memory
+    import tempfile
+    from paper_1811_10498_gb300.hoststream import scan_host
+    blob, offs = datagen.paper_patterns(src, n_pats[-1])
+    text = datagen.paper_input(src, lines[-1])
+    with tempfile.TemporaryDirectory() as d:
+        pf, tf = os.path.join(d, "patterns.txt"), os.path.join(d, "input.txt")
+        with open(pf, "wb") as f:
+            f.write(b"\n".join(datagen.pattern_list(blob, offs)) + b"\n")
+        text.tofile(tf)
+        t0 = time.perf_counter()
+        h_text = torch.from_numpy(b.read_text_file(tf)).pin_memory()
+        read_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        t = b.Table.from_file(pf)
+        build_s = time.perf_counter() - t0
+    h_out = torch.empty(h_text.numel(), dtype=torch.int32).pin_memory()
+    scan_host(t, h_text, h_out, ascii=True)
+    t0 = time.perf_counter()
+    scan_host(t, h_text, h_out, ascii=True)
+    scan_s = time.perf_counter() - t0
+    ref = b.Table((blob, offs))
+    same = bool(torch.equal(h_out, ref.match(torch.from_numpy(text).cuda()).cpu()))
+    n = h_text.numel()
+    print(json.dumps({"suite": "paper", "figure": "4-5 (files)", "input_lines": lines[-1], "input_bytes": n,
+                      "patterns": n_pats[-1], "read_s": read_s, "read_gb_s": n / read_s / 1e9,
+                      "build_from_file_s": build_s, "scan_from_host_s": scan_s,
+                      "scan_from_host_gbases_s": n / scan_s / 1e9, "same_as_in_memory": same}), flush=True)
+    t.close()
+    ref.close()
+
 
 def run_reference(args):
     """The oracle, as it stands, on the host cores: each step scans a bounded sample."""

@@ -51,8 +51,9 @@ enum {
     PFAC_ERR_TIMEOUT = 8,         /* a bounded device-side wait ran out */
     PFAC_ERR_HOST_ONLY = 9,       /* the handle was built without a device copy */
     PFAC_ERR_UNSUPPORTED = 10,    /* option not available for this table (see pfac_info_ex) */
-    PFAC_ERR_SCRATCH_LIMIT = 11   /* the text is longer than pfac_match_packed_noalloc's fixed
+    PFAC_ERR_SCRATCH_LIMIT = 11,  /* the text is longer than pfac_match_packed_noalloc's fixed
                                      scratch buffer can serve */
+    PFAC_ERR_IO = 12              /* a file cannot be opened or read */
 };
 
 /* Opaque, library-owned table handle. */
@@ -87,6 +88,28 @@ typedef struct {
 
 pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, int32_t n,
                           const pfac_build_opts *opts);
+
+/* File front end (the paper's host program reads its patterns and its text from files,
+ * Section V-B, Figs. 4 and 5).
+ *
+ * pfac_build_file: build from a pattern file, as pfac_build_ex would from the same
+ * patterns. One pattern per line (a trailing '\r' is dropped, empty lines are skipped);
+ * a file whose first non-empty line starts with '>' is FASTA: the sequence lines of each
+ * record, joined, make one pattern (ids follow the order in the file). Bytes are taken
+ * as they are (no case folding), so a line holding anything but A/C/G/T fails with
+ * PFAC_ERR_BAD_SYMBOL. Returns NULL on error: PFAC_ERR_IO (cannot open or read),
+ * PFAC_ERR_INVALID_ARG (NULL path, no pattern) or any error of pfac_build_ex. */
+pfac_handle pfac_build_file(const char *path, const pfac_build_opts *opts);
+
+/* pfac_read_text_file: read a text file into a caller-owned HOST buffer.
+ *   fasta = 0 : the bytes as they are, newlines included (a newline ends every walk
+ *               that reaches it, so lines are scanned as separate reads)
+ *   fasta = 1 : header lines dropped, each record's sequence lines joined, records
+ *               separated by one '\n'
+ *   *len      : receives the text's length in bytes; min(*len, cap) bytes go to buf
+ *               (buf may be NULL when cap = 0: a first call that only sizes the text).
+ * Returns PFAC_OK, PFAC_ERR_INVALID_ARG, PFAC_ERR_IO or PFAC_ERR_OOM. */
+int pfac_read_text_file(const char *path, int32_t fasta, uint8_t *buf, int64_t cap, int64_t *len);
 
 /* Status of the last failed call on this thread (PFAC_OK if none). */
 int pfac_last_error(void);

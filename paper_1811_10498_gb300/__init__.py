@@ -5,7 +5,7 @@ package is its thin Python binding plus the launch autotuner, the batched-read d
 and the serving loop. ``datagen`` makes the seeded synthetic inputs.
 """
 from ._binding import (  # noqa: F401
-    CODE, STATUS, PfacError, Table, lib, pack, pfac_build, pfac_debug_timeout_probe, pfac_destroy,
+    CODE, STATUS, PfacError, Table, lib, pack, pfac_build, pfac_build_file, pfac_debug_timeout_probe, pfac_destroy,
     pfac_device_status, pfac_export, pfac_export_shortcuts, pfac_get_config, pfac_info, pfac_info_ex, pfac_match,
-    pfac_match_all, pfac_match_batched, pfac_match_compact, pfac_match_packed, pfac_pack, pfac_set_config,
+    pfac_match_all, pfac_match_batched, pfac_match_compact, pfac_match_packed, pfac_pack, pfac_set_config, read_text_file,
 )

@@ -21,6 +21,7 @@ STATUS = {
     0: "PFAC_OK", 1: "PFAC_ERR_INVALID_ARG", 2: "PFAC_ERR_EMPTY_PATTERN", 3: "PFAC_ERR_BAD_SYMBOL",
     4: "PFAC_ERR_TOO_MANY_STATES", 5: "PFAC_ERR_OOM", 6: "PFAC_ERR_CUDA", 7: "PFAC_ERR_OVERFLOW",
     8: "PFAC_ERR_TIMEOUT", 9: "PFAC_ERR_HOST_ONLY", 10: "PFAC_ERR_UNSUPPORTED", 11: "PFAC_ERR_SCRATCH_LIMIT",
+    12: "PFAC_ERR_IO",
 }
 CODE = {v: k for k, v in STATUS.items()}
 
@@ -56,6 +57,8 @@ _lock = threading.Lock()
 _SIGS = {
     "pfac_build": (P, [P, P, I32]),
     "pfac_build_ex": (P, [P, P, I32, P]),
+    "pfac_build_file": (P, [C.c_char_p, P]),
+    "pfac_read_text_file": (C.c_int, [C.c_char_p, I32, P, I64, P]),
     "pfac_last_error": (C.c_int, []),
     "pfac_error_string": (C.c_char_p, [C.c_int]),
     "pfac_last_cuda_error": (C.c_char_p, []),
@@ -154,6 +157,28 @@ def pfac_build(patterns, host_only: bool = False, filter_b: int = 0) -> int:
     if not h:
         raise PfacError(L.pfac_last_error(), "pfac_build")
     return h
+
+
+def pfac_build_file(path: str, host_only: bool = False, filter_b: int = 0) -> int:
+    """Build from a pattern file (one pattern per line, or FASTA records)."""
+    opts = pfac_build_opts(1 if host_only else 0, int(filter_b))
+    h = lib().pfac_build_file(os.fsencode(path), C.byref(opts))
+    if not h:
+        raise PfacError(lib().pfac_last_error(), "pfac_build_file")
+    return h
+
+
+def read_text_file(path: str, fasta: bool = False) -> np.ndarray:
+    """A text file as ASCII uint8 (as it is, or FASTA records joined with one newline
+    between records)."""
+    n = I64(0)
+    _check(lib().pfac_read_text_file(os.fsencode(path), 1 if fasta else 0, None, 0, C.byref(n)),
+           "pfac_read_text_file")
+    buf = np.empty(max(1, n.value), dtype=np.uint8)
+    got = I64(0)
+    _check(lib().pfac_read_text_file(os.fsencode(path), 1 if fasta else 0, buf.ctypes.data, n.value, C.byref(got)),
+           "pfac_read_text_file")
+    return buf[:min(n.value, got.value)]
 
 
 def pfac_destroy(h: int):
@@ -271,6 +296,12 @@ class Table:
 
     def __init__(self, patterns, host_only: bool = False, filter_b: int = 0):
         self.h = pfac_build(patterns, host_only=host_only, filter_b=filter_b)
+
+    @classmethod
+    def from_file(cls, path: str, host_only: bool = False, filter_b: int = 0) -> "Table":
+        t = cls.__new__(cls)
+        t.h = pfac_build_file(path, host_only=host_only, filter_b=filter_b)
+        return t
 
     def close(self):
         h, self.h = getattr(self, "h", None), None

@@ -15,7 +15,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpfac.so")
-SOURCES = ["pfac_kernels.cu", "pfac_batched.cu", "pfac_api.cpp", "trie_build.cpp", "pfac_noalloc.cu"]
+SOURCES = ["pfac_kernels.cu", "pfac_batched.cu", "pfac_api.cpp", "trie_build.cpp", "pfac_io.cpp",
+           "pfac_noalloc.cu"]
 HEADERS = ["pfac_internal.h", "pfac_device.cuh", os.path.join("..", "..", "include", "pfac.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -340,6 +340,7 @@ const char *pfac_error_string(int status)
     case PFAC_ERR_HOST_ONLY: return "handle has no device copy";
     case PFAC_ERR_UNSUPPORTED: return "option not supported for this table";
     case PFAC_ERR_SCRATCH_LIMIT: return "text longer than the allocation-free scan's fixed scratch allows";
+    case PFAC_ERR_IO: return "file cannot be opened or read";
     default: return "unknown status";
     }
 }

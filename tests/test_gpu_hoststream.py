@@ -63,3 +63,22 @@ def test_ascii_chunks_with_newline_separated_reads():
     assert np.array_equal(got, want), first_diff(got, want)
     assert (want != 0).sum() > 100
     t.close()
+
+
+def test_files_to_ids(tmp_path):
+    """The paper's host program end to end: patterns and newline-separated reads from
+    files, the table built from the file, the text scanned from host memory."""
+    torch = require_cuda()
+    src = datagen.paper_source(n_bases=1 << 16)
+    text = datagen.paper_input(src, 5000)
+    blob, offs = datagen.paper_patterns(src, 300, length=40)
+    pats = datagen.pattern_list(blob, offs)
+    (tmp_path / "patterns.txt").write_bytes(b"\n".join(pats) + b"\n")
+    (tmp_path / "reads.txt").write_bytes(text.tobytes())
+    t = b.Table.from_file(str(tmp_path / "patterns.txt"))
+    h_text = torch.from_numpy(b.read_text_file(str(tmp_path / "reads.txt")))
+    got = scan_host(t, h_text, chunk_bases=1 << 17, ascii=True).numpy()
+    want = oracle.Trie(pats).scan(text)
+    assert np.array_equal(got, want), first_diff(got, want)
+    assert (want != 0).sum() > 100
+    t.close()
