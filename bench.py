@@ -386,7 +386,7 @@ def paper_suite(args):
     # the paper's host program from files (Figs. 4-5): pattern set 5 and input set 5 written
     # to files, read back, the table built from its file, the text scanned from host memory
     import tempfile
-    from paper_1811_10498_gb300.hoststream import scan_host
+    from paper_1811_10498_gb300.hoststream import HostScanner
     blob, offs = datagen.paper_patterns(src, n_pats[-1])
     text = datagen.paper_input(src, lines[-1])
     with tempfile.TemporaryDirectory() as d:
@@ -401,9 +401,12 @@ def paper_suite(args):
         t = b.Table.from_file(pf)
         build_s = time.perf_counter() - t0
     h_out = torch.empty(h_text.numel(), dtype=torch.int32).pin_memory()
-    scan_host(t, h_text, h_out, ascii=True)
+    hs = HostScanner(t, chunk_bases=1 << 24, ascii=True)
+    hs.scan(h_text, h_out)
+    hs.synchronize()
     t0 = time.perf_counter()
-    scan_host(t, h_text, h_out, ascii=True)
+    hs.scan(h_text, h_out)
+    hs.synchronize()
     scan_s = time.perf_counter() - t0
     ref = b.Table((blob, offs))
     same = bool(torch.equal(h_out, ref.match(torch.from_numpy(text).cuda()).cpu()))
