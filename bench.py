@@ -472,8 +472,9 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the large-dictionary (10^6 patterns) leg")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--no-tune", action="store_true", help="use the library's default launch configuration")
-    ap.add_argument("--suite", default=None, choices=["paper"],
-                    help="paper: the paper's placement, pattern-set and input-size experiments (many lines)")
+    ap.add_argument("--suite", default=None, choices=["paper", "batched"],
+                    help="paper: the paper's placement, pattern-set and input-size experiments (many lines); "
+                         "batched: the batched workload alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -482,6 +483,11 @@ def main():
         return
     if args.suite == "paper":
         paper_suite(args)
+        return
+    if args.suite == "batched":
+        from paper_1811_10498_gb300 import build_ext
+        build_ext.build()
+        print(json.dumps({"suite": "batched", **batched_measure(min(args.steps, 20))}), flush=True)
         return
 
     import torch
