@@ -429,6 +429,7 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
+    from paper_1811_10498_gb300 import datagen
     w = make_workload(0, args.n_bases, args.n_patterns)
     threads = os.cpu_count() or 1
     trie = oracle.Trie((w.blob, w.offsets))
@@ -453,7 +454,11 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": {"workload": workload_name(args.n_bases, args.n_patterns)},
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.n_bases, args.n_patterns), "n_bases": int(n),
+                       "n_patterns": args.n_patterns,
+                       "inputs": {"seed": 2, "text_sha256": datagen.sha256(w.text),
+                                  "patterns_sha256": datagen.sha256(w.blob)}},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{per_step} consecutive offsets per step, {threads} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -463,7 +468,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-bases", type=int, default=N_BASES)
@@ -506,7 +511,7 @@ def main():
     dev = torch.device("cuda", local)
 
     from paper_1811_10498_gb300 import _binding as b
-    from paper_1811_10498_gb300 import build_ext
+    from paper_1811_10498_gb300 import build_ext, datagen
     build_ext.build()
 
     w = make_workload(rank, args.n_bases, args.n_patterns)
@@ -615,7 +620,9 @@ def main():
             "config": {"workload": workload_name(args.n_bases, args.n_patterns), "n_bases": n,
                        "n_patterns": args.n_patterns, "n_states": info["n_states"], "filter_b": info["filter_b"],
                        "l2": "flushed between timed steps (memset of 4x L2 outside the events)",
-                       "input_resident": "packed text in HBM"},
+                       "input_resident": "packed text in HBM",
+                       "inputs": {"seed": 2 + rank, "text_sha256": datagen.sha256(w.text),
+                                  "patterns_sha256": datagen.sha256(w.blob)}},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
             "clocks": clocks.summary(),
             "wall_s_timed_region": wall,
