@@ -372,6 +372,7 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
             {(const void **)&h->dt.rank, T.rank_wide ? (const void *)T.rank32.data() : (const void *)T.rank16.data(),
              rank_bytes},
             {(const void **)&h->dt.dense, T.dense.data(), T.dense.size() * 4},
+            {(const void **)&h->dt.filter1, T.filter1.data(), T.filter1.size() * 4},
         };
         size_t total = 256;   // status word
         for (auto &p : parts) total += round256(p.bytes);
@@ -403,6 +404,7 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         h->dt.max_len = T.max_len;
         h->dt.min_len = T.min_len;
         h->dt.filter_b = T.filter_b;
+        h->dt.filter1_b = T.filter1_b;
         h->dt.rank_wide = T.rank_wide;
         // The device copy is complete; the host keeps rows, ids and levels for export.
         std::vector<uint32_t>().swap(h->host.skip);
@@ -410,6 +412,7 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         std::vector<uint16_t>().swap(h->host.rank16);
         std::vector<uint32_t>().swap(h->host.rank32);
         std::vector<uint32_t>().swap(h->host.dense);
+        std::vector<uint32_t>().swap(h->host.filter1);
     }
     return h;
 }

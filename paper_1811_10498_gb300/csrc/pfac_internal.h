@@ -50,6 +50,7 @@ constexpr int kSkipMaxLen = 16;
 // entry with the special bit when a pattern ends within w (the answer then needs the
 // walk from the root).
 constexpr int kMaxFilterB = 12;
+constexpr int kFilter1B = 10;      // order of the shared-memory first-level filter
 
 struct HostTables {
     int64_t n_states = 0;
@@ -67,6 +68,11 @@ struct HostTables {
     std::vector<uint16_t> rank16;    // one per filter word
     std::vector<uint32_t> rank32;
     std::vector<uint32_t> dense;     // 4 per set filter bit
+    // Filter of order kFilter1B derived from the main one when that is of a higher
+    // order (too large for shared memory): bit w10 is the OR of the main bits of every
+    // b-mer whose first kFilter1B bases are w10, i.e. the order-kFilter1B filter itself.
+    int32_t filter1_b = 0;
+    std::vector<uint32_t> filter1;
 };
 
 // Status codes match pfac.h.
@@ -89,12 +95,14 @@ struct DeviceTable {
     const int32_t *out_id;     // n_states
     const uint4 *skip;         // n_states skip entries, or nullptr
     const uint32_t *filter;    // 4^filter_b bits, or nullptr
+    const uint32_t *filter1;   // first-level filter of order filter1_b, or nullptr
     const void *rank;          // one entry per filter word (uint16 or uint32)
     const uint4 *dense;        // one skip entry per set filter bit
     int64_t n_states;
     int32_t max_len;
     int32_t min_len;           // shortest pattern
     int32_t filter_b;          // 0 = no prefix filter
+    int32_t filter1_b;         // 0 = no first-level filter
     int32_t rank_wide;
     int32_t *status;           // device status word (PFAC_OK or the first error)
 };

@@ -265,7 +265,28 @@ __device__ __forceinline__ void queue_round(const ScanParams &P, const Sink &K, 
                                             x2, x3, 0, wlim, rem <= 64, wlim >= P.t.filter_b);
 }
 
-template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW, bool ALL = false>
+// Main-filter bits (global memory) of the lane's offsets whose bit is set in `screen`
+// (the first-level filter's verdict); the loads of the other offsets are skipped.
+template <int LW>
+__device__ __forceinline__ uint32_t filter_bits_screened(const DeviceTable &T, uint32_t x0, uint32_t x1, uint32_t x2,
+                                                         uint32_t bmask, uint32_t screen)
+{
+    uint32_t pend = 0;
+#pragma unroll
+    for (int j = 0; j < LW; j++) {
+        if ((screen >> j) & 1u) {
+            const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
+            const uint32_t kmer = win & bmask;
+            const uint32_t word = __ldg(T.filter + (kmer >> 5));
+            pend |= ((word >> (kmer & 31u)) & 1u) << j;
+        }
+    }
+    return pend;
+}
+
+// L1F (packed text, main filter in global memory): the first-level filter of order
+// kFilter1B sits in shared memory at offset 0 and screens every offset first.
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW, bool ALL = false, bool L1F = false>
 __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -302,14 +323,17 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             for (int64_t i = (bytes & ~(int64_t)15) + tid; i < bytes; i += blockDim.x) dst[i] = src[i];
         };
         const int64_t words = B >= 3 ? ((int64_t)1 << (2 * B)) / 32 : 1;
-        if (FSMEM) {
-            // the filter's words go in bit-reversed (see filter_bits)
+        if (FSMEM || L1F) {
+            // the filter's words go in bit-reversed (see filter_bits): the main filter, or
+            // the first-level one
+            const uint32_t *src = L1F ? T.filter1 : T.filter;
+            const int64_t fwords = L1F ? ((int64_t)1 << (2 * kFilter1B)) / 32 : words;
             uint32_t *dst = reinterpret_cast<uint32_t *>(smem + P.off_filter);
-            for (int64_t i = 4 * (int64_t)tid; i + 4 <= words; i += 4 * (int64_t)blockDim.x) {
-                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(T.filter + i));
+            for (int64_t i = 4 * (int64_t)tid; i + 4 <= fwords; i += 4 * (int64_t)blockDim.x) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(src + i));
                 *reinterpret_cast<uint4 *>(dst + i) = make_uint4(__brev(v.x), __brev(v.y), __brev(v.z), __brev(v.w));
             }
-            for (int64_t i = (words & ~(int64_t)3) + tid; i < words; i += blockDim.x) dst[i] = __brev(__ldg(T.filter + i));
+            for (int64_t i = (fwords & ~(int64_t)3) + tid; i < fwords; i += blockDim.x) dst[i] = __brev(__ldg(src + i));
         }
         if (P.rank_smem) copy_in(P.off_rank, T.rank, words * (int64_t)sizeof(RankT));
     }
@@ -386,7 +410,14 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                 if (LW == 32) x2 = lds_u32(w + 2);
             }
             const uint32_t fast = bad ? clear_runs(bad, B) & valid : valid;   // the b-mer is readable
-            uint32_t pend = filter_bits<FSMEM, LW>(T, sf, x0, x1, x2, bmask) & fast;
+            uint32_t pend;
+            if constexpr (L1F) {
+                const uint32_t bmask1 = (1u << (2 * kFilter1B)) - 1u;
+                pend = filter_bits<true, LW>(T, sf, x0, x1, x2, bmask1) & fast;
+                pend = filter_bits_screened<LW>(T, x0, x1, x2, bmask, pend);
+            } else {
+                pend = filter_bits<FSMEM, LW>(T, sf, x0, x1, x2, bmask) & fast;
+            }
             // near the text end: offsets with fewer than b readable bases walk from the
             // root when a pattern shorter than b could still fit
             if (T.min_len < B) pend |= valid & ~fast & clear_runs(bad, T.min_len);
@@ -550,6 +581,7 @@ static int stages_of(const TiledConfig &cfg, bool packed) { return cfg.stages > 
 struct SmemPlan {
     int64_t filter_bytes, rank_bytes;   // bytes copied into shared memory (0 = global)
     int64_t total;
+    bool l1f;                           // filter_bytes hold the first-level filter
 };
 
 static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool packed, const DeviceProps &dp)
@@ -569,7 +601,14 @@ static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool pac
         return pl;
     }
     pl.filter_bytes = total(fbytes, 0) <= limit ? fbytes : 0;
-    pl.rank_bytes = (cfg.smem_table_bytes >= 0 && total(pl.filter_bytes, rbytes) <= limit) ? rbytes : 0;
+    if (!pl.filter_bytes && packed && t.filter1_b == kFilter1B && t.filter1) {
+        const int64_t f1 = ((int64_t)1 << (2 * kFilter1B)) / 8;
+        if (total(f1, 0) <= limit) {
+            pl.filter_bytes = f1;
+            pl.l1f = true;
+        }
+    }
+    pl.rank_bytes = (!pl.l1f && cfg.smem_table_bytes >= 0 && total(pl.filter_bytes, rbytes) <= limit) ? rbytes : 0;
     pl.total = total(pl.filter_bytes, pl.rank_bytes);
     return pl;
 }
@@ -638,12 +677,12 @@ static cudaError_t launch_with_policy(Kern kern, const ScanParams &P, int grid, 
     return cudaLaunchKernelEx(&lc, kern, P);
 }
 
-template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, bool ALL>
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, bool ALL, bool L1F = false>
 static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t smem, int tail_grid, cudaStream_t st,
                          const TiledConfig &cfg, const DeviceProps &dp)
 {
-    auto kern = lane_width_of(cfg) == 32 ? scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL>
-                                         : scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 16, ALL>;
+    auto kern = lane_width_of(cfg) == 32 ? scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, L1F>
+                                         : scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 16, ALL, L1F>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return PFAC_ERR_CUDA;
     if (launch_with_policy(kern, P, grid, threads, smem, st, cfg, dp) != cudaSuccess) return PFAC_ERR_CUDA;
@@ -653,8 +692,16 @@ static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t sm
 
 template <bool PACKED, bool COMPACT, bool ALL = false>
 static int launch_scan_w(const ScanParams &P, bool fsmem, bool rank16, int grid, int threads, uint32_t smem,
-                         int tail_grid, cudaStream_t st, const TiledConfig &cfg, const DeviceProps &dp)
+                         int tail_grid, cudaStream_t st, const TiledConfig &cfg, const DeviceProps &dp,
+                         bool l1f = false)
 {
+    if constexpr (PACKED) {
+        if (l1f)
+            return rank16 ? launch_scan_t<PACKED, COMPACT, false, true, ALL, true>(P, grid, threads, smem, tail_grid,
+                                                                                 st, cfg, dp)
+                          : launch_scan_t<PACKED, COMPACT, false, false, ALL, true>(P, grid, threads, smem, tail_grid,
+                                                                                  st, cfg, dp);
+    }
     if (fsmem)
         return rank16 ? launch_scan_t<PACKED, COMPACT, true, true, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp)
                       : launch_scan_t<PACKED, COMPACT, true, false, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp);
@@ -712,15 +759,19 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     // a queued offset codes its tile round in 32 - kRelBits bits
     if (packed && (P.n_tiles + grid - 1) / grid > ((int64_t)1 << (32 - kRelBits))) return PFAC_ERR_UNSUPPORTED;
     const int tail_grid = dp.num_sms * 4;
-    const bool fsmem = pl.filter_bytes > 0;
+    const bool fsmem = pl.filter_bytes > 0 && !pl.l1f;
+    const bool l1f = pl.l1f;
     const bool rank16 = !t.rank_wide;
     if (all_matches) {   // the match list of every pattern on every walk (packed text only)
         if (!packed || !compact) return PFAC_ERR_INVALID_ARG;
-        return launch_scan_w<true, true, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp);
+        return launch_scan_w<true, true, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp,
+                                               l1f);
     }
     if (packed)
-        return compact ? launch_scan_w<true, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp)
-                       : launch_scan_w<true, false>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp);
+        return compact ? launch_scan_w<true, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp,
+                                                   l1f)
+                       : launch_scan_w<true, false>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp,
+                                                    l1f);
     return compact ? launch_scan_w<false, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp)
                    : launch_scan_w<false, false>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp);
 }

@@ -245,6 +245,20 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
             T.rank_wide = count > 65535;
             if (T.rank_wide) T.rank32.swap(rank);
             else T.rank16.assign(rank.begin(), rank.end());
+            // A main filter above order kFilter1B gets a first-level filter of that order:
+            // a b-mer whose first kFilter1B bases have a clear bit there has a clear bit
+            // in the main filter too, so the first level screens offsets in shared memory
+            // before the main filter is read from global memory.
+            if (b > kFilter1B) {
+                const size_t E1 = (size_t)1 << (2 * kFilter1B);
+                T.filter1_b = kFilter1B;
+                T.filter1.assign(E1 / 32, 0u);
+                for (size_t w = 0; w < E; w++)
+                    if ((T.filter[w >> 5] >> (w & 31)) & 1u) {
+                        const size_t w1 = w & (E1 - 1);   // the first kFilter1B bases
+                        T.filter1[w1 >> 5] |= 1u << (w1 & 31);
+                    }
+            }
         }
         return PFAC_OK;
     } catch (const std::bad_alloc &) {
