@@ -83,7 +83,9 @@ typedef struct {
                            1..12 = that order. One bit per b-mer, clear when a walk over
                            those b bases ends with no pattern on the way, so the answer
                            at that offset is 0 whatever follows (an exact property of
-                           the same trie). */
+                           the same trie). A filter above order 10 (too large for shared
+                           memory) comes with a first-level filter of order 10, derived
+                           from it, that the packed scan keeps in shared memory. */
 } pfac_build_opts;
 
 pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, int32_t n,
