@@ -104,3 +104,23 @@ def test_tune_batched_is_exact(tmp_path):
     assert np.array_equal(d_out.cpu().numpy(), want)
     for t in tables:
         t.close()
+
+
+@pytest.mark.gpu
+def test_tune_scan_ascii_is_exact(tmp_path):
+    """ASCII text with newline-separated lines (the paper's input shape)."""
+    from gpu_util import require_cuda, to_dev
+    import oracle
+    from paper_1811_10498_gb300 import _binding as b
+    from paper_1811_10498_gb300 import datagen
+    torch = require_cuda()
+    src = datagen.paper_source(n_bases=1 << 18)
+    text = datagen.paper_input(src, 30_000)
+    blob, offs = datagen.paper_patterns(src, 2000, length=30)
+    t = b.Table((blob, offs))
+    d = to_dev(text)
+    cfg = autotune.tune_scan(t, d, text.size, packed=False, reps=3, cache=str(tmp_path / "a.json"))
+    assert not cfg["cached"]
+    got = t.match(d).cpu().numpy()
+    assert np.array_equal(got, oracle.Trie((blob, offs)).scan(text))
+    t.close()
