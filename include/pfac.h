@@ -205,7 +205,9 @@ typedef struct {
 /* Set (cfg != NULL) or reset (cfg == NULL) the launch configuration of a handle.
  * Takes effect for launches issued afterwards. */
 int pfac_set_config(pfac_handle h, const pfac_config *cfg);
-/* The configuration the next launch on `n_bases` bases would use. */
+/* The configuration the next packed-text launch on `n_bases` bases would use (an ASCII
+ * launch differs only where the set configuration leaves stages or lane_offsets at 0:
+ * it then uses 2 stages and 16 offsets per lane). */
 int pfac_get_config(pfac_handle h, int64_t n_bases, pfac_config *cfg);
 
 /* ---------------------------------------------------------------------------
