@@ -44,6 +44,9 @@ inline int base_code(unsigned char b)
 
 constexpr int64_t kMaxStates = int64_t(0x7FFFFFFF);
 
+// A skip label is kSkipMaxLen two-bit symbols, low symbol first, in one 32-bit word.
+static_assert(kSkipMaxLen == 16, "skip labels fill exactly one 32-bit word");
+
 }  // namespace
 
 int build_host_tables(const char *const *patterns, const int32_t *lengths, int32_t n,
@@ -94,28 +97,9 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
             else dups++;
         }
 
-        // ---- step 2: breadth-first renumbering ---------------------------------
-        std::vector<int32_t> order((size_t)n_states);   // new id -> old id
-        std::vector<int32_t> renum((size_t)n_states);   // old id -> new id
-        std::vector<int32_t> depth_of((size_t)n_states);
-        int64_t head = 0, tail = 0;
-        order[tail++] = 0;
-        renum[0] = 0;
-        depth_of[0] = 0;
-        while (head < tail) {
-            int32_t old = order[(size_t)head];
-            int32_t dnew = depth_of[(size_t)head];
-            head++;
-            for (int c = 0; c < 4; c++) {
-                int32_t ch = go[(size_t)(4 * (int64_t)old + c)];
-                if (ch) {
-                    renum[(size_t)ch] = (int32_t)tail;
-                    depth_of[(size_t)tail] = dnew + 1;
-                    order[(size_t)tail++] = ch;
-                }
-            }
-        }
-
+        // ---- steps 2 and 3a: breadth-first renumbering, rows and pattern ids -----
+        // The queue holds old ids in their new order; the children of the state at
+        // `head` take the next new ids, so its row is written as soon as it is visited.
         HostTables &T = *out;
         T = HostTables();
         T.n_states = n_states;
@@ -123,67 +107,92 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
         T.max_len = max_len;
         T.min_len = min_len;
         T.n_duplicates = dups;
-        T.level.assign((size_t)max_len + 2, n_states);
-        for (int64_t s = n_states - 1; s >= 0; s--) T.level[(size_t)depth_of[(size_t)s]] = s;
-        for (int d = max_len; d >= 0; d--) T.level[(size_t)d] = std::min(T.level[(size_t)d], T.level[(size_t)d + 1]);
-
-        // ---- step 3a: 16-byte rows and pattern ids ------------------------------
         T.rows.assign((size_t)n_states * 4, 0);
         T.out_id.assign((size_t)n_states, 0);
-        for (int64_t s = 0; s < n_states; s++) {
-            int32_t old = order[(size_t)s];
-            T.out_id[(size_t)s] = term[(size_t)old];
-            for (int c = 0; c < 4; c++) {
-                int32_t ch = go[(size_t)(4 * (int64_t)old + c)];
-                if (ch) {
-                    uint32_t e = (uint32_t)renum[(size_t)ch];
-                    if (term[(size_t)ch]) e |= 0x80000000u;
-                    T.rows[(size_t)(4 * s + c)] = (int32_t)e;
+        T.level.assign((size_t)max_len + 2, n_states);
+        std::vector<int32_t> order((size_t)n_states);    // new id -> old id
+        std::vector<int32_t> parent((size_t)n_states);   // new id -> new id of its parent
+        {
+            int64_t head = 0, tail = 1, depth_end = 1;
+            int32_t depth = 0;
+            order[0] = 0;
+            parent[0] = 0;
+            T.out_id[0] = term[0];
+            T.level[0] = 0;
+            constexpr int64_t kAhead = 16;   // queue entries whose rows are fetched early
+            while (head < tail) {
+                if (head == depth_end) {     // every state of `depth` has been visited
+                    T.level[(size_t)++depth] = head;
+                    depth_end = tail;
                 }
+                if (head + kAhead < tail) __builtin_prefetch(&go[(size_t)(4 * (int64_t)order[(size_t)(head + kAhead)])]);
+                const int32_t *g = &go[(size_t)(4 * (int64_t)order[(size_t)head])];
+                for (int c = 0; c < 4; c++) {
+                    const int32_t ch = g[c];
+                    if (!ch) continue;
+                    uint32_t e = (uint32_t)tail;
+                    if (term[(size_t)ch]) e |= 0x80000000u;
+                    T.rows[(size_t)(4 * head + c)] = (int32_t)e;
+                    T.out_id[(size_t)tail] = term[(size_t)ch];
+                    parent[(size_t)tail] = (int32_t)head;
+                    order[(size_t)tail++] = ch;
+                }
+                head++;
             }
         }
+        for (int d = max_len; d >= 0; d--) T.level[(size_t)d] = std::min(T.level[(size_t)d], T.level[(size_t)d + 1]);
         std::vector<int32_t>().swap(go);
         std::vector<int32_t>().swap(term);
         std::vector<int32_t>().swap(order);
-        std::vector<int32_t>().swap(renum);
-        std::vector<int32_t>().swap(depth_of);
 
         // ---- step 3b: skip entries ----------------------------------------------
+        // From the deepest state up, so a child's entry is final before its parent's.
+        // A single-child state s with child ch (edge symbol c) stops at ch when ch is
+        // terminal or has other than one child; otherwise its chain is c followed by
+        // ch's chain, cut at kSkipMaxLen symbols: a chain of ch that already has
+        // kSkipMaxLen symbols loses its last one, so s stops at the parent of ch's
+        // target, which lies strictly inside ch's chain and so is not terminal.
         if (n_states < kMaxNodeStates) {
-            std::vector<uint32_t> node((size_t)n_states, 0);
-            std::vector<uint8_t> nchild((size_t)n_states, 0), onlyc((size_t)n_states, 0);
-            for (int64_t s = 0; s < n_states; s++) {
-                uint32_t mask = 0, first = 0;
-                for (int c = 3; c >= 0; c--) {
-                    uint32_t e = (uint32_t)T.rows[(size_t)(4 * s + c)];
-                    if (e) { mask |= 1u << c; first = e & 0x7FFFFFFFu; onlyc[(size_t)s] = (uint8_t)c; }
-                }
-                nchild[(size_t)s] = (uint8_t)__builtin_popcount(mask);
-                uint32_t w = mask | (first << kNodeFirstShift);
-                if (T.out_id[(size_t)s]) w |= kNodeTermBit;
-                node[(size_t)s] = w;
-            }
             T.skip.assign((size_t)n_states * 4, 0u);
-            for (int64_t s = 0; s < n_states; s++) {
-                uint32_t label = 0, len = 0;
-                int64_t cur = s;
-                while ((int)len < kSkipMaxLen && nchild[(size_t)cur] == 1) {
-                    const int c = onlyc[(size_t)cur];
-                    label |= (uint32_t)c << (2 * len);
-                    len++;
-                    cur = (int64_t)((uint32_t)T.rows[(size_t)(4 * cur + c)] & 0x7FFFFFFFu);
-                    if (T.out_id[(size_t)cur]) break;
+            for (int64_t s = n_states - 1; s >= 0; s--) {
+                uint32_t mask = 0, first = 0;
+                int onlyc = 0;
+                for (int c = 3; c >= 0; c--) {
+                    const uint32_t e = (uint32_t)T.rows[(size_t)(4 * s + c)];
+                    if (e) { mask |= 1u << c; first = e & 0x7FFFFFFFu; onlyc = c; }
                 }
-                uint32_t y = len;
-                if (T.out_id[(size_t)s]) y |= kSkipSelfTerm;
-                if (len && T.out_id[(size_t)cur]) y |= kSkipTargetTerm;
+                uint32_t node = mask | (first << kNodeFirstShift);
+                if (T.out_id[(size_t)s]) node |= kNodeTermBit;
+                uint32_t label = 0, len = 0, target = 0, target_term = 0;
+                if (__builtin_popcount(mask) == 1) {
+                    const uint32_t *ce = &T.skip[(size_t)(4 * (int64_t)first)];
+                    const uint32_t child_node = ce[3];
+                    if ((child_node & kNodeTermBit) || __builtin_popcount(child_node & kNodeMaskBits) != 1) {
+                        label = (uint32_t)onlyc;
+                        len = 1;
+                        target = first;
+                        target_term = child_node & kNodeTermBit ? kSkipTargetTerm : 0u;
+                    } else {
+                        const uint32_t child_len = ce[1] & kSkipLenMask;
+                        label = (uint32_t)onlyc | (ce[0] << 2);   // a 17th symbol falls off the top
+                        if (child_len < (uint32_t)kSkipMaxLen) {
+                            len = child_len + 1;
+                            target = ce[2];
+                            target_term = ce[1] & kSkipTargetTerm;
+                        } else {
+                            len = kSkipMaxLen;
+                            target = (uint32_t)parent[(size_t)ce[2]];
+                        }
+                    }
+                }
                 uint32_t *e = &T.skip[(size_t)(4 * s)];
                 e[0] = label;
-                e[1] = y;
-                e[2] = len ? (uint32_t)cur : 0u;
-                e[3] = node[(size_t)s];
+                e[1] = len | target_term | (T.out_id[(size_t)s] ? kSkipSelfTerm : 0u);
+                e[2] = target;
+                e[3] = node;
             }
         }
+        std::vector<int32_t>().swap(parent);
 
         // ---- step 3c: prefix filter, rank index, dense entries ------------------------
         // Depth-first over the trie down to depth b. A b-mer's bit is set when its walk
