@@ -160,3 +160,30 @@ def test_skip_filter_dense_definition(seed, b):
         else:
             assert not dense[r, 1] & (1 << 9)
             assert np.array_equal(dense[r], skip[new[st]])
+
+
+@pytest.mark.parametrize("cuts", [(15, 16, 17, 33), (16, 32, 48), (1, 17, 34, 40), (31, 32, 47), ()])
+def test_skip_entries_at_the_chain_cap(cuts):
+    """Single-child chains far longer than the 16-base cap, with pattern ends just
+    before, at and after the cap's multiples and a branch deep inside the chain: every
+    state's entry (cut at 16 bases, at a terminal or at the branch) follows its
+    definition."""
+    rng = datagen.rng_for(100 + sum(cuts))
+    long = datagen.iid_text(70, rng).tobytes()
+    other = b"A" if long[20:21] != b"A" else b"C"
+    pats = [long] + [long[:k] for k in cuts] + [long[:20] + other + long[21:45]]
+    go, term = oracle.Trie(pats).export()
+    order = bfs_relabel(go)
+    new = np.empty(go.shape[0], dtype=np.int64)
+    new[np.array(order)] = np.arange(go.shape[0])
+    h = b_.pfac_build(pats, host_only=True, filter_b=3)
+    try:
+        skip, _, _ = b_.pfac_export_shortcuts(h)
+    finally:
+        b_.pfac_destroy(h)
+    assert skip.shape[0] == go.shape[0]
+    lengths = set()
+    for s_old in range(go.shape[0]):
+        check_skip_entry(skip[new[s_old]], s_old, go, term, new)
+        lengths.add(int(skip[new[s_old]][1]) & 31)
+    assert 16 in lengths and 1 in lengths
