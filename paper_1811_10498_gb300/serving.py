@@ -31,6 +31,33 @@ class Request:
     arrival: float            # seconds from the start of the run
 
 
+# device bytes one base costs while its batch is in flight: its byte in, its int32 id out
+BYTES_PER_BASE = 5
+
+
+def take_batch(waiting: deque, in_flight: int, budget: int, slot_bases: int, max_reads: int) -> list:
+    """Pops the next batch from the front of `waiting`, in arrival order: at most
+    `max_reads` requests and `slot_bases` bases, and only while the device bytes of
+    the batches in flight (`in_flight`) plus this one's stay within `budget`. With
+    nothing in flight the first request is taken whatever its size, so a request
+    larger than the budget still runs, alone. A request longer than `slot_bases` can
+    never run: the batch before it is returned as usual, and the call that finds it at
+    the front of `waiting` raises ValueError and leaves it there."""
+    batch, bases = [], 0
+    while waiting and len(batch) < max_reads:
+        r = waiting[0]
+        n = int(r.text.shape[0])
+        if bases + n > slot_bases:
+            if not batch:
+                raise ValueError(f"request {r.rid} ({n} bases) exceeds the slot capacity")
+            break
+        if in_flight + BYTES_PER_BASE * (bases + n) > budget and (in_flight or batch):
+            break        # admitted only when device memory frees up
+        batch.append(waiting.popleft())
+        bases += n
+    return batch
+
+
 @dataclass
 class _Slot:
     stream: object
@@ -58,7 +85,6 @@ class Server:
         self.slot_bases = int(slot_bases)
         self.max_reads = int(max_reads)
         free, _total = torch.cuda.mem_get_info()
-        # device bytes one base costs while in flight: its byte in, its int32 id out
         self.budget = int(free * hbm_fraction)
         self.keep_results = keep_results
         self.slots = []
@@ -82,7 +108,7 @@ class Server:
 
     @staticmethod
     def request_bytes(req: Request) -> int:
-        return 5 * int(req.text.shape[0])
+        return BYTES_PER_BASE * int(req.text.shape[0])
 
     def _launch(self, sl: _Slot, batch: list):
         torch = self.torch
@@ -106,7 +132,7 @@ class Server:
         sl.event = ev
         sl.requests = batch
         sl.starts = offs
-        sl.bytes = 5 * total
+        sl.bytes = BYTES_PER_BASE * total
 
     def run(self, requests, realtime: bool = True):
         """Serve `requests` (sorted by arrival). Returns (per-request latency in s,
@@ -147,18 +173,7 @@ class Server:
             for sl in self.slots:
                 if sl.event is not None or not waiting:
                     continue
-                batch, bases = [], 0
-                while waiting and len(batch) < self.max_reads:
-                    r = waiting[0]
-                    n = int(r.text.shape[0])
-                    if n > self.slot_bases:
-                        raise ValueError(f"request {r.rid} ({n} bases) exceeds the slot capacity")
-                    if bases + n > self.slot_bases:
-                        break
-                    if in_flight + 5 * (bases + n) > self.budget and (in_flight or batch):
-                        break        # admitted only when device memory frees up
-                    batch.append(waiting.popleft())
-                    bases += n
+                batch = take_batch(waiting, in_flight, self.budget, self.slot_bases, self.max_reads)
                 if batch:
                     self._launch(sl, batch)
                     in_flight += sl.bytes
