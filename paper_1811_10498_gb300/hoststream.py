@@ -15,6 +15,16 @@ from __future__ import annotations
 from . import _binding as b
 
 
+def chunk_spans(n: int, chunk: int, max_len: int):
+    """(lo, hi, ext) for each chunk of a text of `n` bases: the chunk's own offsets are
+    [lo, hi), and it is scanned over [lo, ext), which adds the first max_len - 1 bases
+    after it (fewer at the end of the text). A walk from an offset below hi reads at
+    most max_len bases, so it never needs a base at or past ext."""
+    if chunk <= 0 or max_len <= 0:
+        raise ValueError("chunk and max_len must be positive")
+    return [(lo, min(n, lo + chunk), min(n, lo + chunk + max_len - 1)) for lo in range(0, n, chunk)]
+
+
 class HostScanner:
     """Device buffers and streams for chunked scans of host texts with one table."""
 
@@ -53,10 +63,8 @@ class HostScanner:
             raise ValueError("h_out must have one entry per base")
         n_chunks = (n + self.chunk - 1) // self.chunk
         status = torch.zeros(max(1, n_chunks), dtype=torch.int32, device=self.d_text[0].device)
-        for i, lo in enumerate(range(0, n, self.chunk)):
+        for i, (lo, hi, ext) in enumerate(chunk_spans(n, self.chunk, self.max_len)):
             k = i & 1
-            hi = min(n, lo + self.chunk)
-            ext = min(n, hi + self.max_len - 1)
             m = ext - lo
             # input buffer k is free once the scan of chunk i-2 has read it
             self.s_in.wait_event(self.ev_scan[k])
