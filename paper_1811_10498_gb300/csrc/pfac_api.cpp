@@ -407,7 +407,7 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         h->dt.filter1_b = T.filter1_b;
         h->dt.rank_wide = T.rank_wide;
         // The device copy is complete; the host keeps rows, ids and levels for export.
-        std::vector<uint32_t>().swap(h->host.skip);
+        pfac::TableVector<uint32_t>().swap(h->host.skip);
         std::vector<uint32_t>().swap(h->host.filter);
         std::vector<uint16_t>().swap(h->host.rank16);
         std::vector<uint32_t>().swap(h->host.rank32);
@@ -485,12 +485,13 @@ int pfac_export_shortcuts(pfac_handle h, uint32_t *skip, int64_t skip_words, uin
     if (!h) return fail(PFAC_ERR_INVALID_ARG);
     if (h->device >= 0) return fail(PFAC_ERR_UNSUPPORTED);
     const pfac::HostTables &T = h->host;
-    struct Out { uint32_t *dst; int64_t cap; const std::vector<uint32_t> &src; } outs[] = {
-        {skip, skip_words, T.skip}, {filter, filter_words, T.filter}, {dense, dense_words, T.dense}};
+    struct Out { uint32_t *dst; int64_t cap; const uint32_t *src; size_t words; } outs[] = {
+        {skip, skip_words, T.skip.data(), T.skip.size()}, {filter, filter_words, T.filter.data(), T.filter.size()},
+        {dense, dense_words, T.dense.data(), T.dense.size()}};
     for (auto &o : outs)
-        if (o.dst && o.cap < (int64_t)o.src.size()) return fail(PFAC_ERR_INVALID_ARG);
+        if (o.dst && o.cap < (int64_t)o.words) return fail(PFAC_ERR_INVALID_ARG);
     for (auto &o : outs)
-        if (o.dst) memcpy(o.dst, o.src.data(), o.src.size() * 4);
+        if (o.dst && o.words) memcpy(o.dst, o.src, o.words * 4);
     return PFAC_OK;
 }
 

@@ -3,6 +3,9 @@
 
 #include <stdint.h>
 
+#include <memory>
+#include <new>
+#include <utility>
 #include <vector>
 
 namespace pfac {
@@ -52,16 +55,29 @@ constexpr int kSkipMaxLen = 16;
 constexpr int kMaxFilterB = 12;
 constexpr int kFilter1B = 10;      // order of the shared-memory first-level filter
 
+// Allocator whose construction without a value leaves the element uninitialised: the
+// builder sizes its largest arrays with resize() and then writes every element from
+// several threads, instead of zero-filling gigabytes on one thread first.
+template <typename T>
+struct NoInitAllocator : std::allocator<T> {
+    template <typename U> struct rebind { using other = NoInitAllocator<U>; };
+    NoInitAllocator() = default;
+    template <typename U> NoInitAllocator(const NoInitAllocator<U> &) noexcept {}
+    template <typename U> void construct(U *p) noexcept { ::new ((void *)p) U; }
+    template <typename U, typename... A> void construct(U *p, A &&...a) { ::new ((void *)p) U(std::forward<A>(a)...); }
+};
+template <typename T> using TableVector = std::vector<T, NoInitAllocator<T>>;
+
 struct HostTables {
     int64_t n_states = 0;
     int32_t n_patterns = 0;
     int32_t max_len = 0;
     int32_t min_len = 0;
     int64_t n_duplicates = 0;
-    std::vector<int32_t> rows;       // 4 * n_states: child | (terminal(child) << 31), 0 = none
-    std::vector<int32_t> out_id;     // n_states: pattern id ending at the state, 0 = none
+    TableVector<int32_t> rows;       // 4 * n_states: child | (terminal(child) << 31), 0 = none
+    TableVector<int32_t> out_id;     // n_states: pattern id ending at the state, 0 = none
     std::vector<int64_t> level;      // max_len + 2: states of depth d in [level[d], level[d+1])
-    std::vector<uint32_t> skip;      // 4 * n_states (empty when the trie has 2^27 states or more)
+    TableVector<uint32_t> skip;      // 4 * n_states (empty when the trie has 2^27 states or more)
     int32_t filter_b = 0;            // 0 = no prefix filter
     std::vector<uint32_t> filter;    // 4^b bits
     int32_t rank_wide = 0;           // 32-bit rank entries

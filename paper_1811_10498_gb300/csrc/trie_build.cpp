@@ -278,11 +278,12 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
         T.min_len = min_len;
         T.n_duplicates = dups;
         T.level.assign(level.begin(), level.begin() + max_len + 2);
-        T.rows.assign((size_t)n_states * 4, 0);
-        T.out_id.assign((size_t)n_states, 0);
-        std::vector<int32_t> parent((size_t)n_states, 0);   // id -> id of its parent
+        // Sized without a fill: the passes below write every element of these arrays.
+        T.rows.resize((size_t)n_states * 4);
+        T.out_id.resize((size_t)n_states);
+        TableVector<int32_t> parent((size_t)n_states);      // id -> id of its parent
         const bool with_skip = n_states < kMaxNodeStates;
-        if (with_skip) T.skip.assign((size_t)n_states * 4, 0u);
+        if (with_skip) T.skip.resize((size_t)n_states * 4);
 
         // ---- step 3a: rows and pattern ids -------------------------------------------
         // Row entries: the child's id, bit 31 set when the child is terminal.
@@ -363,9 +364,12 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
                     parent[(size_t)g] = e ? (int32_t)(B.base[e - 1] + (B.parent[(size_t)q] - B.start[e - 1])) : up;
                     for (int c = 0; c < 4; c++) {
                         const uint32_t v = (uint32_t)B.rows[(size_t)(4 * q + c)];
-                        if (!v) continue;
-                        const int64_t child = B.base[e + 1] + ((int64_t)(v & 0x7FFFFFFFu) - B.start[e + 1]);
-                        T.rows[(size_t)(4 * g + c)] = (int32_t)((uint32_t)child | (v & 0x80000000u));
+                        uint32_t w = 0;
+                        if (v) {
+                            const int64_t child = B.base[e + 1] + ((int64_t)(v & 0x7FFFFFFFu) - B.start[e + 1]);
+                            w = (uint32_t)child | (v & 0x80000000u);
+                        }
+                        T.rows[(size_t)(4 * g + c)] = (int32_t)w;
                     }
                 }
             std::vector<int32_t>().swap(B.rows);
@@ -380,7 +384,7 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
         if (with_skip)
             for (int64_t s = level[kTopDepth] - 1; s >= 0; s--) skip_entry(s);
         std::vector<SubTrie>().swap(sub);
-        std::vector<int32_t>().swap(parent);
+        TableVector<int32_t>().swap(parent);
 
         // ---- step 3c: prefix filter, rank index, dense entries ------------------------
         // Depth-first over the trie down to depth b. A b-mer's bit is set when its walk
