@@ -187,3 +187,59 @@ def test_skip_entries_at_the_chain_cap(cuts):
         check_skip_entry(skip[new[s_old]], s_old, go, term, new)
         lengths.add(int(skip[new[s_old]][1]) & 31)
     assert 16 in lengths and 1 in lengths
+
+
+def test_threaded_build_numbers_prefixes_by_length_then_lexicographically():
+    """A set big enough for the builder to spread its sub-tries over several threads,
+    checked against an independent definition of the breadth-first numbering: the
+    distinct prefixes of the patterns (the empty one included) sorted by length and then
+    lexicographically in A < C < G < T order. A row entry is the id of the prefix
+    extended by that base, and a state's pattern id is the lowest 1-based index of a
+    pattern equal to its prefix."""
+    rng = datagen.rng_for(11)
+    text = datagen.iid_text(1 << 20, rng)
+    blob, offs = datagen.pattern_set(text, rng, 300_000, (1, 28), 0.7)
+    lens = np.diff(offs)
+    n = lens.size
+    assert int(lens.sum()) >= 4 << 20          # four threads' worth of bases
+    base = np.searchsorted(np.frombuffer(b"ACGT", dtype=np.uint8), blob).astype(np.uint64)
+    # key of a prefix of d bases: d << 56 | its code, first base most significant
+    # (lengths up to 28, so a code fits in 56 bits)
+    sh = np.uint64(56)
+    code = np.zeros(n, dtype=np.uint64)
+    full = np.zeros(n, dtype=np.uint64)
+    keys = [np.zeros(1, dtype=np.uint64)]
+    for d in range(1, 29):
+        live = lens >= d
+        code[live] = code[live] * np.uint64(4) + base[offs[:-1][live] + d - 1]
+        keys.append((np.uint64(d) << sh) | code[live])
+        ends = lens == d
+        full[ends] = (np.uint64(d) << sh) | code[ends]
+    keys = np.unique(np.concatenate(keys))
+    depth = (keys >> sh).astype(np.int64)
+    kcode = keys & np.uint64((1 << 56) - 1)
+
+    first = np.full(keys.size, n + 1, dtype=np.int64)
+    np.minimum.at(first, np.searchsorted(keys, full), np.arange(1, n + 1))
+    want_out = np.where(first == n + 1, 0, first)
+
+    h = b.pfac_build((blob, offs), host_only=True, filter_b=-1)
+    try:
+        rows, out_id, level = b.pfac_export(h)
+        info = b.pfac_info_ex(h)
+    finally:
+        b.pfac_destroy(h)
+    assert info["n_states"] == keys.size
+    assert info["n_duplicates"] == n - np.unique(full).size
+    assert np.array_equal(out_id, want_out)
+    assert np.array_equal(level, np.searchsorted(depth, np.arange(info["max_len"] + 2)))
+    urows = rows.view(np.uint32)
+    for c in range(4):
+        inner = depth < 28
+        child = ((depth[inner].astype(np.uint64) + np.uint64(1)) << sh) | (kcode[inner] * np.uint64(4) + np.uint64(c))
+        pos = np.minimum(np.searchsorted(keys, child), keys.size - 1)
+        exists = keys[pos] == child
+        want = np.zeros(keys.size, dtype=np.uint32)
+        want[inner] = np.where(exists, pos, 0).astype(np.uint32)
+        want[inner] |= np.where(exists & (want_out[pos] != 0), np.uint32(1 << 31), np.uint32(0))
+        assert np.array_equal(urows[:, c], want)
