@@ -113,19 +113,25 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the scan kernel from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "scan_kernel_genome_scan.md")
-    try:
-        txt = open(p).read()
-    except OSError:
-        return None
+def profile_fields(txt: str) -> dict:
+    """The "- key: value" lines of an ncu summary."""
     vals = {}
     for line in txt.splitlines():
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
+    return vals
+
+
+def profiled_traffic(path: str | None = None):
+    """DRAM bytes per launch of the scan kernel from the committed ncu summary (or the
+    summary at `path`), if it was taken on the current kernel source; else None."""
+    p = path or os.path.join(ROOT, "profiles", "scan_kernel_genome_scan.md")
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None
+    vals = profile_fields(txt)
     if vals.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     try:
