@@ -248,6 +248,29 @@ def check_all_matches_random_tiny(lib, cases: int = 300, seed: int = 17):
         assert longest == brute.brute_longest(text, pats), (text, pats)
 
 
+def check_pack_layout(lib=None):
+    """Hand-packed words: base p of the text in bits 2(p mod 16)..2(p mod 16)+1 of word
+    p / 16 with A=0, C=1, G=2, T=3, bases past the end 0; the first byte outside
+    A/C/G/T is reported by its offset."""
+    words, bad = oracle.pack(b"ACGT")
+    assert bad == -1 and words.tolist() == [0b11100100]
+    words, bad = oracle.pack(b"T" * 16 + b"C")
+    assert words.tolist() == [0xFFFFFFFF, 1]
+    words, bad = oracle.pack(b"A" * 15 + b"G")
+    assert words.tolist() == [2 << 30]
+    assert oracle.pack(b"ACGTnA")[1] == 4
+    assert oracle.pack(b"NACGT")[1] == 0
+    assert oracle.pack(b"")[0].shape == (0,)
+
+
+def check_compact_definition(lib=None):
+    """The match list holds exactly the offsets with a non-zero id, ascending."""
+    offs, ids = oracle.compact(np.array([0, 3, 0, 0, 7, 1], dtype=np.int32))
+    assert offs.tolist() == [1, 4, 5] and ids.tolist() == [3, 7, 1]
+    offs, ids = oracle.compact(np.zeros(5, dtype=np.int32))
+    assert offs.size == 0 and ids.size == 0
+
+
 ALL_PINS = [check_fig1_numbering, check_table1, check_fig2_failure, check_fig1_scans,
             check_random_tiny, check_special_cases, check_invariants, check_fig1_all,
-            check_all_matches_random_tiny]
+            check_all_matches_random_tiny, check_pack_layout, check_compact_definition]

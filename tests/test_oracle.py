@@ -57,19 +57,3 @@ def test_reads_scan_stops_at_read_end(oracle_lib):
     out = oracle.pfac_scan_reads(reads, offs, np.array([0, 1], dtype=np.int32), sets)
     # read 0 = "AC" cannot contain ACG; read 1 = "GTACG" has ACG at its offset 2.
     assert out.tolist() == [0, 0, 0, 0, 1, 0, 0]
-
-
-def test_pack_definition():
-    words, bad = oracle.pack(b"ACGT")
-    assert bad == -1 and words.tolist() == [0b11100100]
-    words, bad = oracle.pack(b"T" * 16 + b"C")
-    assert words.tolist() == [0xFFFFFFFF, 1]
-    words, bad = oracle.pack(b"A" * 15 + b"G")
-    assert words.tolist() == [2 << 30]
-    assert oracle.pack(b"ACGTnA")[1] == 4
-    assert oracle.pack(b"")[0].shape == (0,)
-
-
-def test_compact_definition():
-    offs, ids = oracle.compact(np.array([0, 3, 0, 0, 7, 1], dtype=np.int32))
-    assert offs.tolist() == [1, 4, 5] and ids.tolist() == [3, 7, 1]

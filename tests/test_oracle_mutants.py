@@ -1,8 +1,11 @@
 """Plant plausible mistakes in copies of the CPU oracle and check that the pins
-catch every one of them (CPU only; the mutants are built with the host compiler
-into a temporary folder and never touch the real oracle)."""
+catch every one of them (CPU only). Mutants of the C part are built with the host
+compiler into a temporary folder; mutants of the Python part are executed as a
+separate module whose function stands in for the oracle's during the test. Neither
+touches the real oracle."""
 import os
 import subprocess
+import types
 
 import pytest
 
@@ -69,3 +72,69 @@ def test_pins_catch_mutant(name, tmp_path):
         except (AssertionError, oracle.OracleError):
             failed.append(check.__name__)
     assert failed, f"no pin detects the mutant {name}"
+
+
+# Mutants of the Python part of the oracle: (function replaced, old text, new text).
+PY_MUTANTS = {
+    # A start is end - length + 1.
+    "all_matches_start_off_by_one": ("all_matches",
+        "starts = ends - lens + 1",
+        "starts = ends - lens"),
+    # Equal pattern strings at one start: the lowest id is reported.
+    "all_matches_keeps_highest_duplicate_id": ("all_matches",
+        "order = np.lexsort((ids, lens, starts))",
+        "order = np.lexsort((-ids, lens, starts))"),
+    # Equal pattern strings at one start are reported once.
+    "all_matches_without_dedupe": ("all_matches",
+        "keep[1:] = (starts[1:] != starts[:-1]) | (lens[1:] != lens[:-1])",
+        "keep[1:] = True"),
+    # Within a start the list is ordered by length, not by id.
+    "all_matches_sorted_by_id": ("all_matches",
+        "order = np.lexsort((ids, lens, starts))",
+        "order = np.lexsort((lens, ids, starts))"),
+    # Base p goes to the low bits of its word first.
+    "pack_high_bits_first": ("pack",
+        "shifts = (2 * np.arange(16, dtype=np.uint32))",
+        "shifts = (30 - 2 * np.arange(16, dtype=np.uint32))"),
+    # The first bad byte is reported at its own offset.
+    "pack_first_bad_off_by_one": ("pack",
+        "first_bad = int(bad[0]) if bad.size else -1",
+        "first_bad = int(bad[0]) + 1 if bad.size else -1"),
+    # Offsets with id 0 are not matches.
+    "compact_keeps_zeros": ("compact",
+        "offs = np.flatnonzero(out_ids).astype(np.int64)",
+        "offs = np.arange(out_ids.size, dtype=np.int64)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_pins_catch_python_mutant(name, monkeypatch):
+    func, old, new = PY_MUTANTS[name]
+    path = oracle.__file__
+    src = open(path).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mod = types.ModuleType("oracle_mutant")
+    mod.__file__ = path
+    exec(compile(src.replace(old, new), path, "exec"), mod.__dict__)
+    monkeypatch.setattr(oracle, func, getattr(mod, func))
+    lib = oracle.load()
+    failed = []
+    for check in pins.ALL_PINS:
+        try:
+            check(lib)
+        except (AssertionError, oracle.OracleError):
+            failed.append(check.__name__)
+    assert failed, f"no pin detects the mutant {name}"
+
+
+def test_python_mutant_harness_passes_the_unchanged_oracle(monkeypatch):
+    """Control: the oracle's own source, executed the same way, passes every pin."""
+    path = oracle.__file__
+    mod = types.ModuleType("oracle_copy")
+    mod.__file__ = path
+    exec(compile(open(path).read(), path, "exec"), mod.__dict__)
+    for func in {f for f, _, _ in PY_MUTANTS.values()}:
+        monkeypatch.setattr(oracle, func, getattr(mod, func))
+    lib = oracle.load()
+    for check in pins.ALL_PINS:
+        check(lib)
