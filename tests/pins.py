@@ -271,6 +271,21 @@ def check_compact_definition(lib=None):
     assert offs.size == 0 and ids.size == 0
 
 
+def check_reads_scan(lib=None):
+    """Per-read scans: a walk ends at its read's end, and each read uses its own set's
+    trie and ids. Worked by hand."""
+    reads = np.frombuffer(b"ACGTACG", dtype=np.uint8)
+    offs = np.array([0, 2, 7])
+    # read 0 = "AC" with {ACG}: ACG does not fit in the read.
+    # read 1 = "GTACG" with {ACG, AC}: ACG at its offset 2 (text offset 4).
+    out = oracle.pfac_scan_reads(reads, offs, np.array([0, 1], dtype=np.int32), [[b"ACG"], [b"ACG", b"AC"]])
+    assert out.tolist() == [0, 0, 0, 0, 1, 0, 0]
+    # read 1 with {GT, ACG}: GT (id 1) at text offset 2, ACG (id 2) at 4.
+    out = oracle.pfac_scan_reads(reads, offs, np.array([0, 1], dtype=np.int32), [[b"ACG"], [b"GT", b"ACG"]])
+    assert out.tolist() == [0, 0, 1, 0, 2, 0, 0]
+
+
 ALL_PINS = [check_fig1_numbering, check_table1, check_fig2_failure, check_fig1_scans,
             check_random_tiny, check_special_cases, check_invariants, check_fig1_all,
-            check_all_matches_random_tiny, check_pack_layout, check_compact_definition]
+            check_all_matches_random_tiny, check_pack_layout, check_compact_definition,
+            check_reads_scan]

@@ -48,12 +48,3 @@ def test_threaded_scan_equals_single(oracle_lib):
     w = datagen.small_scan(n_bases=200_000, n_patterns=300)
     t = oracle.Trie((w.blob, w.offsets), oracle_lib)
     assert np.array_equal(t.scan(w.text), t.scan_threads(w.text, 7))
-
-
-def test_reads_scan_stops_at_read_end(oracle_lib):
-    reads = np.frombuffer(b"ACGTACG", dtype=np.uint8)
-    offs = np.array([0, 2, 7])
-    sets = [[b"ACG"], [b"ACG", b"AC"]]
-    out = oracle.pfac_scan_reads(reads, offs, np.array([0, 1], dtype=np.int32), sets)
-    # read 0 = "AC" cannot contain ACG; read 1 = "GTACG" has ACG at its offset 2.
-    assert out.tolist() == [0, 0, 0, 0, 1, 0, 0]
