@@ -14,7 +14,7 @@
 
 #include <algorithm>
 #include <new>
-#include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/pfac.h"
@@ -62,23 +62,31 @@ bool is_fasta(const std::vector<uint8_t> &data)
     return false;
 }
 
-// FASTA records: each record's sequence lines joined (headers dropped).
-std::vector<std::string> fasta_records(const std::vector<uint8_t> &data)
+// FASTA records joined in place: each record's sequence lines are moved together
+// (header lines dropped), with one '\n' between records when `newline_between` is set.
+// Returns each record's (offset, length) in `data`, which is cut to the joined bytes.
+// A record opens at a header line, or at a sequence line before the first header.
+// Writes never pass the line being read: a sequence line moves left onto itself or
+// earlier, and the one separator byte a record adds replaces its header's '>'.
+std::vector<std::pair<size_t, size_t>> fasta_join_in_place(std::vector<uint8_t> &data, bool newline_between)
 {
-    std::vector<std::string> recs;
-    bool open = false;
-    for_each_line(data.data(), data.data() + data.size(), [&](const uint8_t *b, const uint8_t *e) {
-        if (b < e && *b == '>') {
-            recs.emplace_back();
-            open = true;
-        } else if (b < e) {
-            if (!open) {
-                recs.emplace_back();
-                open = true;
-            }
-            recs.back().append((const char *)b, (size_t)(e - b));
+    std::vector<std::pair<size_t, size_t>> recs;
+    uint8_t *base = data.data();
+    size_t w = 0;
+    for_each_line(base, base + data.size(), [&](const uint8_t *b, const uint8_t *e) {
+        if (b == e) return;
+        const bool header = *b == '>';
+        if (header || recs.empty()) {
+            if (newline_between && !recs.empty()) base[w++] = '\n';
+            recs.emplace_back(w, 0);
+            if (header) return;
         }
+        const size_t len = (size_t)(e - b);
+        memmove(base + w, b, len);
+        w += len;
+        recs.back().second += len;
     });
+    data.resize(w);
     return recs;
 }
 
@@ -96,12 +104,14 @@ extern "C" pfac_handle pfac_build_file(const char *path, const pfac_build_opts *
             pfac::set_last_error(PFAC_ERR_IO);
             return nullptr;
         }
-        std::vector<std::string> pats;
+        // Patterns point into the file's bytes: lines as they are, FASTA records
+        // joined in place.
+        std::vector<std::pair<size_t, size_t>> pats;
         if (is_fasta(data)) {
-            pats = fasta_records(data);
+            pats = fasta_join_in_place(data, false);
         } else {
             for_each_line(data.data(), data.data() + data.size(), [&](const uint8_t *b, const uint8_t *e) {
-                if (b < e) pats.emplace_back((const char *)b, (size_t)(e - b));
+                if (b < e) pats.emplace_back((size_t)(b - data.data()), (size_t)(e - b));
             });
         }
         if (pats.empty() || pats.size() > (size_t)INT32_MAX) {
@@ -111,12 +121,12 @@ extern "C" pfac_handle pfac_build_file(const char *path, const pfac_build_opts *
         std::vector<const char *> ptrs(pats.size());
         std::vector<int32_t> lens(pats.size());
         for (size_t j = 0; j < pats.size(); j++) {
-            if (pats[j].size() > (size_t)INT32_MAX) {
+            if (pats[j].second > (size_t)INT32_MAX) {
                 pfac::set_last_error(PFAC_ERR_INVALID_ARG);
                 return nullptr;
             }
-            ptrs[j] = pats[j].data();
-            lens[j] = (int32_t)pats[j].size();
+            ptrs[j] = (const char *)data.data() + pats[j].first;
+            lens[j] = (int32_t)pats[j].second;
         }
         return pfac_build_ex(ptrs.data(), lens.data(), (int32_t)pats.size(), opts);
     } catch (const std::bad_alloc &) {
@@ -131,15 +141,7 @@ extern "C" int pfac_read_text_file(const char *path, int32_t fasta, uint8_t *buf
     try {
         std::vector<uint8_t> data;
         if (!slurp(path, &data)) return pfac::set_last_error(PFAC_ERR_IO);
-        if (fasta) {
-            std::vector<std::string> recs = fasta_records(data);
-            std::vector<uint8_t> text;
-            for (size_t i = 0; i < recs.size(); i++) {
-                if (i) text.push_back('\n');
-                text.insert(text.end(), recs[i].begin(), recs[i].end());
-            }
-            data.swap(text);
-        }
+        if (fasta) fasta_join_in_place(data, true);
         *len = (int64_t)data.size();
         if (buf && cap > 0) memcpy(buf, data.data(), (size_t)std::min<int64_t>(cap, (int64_t)data.size()));
         return PFAC_OK;

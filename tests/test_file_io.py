@@ -77,3 +77,77 @@ def test_text_file_as_is_and_fasta(tmp_path):
     e0 = tmp_path / "zero.txt"
     e0.write_bytes(b"")
     assert b.read_text_file(str(e0)).size == 0
+
+
+def fasta_reference(raw: bytes):
+    """Records of a FASTA file by the front end's rules, written out plainly: lines split
+    at '\\n' with a trailing '\\r' dropped, empty lines skipped, a line starting with '>'
+    opens a record, a sequence line before any header opens one too, and a record's
+    sequence lines are joined."""
+    recs = []
+    for line in raw.split(b"\n"):
+        if line.endswith(b"\r"):
+            line = line[:-1]
+        if not line:
+            continue
+        if line.startswith(b">"):
+            recs.append(b"")
+            continue
+        if not recs:
+            recs.append(b"")
+        recs[-1] += line
+    return recs
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_fasta_files_against_the_plain_rules(tmp_path, seed):
+    """Random line mixes (seeds 0-5, headers without sequence included) and well-formed
+    files where every header has one to three sequence lines (seeds 6-11)."""
+    rng = np.random.default_rng(seed)
+
+    def seq():
+        return rng.choice(np.frombuffer(b"ACGT", dtype=np.uint8), size=int(rng.integers(1, 30))).tobytes()
+
+    parts = []
+    for _ in range(int(rng.integers(1, 40))):
+        kind = rng.integers(0, 10)
+        if kind < 3:
+            parts.append(b">rec " + str(int(rng.integers(1000))).encode())
+            if seed >= 6:
+                parts += [seq() for _ in range(int(rng.integers(1, 4)))]
+        elif kind < 4:
+            parts.append(b"")
+        else:
+            parts.append(seq())
+    ends = [b"\r\n" if rng.random() < 0.3 else b"\n" for _ in parts]
+    raw = b"".join(p + e for p, e in zip(parts, ends))
+    if rng.random() < 0.5:
+        raw = raw.rstrip(b"\r\n")                        # no final newline
+    if seed % 2 == 0 and not raw.lstrip(b"\r\n").startswith(b">"):
+        raw = b">first\n" + raw                          # a FASTA file for the pattern front end
+    f = tmp_path / "x.fa"
+    f.write_bytes(raw)
+    recs = fasta_reference(raw)
+    assert b.read_text_file(str(f), fasta=True).tobytes() == b"\n".join(recs)
+    if not raw.lstrip(b"\r\n\t ").startswith(b">"):
+        return                                           # read as one pattern per line instead
+    if not recs or any(len(r) == 0 for r in recs):
+        with pytest.raises(b.PfacError) as e:
+            b.pfac_build_file(str(f), host_only=True)
+        assert e.value.code in (b.CODE["PFAC_ERR_EMPTY_PATTERN"], b.CODE["PFAC_ERR_INVALID_ARG"])
+        return
+    h = b.pfac_build_file(str(f), host_only=True)
+    try:
+        same_table(h, recs)
+        assert b.pfac_info_ex(h)["n_patterns"] == len(recs)
+    finally:
+        b.pfac_destroy(h)
+
+
+def test_fasta_header_without_sequence_is_an_empty_pattern(tmp_path):
+    f = tmp_path / "e.fa"
+    f.write_bytes(b">a\nACGT\n>b\n>c\nGG\n")
+    with pytest.raises(b.PfacError) as e:
+        b.pfac_build_file(str(f), host_only=True)
+    assert e.value.code == b.CODE["PFAC_ERR_EMPTY_PATTERN"]
+    assert b.read_text_file(str(f), fasta=True).tobytes() == b"ACGT\n\nGG"

@@ -1,7 +1,7 @@
 """The host code under AddressSanitizer and UndefinedBehaviorSanitizer (no GPU): the
-table builder of the CUDA library (csrc/trie_build.cpp) and, separately, the CPU oracle,
-each driven by a fuzz program in tests/sanitize/ with random inputs; and the builder's
-threads under ThreadSanitizer."""
+table builder (csrc/trie_build.cpp) and the file front end (csrc/pfac_io.cpp) of the CUDA
+library and, separately, the CPU oracle, each driven by a fuzz program in tests/sanitize/
+with random inputs; and the builder's threads under ThreadSanitizer."""
 import os
 import shutil
 import subprocess
@@ -48,6 +48,18 @@ def test_table_builder_threads_under_thread_sanitizer(tmp_path):
            "-I" + os.path.join(ROOT, "include"), os.path.join(HERE, "sanitize", "builder_fuzz.cpp"),
            os.path.join(ROOT, "paper_1811_10498_gb300", "csrc", "trie_build.cpp"), "-o", str(exe)]
     assert "builder_fuzz: ok" in _run(cmd, exe, tmp_path, "threaded")
+
+
+def test_file_front_end_under_sanitizers(tmp_path):
+    """Files read as texts and as pattern files: FASTA records are joined in place, and
+    every pattern pointer handed to the table build stays inside the file's bytes."""
+    if not shutil.which("g++"):
+        pytest.skip("no host C++ compiler")
+    exe = tmp_path / "io_fuzz"
+    cmd = ["g++", "-std=c++17", *SAN, f"-I{_cuda_include()}", "-I" + os.path.join(ROOT, "include"),
+           os.path.join(HERE, "sanitize", "io_fuzz.cpp"),
+           os.path.join(ROOT, "paper_1811_10498_gb300", "csrc", "pfac_io.cpp"), "-o", str(exe)]
+    assert "io_fuzz: ok" in _run(cmd, exe, tmp_path, str(tmp_path / "f.txt"))
 
 
 def test_oracle_under_sanitizers(tmp_path):
