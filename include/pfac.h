@@ -68,7 +68,10 @@ typedef struct pfac_table *pfac_handle;
 /* Build the goto table from `n` patterns and upload it once to the current device.
  *   patterns[j] : host pointer to the bytes of pattern j (not NUL-terminated)
  *   lengths[j]  : its length in bytes, >= 1
- * The library copies everything it needs; the caller keeps its arrays.
+ * The library copies everything it needs; the caller keeps its arrays. Sets of
+ * 2 Mi bases or more are built on up to 16 host threads (one sub-trie per
+ * three-base prefix, run side by side); the call returns when all of them are
+ * done, and the table is the same whatever the thread count.
  * Returns NULL on error; pfac_last_error() then gives PFAC_ERR_INVALID_ARG (n <= 0
  * or a NULL array), PFAC_ERR_EMPTY_PATTERN, PFAC_ERR_BAD_SYMBOL,
  * PFAC_ERR_TOO_MANY_STATES, PFAC_ERR_OOM or PFAC_ERR_CUDA. */
