@@ -139,10 +139,14 @@ def _events_median(torch, run, reps: int, flush=None) -> float:
 _AUTO = {"walk_loads": 2, "lane_offsets": 16, "l2_persist": -1}
 
 
-def _start(h: int, n_bases: int, knobs) -> dict:
-    """The library's default configuration for ``n_bases``, with automatic fields
-    replaced by the values they stand for."""
+def _start(h: int, n_bases: int, knobs, packed: bool = True) -> dict:
+    """The library's default configuration for ``n_bases`` (the handle's configuration
+    must have been reset), with automatic fields replaced by the values they stand for.
+    ``pfac_get_config`` describes packed-text launches; an ASCII scan or a batched pass
+    with no configuration set uses 2 stages and 16 offsets per lane instead."""
     d = b.pfac_get_config(h, n_bases)
+    if not packed:
+        d = dict(d, stages=2, lane_offsets=16)
     cfg = {"kernel": d["kernel"]}
     for k, _ in knobs:
         v = d[k]
@@ -177,7 +181,7 @@ def tune_scan(table, d_input, n_bases: int, packed: bool = True, sample_bases: i
             b.pfac_match(h, src, out, length=n)
 
     b.pfac_set_config(h, None)
-    start = _start(h, n, knobs or SCAN_KNOBS)
+    start = _start(h, n, knobs or SCAN_KNOBS, packed)
     if start["kernel"] != 2:
         return {"kernel": start["kernel"], "cached": False}
     run()
@@ -229,7 +233,7 @@ def tune_batched(tables, d_texts, d_read_offsets, d_read_set, d_out, reps: int =
         b.pfac_match_batched(handles, d_texts, d_read_offsets, d_read_set, d_out)
 
     b.pfac_set_config(h0, None)
-    start = _start(h0, 0, knobs or BATCH_KNOBS)
+    start = _start(h0, 0, knobs or BATCH_KNOBS, packed=False)
     # offsets outside every read are never written: -1 marks them on both sides
     d_out.fill_(-1)
     run()

@@ -124,3 +124,22 @@ def test_tune_scan_ascii_is_exact(tmp_path):
     got = t.match(d).cpu().numpy()
     assert np.array_equal(got, oracle.Trie((blob, offs)).scan(text))
     t.close()
+
+
+def test_search_starts_from_the_default_of_the_launch_kind(cuda_lib_path):
+    """The first candidate timed is the configuration the library uses when none is set:
+    3 stages and 32 offsets per lane for packed text, 2 and 16 for ASCII text and for
+    batched passes (a host-only handle is enough to read it)."""
+    from paper_1811_10498_gb300 import _binding as b
+    h = b.pfac_build([b"ACGT", b"GATTACA"], host_only=True)
+    try:
+        b.pfac_set_config(h, None)
+        packed = autotune._start(h, 1 << 20, autotune.SCAN_KNOBS, packed=True)
+        ascii_ = autotune._start(h, 1 << 20, autotune.SCAN_KNOBS, packed=False)
+        batch = autotune._start(h, 0, autotune.BATCH_KNOBS, packed=False)
+    finally:
+        b.pfac_destroy(h)
+    assert (packed["stages"], packed["lane_offsets"]) == (3, 32)
+    assert (ascii_["stages"], ascii_["lane_offsets"]) == (2, 16)
+    assert batch["lane_offsets"] == 16 and batch["threads"] == 1024 and batch["ctas_per_sm"] == 1
+    assert packed["walk_loads"] == ascii_["walk_loads"] == batch["walk_loads"] == 2
