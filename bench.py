@@ -160,8 +160,9 @@ def make_workload(rank: int, n_bases: int, n_patterns: int):
     return datagen.genome_scan(seed=2 + rank, n_bases=n_bases, n_patterns=n_patterns)
 
 
-def cpu_baseline(w, got_prefix: np.ndarray | None, seconds: float = 8.0):
-    """The CPU oracle (scan only), all host threads, on the first bases of the text."""
+def cpu_baseline(w, got_prefix: np.ndarray | None, seconds: float = 8.0, single_seconds: float = 2.0):
+    """The CPU oracle (scan only) on the first bases of the text: on all host threads,
+    and (``single_core``) the same scan on one thread over a shorter prefix."""
     import oracle
     threads = os.cpu_count() or 1
     trie = oracle.Trie((w.blob, w.offsets))
@@ -181,6 +182,12 @@ def cpu_baseline(w, got_prefix: np.ndarray | None, seconds: float = 8.0):
                      f"{threads} threads, scan only"}
     if got_prefix is not None:
         out["parity_on_sample"] = bool(np.array_equal(ref[:sample], got_prefix[:sample]))
+    one = int(min(n, max(1 << 18, sample / dt / threads * single_seconds)))
+    t0 = time.perf_counter()
+    trie.scan(w.text, 0, one)
+    dt1 = time.perf_counter() - t0
+    out["single_core"] = {"value": one / dt1 / 1e9, "unit": UNIT, "cores": 1,
+                          "sample": f"first {one} offsets of the same text, 1 thread, scan only"}
     return out
 
 
