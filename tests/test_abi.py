@@ -64,3 +64,38 @@ def test_host_only_handle_rejects_scans(cuda_lib_path):
         assert b.pfac_info_ex(h)["device"] == -1
     finally:
         b.pfac_destroy(h)
+
+
+def test_launch_configuration_checks(cuda_lib_path):
+    """pfac_set_config rejects values outside the documented ranges, refuses kernel 2 for
+    a table without a prefix filter, and pfac_get_config reports what was set (host-only
+    handles: no device call)."""
+    from paper_1811_10498_gb300 import _binding as b
+    h = b.pfac_build([b"ACGT", b"GATTACA", b"TTAGG"], host_only=True, filter_b=4)
+    h_plain = b.pfac_build([b"ACGT"], host_only=True, filter_b=-1)
+    try:
+        good = {"kernel": 2, "threads": 512, "ctas_per_sm": 1, "stages": 4, "walk_loads": 3, "lane_offsets": 32}
+        b.pfac_set_config(h, good)
+        got = b.pfac_get_config(h)
+        assert {k: got[k] for k in good} == good
+        for field, bad in [("kernel", 3), ("kernel", -1), ("threads", 100), ("threads", 32), ("threads", 2048),
+                           ("ctas_per_sm", 33), ("stages", 1), ("stages", 9), ("walk_loads", -1),
+                           ("lane_offsets", 8), ("lane_offsets", 64)]:
+            with pytest.raises(b.PfacError) as e:
+                b.pfac_set_config(h, dict(good, **{field: bad}))
+            assert e.value.code == b.CODE["PFAC_ERR_INVALID_ARG"], (field, bad)
+        # a rejected configuration leaves the previous one in place
+        assert {k: b.pfac_get_config(h)[k] for k in good} == good
+        with pytest.raises(b.PfacError) as e:
+            b.pfac_set_config(h_plain, {"kernel": 2})
+        assert e.value.code == b.CODE["PFAC_ERR_UNSUPPORTED"]
+        b.pfac_set_config(h_plain, {"kernel": 1})
+        # zero fields mean the library's default; a reset restores every default
+        b.pfac_set_config(h, {"kernel": 0})
+        d = b.pfac_get_config(h)
+        assert d["stages"] == 3 and d["lane_offsets"] == 32 and d["threads"] == 1024
+        b.pfac_set_config(h, None)
+        assert b.pfac_get_config(h) == d
+    finally:
+        b.pfac_destroy(h)
+        b.pfac_destroy(h_plain)
