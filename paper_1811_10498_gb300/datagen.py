@@ -17,6 +17,7 @@ pattern ``j`` (0-based; its id is ``j + 1``) is ``blob[offsets[j]:offsets[j+1]]`
 """
 from __future__ import annotations
 
+import functools
 import hashlib
 import math
 from dataclasses import dataclass, field
@@ -66,11 +67,13 @@ def iid_text(n: int, rng: np.random.Generator, probs=UNIFORM) -> np.ndarray:
 # Order-2 Markov chain with 41 % stationary GC.
 #
 # P(x_t | x_{t-2}, x_{t-1}) is proportional to w[x_t] * m(x_{t-2}, x_{t-1}, x_t) with
-#   w = (a, c, c, a), a + c = 1/2                    (strand-symmetric composition)
+#   w = (a, c, c, a), a + c = 1/2                    (strand-symmetric base weights)
 #   m = 0.25 when x_{t-1} = C and x_t = G            (CpG depletion)
 #   m = 1.25 when x_{t-2} = x_{t-1} = x_t in {A, T}  (A/T homopolymer runs)
 #   m = 1 otherwise.
-# ``c`` is set by bisection so that the chain's stationary G+C fraction is 0.41.
+# ``c`` is set by bisection so that the chain's stationary G+C fraction is 0.41. The
+# stationary composition is then A = T = 29.5 %, C = 22.75 %, G = 18.25 %: the mass
+# taken from G after C goes to the other bases, so C and G differ.
 # ----------------------------------------------------------------------------
 
 def _markov2_matrix(c: float) -> np.ndarray:
@@ -105,7 +108,12 @@ def _gc_of(P: np.ndarray) -> float:
     return float(last[1] + last[2])
 
 
-def markov2_matrix(gc: float = 0.41) -> np.ndarray:
+@functools.lru_cache(maxsize=None)
+def _chain(gc: float):
+    """For a stationary G+C fraction ``gc``: the transition matrix (found by bisection
+    on ``c``), its sampling table (16 contexts x 65536 uniform 16-bit draws) and its
+    stationary pair distribution. Computed once per ``gc``; callers must not modify
+    the arrays."""
     lo, hi = 0.01, 0.49
     for _ in range(60):
         mid = 0.5 * (lo + hi)
@@ -113,7 +121,21 @@ def markov2_matrix(gc: float = 0.41) -> np.ndarray:
             lo = mid
         else:
             hi = mid
-    return _markov2_matrix(0.5 * (lo + hi))
+    P = _markov2_matrix(0.5 * (lo + hi))
+    cum = np.cumsum(P, axis=1)
+    cum[:, -1] = 1.0
+    lut = np.empty((16, 65536), dtype=np.uint8)
+    for ctx in range(16):
+        cuts = np.round(cum[ctx] * 65536.0).astype(np.int64)
+        lo_i = 0
+        for b, hi_i in enumerate(cuts):
+            lut[ctx, lo_i:hi_i] = b
+            lo_i = hi_i
+    return P, lut, _stationary_pairs(P)
+
+
+def markov2_matrix(gc: float = 0.41) -> np.ndarray:
+    return _chain(float(gc))[0].copy()
 
 
 def markov2_text(n: int, rng: np.random.Generator, gc: float = 0.41,
@@ -128,17 +150,7 @@ def markov2_text(n: int, rng: np.random.Generator, gc: float = 0.41,
     """
     if n == 0:
         return np.empty(0, dtype=np.uint8)
-    P = markov2_matrix(gc)
-    cum = np.cumsum(P, axis=1)
-    cum[:, -1] = 1.0
-    lut = np.empty((16, 65536), dtype=np.uint8)
-    for ctx in range(16):
-        cuts = np.round(cum[ctx] * 65536.0).astype(np.int64)
-        lo = 0
-        for b, hi in enumerate(cuts):
-            lut[ctx, lo:hi] = b
-            lo = hi
-    pairs = _stationary_pairs(P)
+    _, lut, pairs = _chain(float(gc))
     n_seg = (n + segment - 1) // segment
     out = np.empty((segment, n_seg), dtype=np.uint8)  # position-major
     first = rng.choice(16, size=n_seg, p=pairs)
