@@ -99,3 +99,45 @@ def test_launch_configuration_checks(cuda_lib_path):
     finally:
         b.pfac_destroy(h)
         b.pfac_destroy(h_plain)
+
+
+_OOM_CHILD = r"""
+import resource, sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+from paper_1811_10498_gb300 import _binding as b
+b.lib()
+rng = np.random.default_rng(0)
+n, L = 200_000, 200                     # about 40M trie states: gigabytes of tables
+blob = np.frombuffer(b"ACGT", dtype=np.uint8)[rng.integers(0, 4, n * L)]
+offs = np.arange(0, n * L + 1, L, dtype=np.int64)
+vm = next(int(l.split()[1]) * 1024 for l in open("/proc/self/status") if l.startswith("VmSize"))
+limit = vm + (400 << 20)
+resource.setrlimit(resource.RLIMIT_AS, (limit, limit))
+try:
+    b.pfac_build((blob, offs), host_only=True)
+    print("built")
+except b.PfacError as e:
+    print("code", e.code)
+h = b.pfac_build([b"ACGT", b"GATTACA"], host_only=True)      # the library still works
+print("small ok", b.pfac_info_ex(h)["n_states"])
+b.pfac_destroy(h)
+"""
+
+
+def test_build_out_of_host_memory_reports_oom(cuda_lib_path, tmp_path):
+    """A build whose tables do not fit in the memory the process may take fails with
+    PFAC_ERR_OOM and a NULL handle (the failure is made on the host: the child process
+    caps its own address space), and the library keeps working afterwards."""
+    import subprocess
+    import sys
+    if not os.path.exists("/proc/self/status"):
+        pytest.skip("needs /proc")
+    script = tmp_path / "oom_child.py"
+    script.write_text(_OOM_CHILD)
+    r = subprocess.run([sys.executable, str(script), ROOT], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = r.stdout.split("\n")
+    from paper_1811_10498_gb300 import _binding as b
+    assert f"code {b.CODE['PFAC_ERR_OOM']}" in lines, r.stdout
+    assert "small ok 12" in lines, r.stdout
