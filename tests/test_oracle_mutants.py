@@ -3,7 +3,6 @@ catch every one of them (CPU only). Mutants of the C part are built with the hos
 compiler into a temporary folder; mutants of the Python part are executed as a
 separate module whose function stands in for the oracle's during the test. Neither
 touches the real oracle."""
-import os
 import subprocess
 import types
 
