@@ -403,27 +403,37 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
             const size_t E = (size_t)1 << (2 * b);
             const uint32_t kNone = 0xFFFFFFFFu, kSpecialVal = 0xFFFFFFFEu;
             std::vector<uint32_t> val(E, kNone);      // state reached at depth b, or special
-            struct Frame { int32_t s; int32_t d; uint32_t code; bool term; };
-            std::vector<Frame> stack;
-            stack.push_back({0, 0, 0u, false});
-            while (!stack.empty()) {
-                Frame f = stack.back();
-                stack.pop_back();
-                if (f.d == b) {
-                    val[f.code] = f.term ? kSpecialVal : (uint32_t)f.s;
-                    continue;
-                }
-                for (int c = 0; c < 4; c++) {
-                    const uint32_t code = f.code | ((uint32_t)c << (2 * f.d));
-                    const uint32_t e = (uint32_t)T.rows[(size_t)(4 * (int64_t)f.s + c)];
-                    if (e) {
-                        stack.push_back({(int32_t)(e & 0x7FFFFFFFu), f.d + 1, code, f.term || (e & 0x80000000u)});
-                    } else if (f.term) {
-                        const size_t stride = (size_t)1 << (2 * (f.d + 1));
-                        for (size_t idx = code; idx < E; idx += stride) val[idx] = kSpecialVal;
+            // One pass over the states of depth <= b in id order (a parent's id is below
+            // its children's): each state carries the code of its string (first base in
+            // the low bits) and whether a pattern ends on its path, and hands both to
+            // its children. Every entry of val is written by one state or one missing
+            // edge, so the order of the writes does not matter.
+            const int32_t top = std::min(b, max_len);
+            const int64_t upto = T.level[(size_t)top + 1];
+            std::vector<uint32_t> code((size_t)upto, 0u);
+            std::vector<uint8_t> seen((size_t)upto, 0);
+            for (int32_t d = 0; d <= top; d++) {
+                for (int64_t s = T.level[(size_t)d]; s < T.level[(size_t)d + 1]; s++) {
+                    if (d == b) {
+                        val[code[(size_t)s]] = seen[(size_t)s] ? kSpecialVal : (uint32_t)s;
+                        continue;
+                    }
+                    for (int c = 0; c < 4; c++) {
+                        const uint32_t k = code[(size_t)s] | ((uint32_t)c << (2 * d));
+                        const uint32_t e = (uint32_t)T.rows[(size_t)(4 * s + c)];
+                        if (e) {
+                            const size_t child = e & 0x7FFFFFFFu;
+                            code[child] = k;
+                            seen[child] = (uint8_t)(seen[(size_t)s] | (e >> 31));
+                        } else if (seen[(size_t)s]) {
+                            const size_t stride = (size_t)1 << (2 * (d + 1));
+                            for (size_t idx = k; idx < E; idx += stride) val[idx] = kSpecialVal;
+                        }
                     }
                 }
             }
+            std::vector<uint32_t>().swap(code);
+            std::vector<uint8_t>().swap(seen);
             const size_t words = E >= 32 ? E / 32 : 1;
             T.filter.assign(words, 0u);
             std::vector<uint32_t> rank(words, 0u);
