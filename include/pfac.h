@@ -100,7 +100,8 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
  * pfac_build_file: build from a pattern file, as pfac_build_ex would from the same
  * patterns. One pattern per line (a trailing '\r' is dropped, empty lines are skipped);
  * a file whose first non-empty line starts with '>' is FASTA: the sequence lines of each
- * record, joined, make one pattern (ids follow the order in the file). Bytes are taken
+ * record, joined, make one pattern (ids follow the order in the file; a header with no
+ * sequence line is an empty pattern, PFAC_ERR_EMPTY_PATTERN). Bytes are taken
  * as they are (no case folding), so a line holding anything but A/C/G/T fails with
  * PFAC_ERR_BAD_SYMBOL. Returns NULL on error: PFAC_ERR_IO (cannot open or read),
  * PFAC_ERR_INVALID_ARG (NULL path, no pattern) or any error of pfac_build_ex. */
@@ -110,7 +111,9 @@ pfac_handle pfac_build_file(const char *path, const pfac_build_opts *opts);
  *   fasta = 0 : the bytes as they are, newlines included (a newline ends every walk
  *               that reaches it, so lines are scanned as separate reads)
  *   fasta = 1 : header lines dropped, each record's sequence lines joined, records
- *               separated by one '\n'
+ *               separated by one '\n' (a record opens at a header line, or at a
+ *               sequence line before the first header; one without sequence lines
+ *               is an empty line of the text)
  *   *len      : receives the text's length in bytes; min(*len, cap) bytes go to buf
  *               (buf may be NULL when cap = 0: a first call that only sizes the text).
  * Returns PFAC_OK, PFAC_ERR_INVALID_ARG, PFAC_ERR_IO or PFAC_ERR_OOM. */
