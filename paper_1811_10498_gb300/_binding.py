@@ -304,9 +304,17 @@ class Table:
         return t
 
     def close(self):
+        """Destroy the handle (no launch using it may still be in flight); a second call
+        does nothing, and calls on a closed table raise PfacError."""
         h, self.h = getattr(self, "h", None), None
         if h:
             lib().pfac_destroy(h)
+
+    def __enter__(self) -> "Table":
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:

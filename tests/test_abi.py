@@ -141,3 +141,20 @@ def test_build_out_of_host_memory_reports_oom(cuda_lib_path, tmp_path):
     from paper_1811_10498_gb300 import _binding as b
     assert f"code {b.CODE['PFAC_ERR_OOM']}" in lines, r.stdout
     assert "small ok 12" in lines, r.stdout
+
+
+def test_table_lifecycle(cuda_lib_path, tmp_path):
+    """Table owns its handle: a context manager closes it, close() twice is harmless, and
+    a closed table raises instead of passing a stale handle to the library."""
+    from paper_1811_10498_gb300 import _binding as b
+    with b.Table([b"ACGT", b"GATTACA"], host_only=True) as t:
+        assert t.info["n_patterns"] == 2
+    assert t.h is None
+    t.close()
+    with pytest.raises(b.PfacError) as e:
+        t.info
+    assert e.value.code == b.CODE["PFAC_ERR_INVALID_ARG"]
+    f = tmp_path / "p.txt"
+    f.write_bytes(b"ACGT\nGATTACA\n")
+    with b.Table.from_file(str(f), host_only=True) as t2:
+        assert t2.info["n_states"] == 12
