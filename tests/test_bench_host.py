@@ -51,3 +51,28 @@ def test_clock_summary_counts_samples_under_load_only():
 def test_clock_summary_without_samples():
     got = bench.ClockSampler(0).summary()
     assert got == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples_under_load": 0}
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the CPU oracle alone) prints one JSON line with the
+    fields of the benchmark contract, its CPU baseline and an end-to-end object with no
+    host-device traffic."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                        "--n-bases", str(1 << 20), "--steps", "3", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 3 and d["warmup"] == 3 and d["value"] > 0
+    assert d["unit"] == bench.UNIT and d["higher_is_better"] is True
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["n_bases"] == 1 << 20 and len(d["config"]["inputs"]["text_sha256"]) == 64
