@@ -158,3 +158,23 @@ def test_table_lifecycle(cuda_lib_path, tmp_path):
     f.write_bytes(b"ACGT\nGATTACA\n")
     with b.Table.from_file(str(f), host_only=True) as t2:
         assert t2.info["n_states"] == 12
+
+
+def test_plain_c_client(cuda_lib_path, tmp_path):
+    """The header compiles as strict C99, and a C program linked against the library
+    builds, exports and destroys host-only tables and reads its error codes, with no
+    Python in between (tests/native/c_client.c)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no host C compiler")
+    exe = tmp_path / "c_client"
+    libdir = os.path.dirname(cuda_lib_path)
+    lib = os.path.basename(cuda_lib_path)
+    assert lib.startswith("lib") and lib.endswith(".so")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I" + os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "native", "c_client.c"), f"-L{libdir}", f"-l{lib[3:-3]}",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip().endswith("c_client: ok")
