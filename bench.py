@@ -49,22 +49,25 @@ def measured_hbm():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms in the background."""
+    """nvidia-smi clocks and throttle reasons, sampled every `interval_ms` (default 50)
+    in the background from start() to stop(); each sample carries its host time, so the
+    samples inside a window (the timed steps) can be picked out."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 50):
         self.gpu = gpu_index
+        self.interval_ms = interval_ms
         self.proc = None
-        self.lines = []
+        self.lines = []          # (host time, csv line)
 
-    def __enter__(self):
+    def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -73,20 +76,32 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def __exit__(self, *a):
+    def stop(self):
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+            self.proc = None
 
-    def summary(self):
+    def __enter__(self):
+        return self.start()
+
+    def __exit__(self, *a):
+        self.stop()
+
+    def summary(self, t0: float | None = None, t1: float | None = None):
+        """Median SM clock over the samples taken under load (GPU utilisation > 0),
+        between host times t0 and t1 when given, and every throttle reason seen active
+        in them."""
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for ts, line in list(self.lines):
+            if (t0 is not None and ts < t0) or (t1 is not None and ts > t1):
+                continue
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 10:
                 continue
@@ -197,7 +212,7 @@ def batched_measure(steps: int):
     import torch
     from paper_1811_10498_gb300 import _binding as b
     from paper_1811_10498_gb300 import datagen
-    from paper_1811_10498_gb300.batched import BatchedScanner, scan_per_read
+    from paper_1811_10498_gb300.batched import BatchedScanner, PerReadGraph, scan_per_read
     w = datagen.read_batch(seed=4)
     t0 = time.perf_counter()
     tables = [b.Table(s) for s in w.sets]
@@ -224,26 +239,46 @@ def batched_measure(steps: int):
     batched_out = sc.out[:n].clone()
     ms = statistics.median(times)
     d_text = sc.texts[:n]
+    # the baseline as device work: one pfac_match per read, captured in one CUDA graph
     out = torch.zeros(n, dtype=torch.int32, device="cuda")
-    scan_per_read(tables, d_text, w.read_offsets, w.read_set, out)      # warm-up
+    pg = PerReadGraph(tables, d_text, w.read_offsets, w.read_set, out)
+    for _ in range(2):
+        pg.run()
+    torch.cuda.synchronize()
+    per_times = []
+    for _ in range(max(3, steps // 4)):
+        with torch.cuda.stream(pg.stream):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(pg.stream)
+        pg.run()
+        with torch.cuda.stream(pg.stream):
+            e1.record(pg.stream)
+        e1.synchronize()
+        per_times.append(e0.elapsed_time(e1))
+    per_ms = statistics.median(per_times)
+    same = bool(torch.equal(out, batched_out))
+    # and as a host loop issuing the same calls one by one (context: host cost per call)
+    out2 = torch.zeros(n, dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    scan_per_read(tables, d_text, w.read_offsets, w.read_set, out)
-    e1.record()
+    scan_per_read(tables, d_text, w.read_offsets, w.read_set, out2)
     torch.cuda.synchronize()
-    per_ms = e0.elapsed_time(e1)
-    same = bool(torch.equal(out, batched_out))
+    loop_ms = 1e3 * (time.perf_counter() - t0)
+    same = same and bool(torch.equal(out2, batched_out))
     for t in tables:
         t.close()
     return {"workload": w.name, "bases": n, "reads": int(len(w.read_set)), "tables": len(w.sets),
             "table_build_s": build_s, "graph_replay_ms": ms, "gbases_s": n / ms / 1e6,
-            "per_read_launches_ms": per_ms, "per_read_gbases_s": n / per_ms / 1e6,
-            "batched_vs_per_read": per_ms / ms, "same_output": same,
+            "per_read_graph_ms": per_ms, "per_read_gbases_s": n / per_ms / 1e6,
+            "batched_vs_per_read": per_ms / ms,
+            "per_read_host_loop_ms": loop_ms, "batched_vs_per_read_host_loop": loop_ms / ms,
+            "same_output": same,
             "autotune": {k: tuned.get(k) for k in ("lane_offsets", "threads", "ctas_per_sm", "walk_loads",
                                                    "ms", "default_ms", "candidates")},
-            "launches_per_batch": 4, "launches_per_read_pass": 2 * int(len(w.read_set))}
+            "launches_per_batch": 4, "launches_per_read_pass": pg.launches,
+            "per_read_baseline": "one pfac_match (scan + tail kernel) per read, all captured in one CUDA graph "
+                                 "and replayed; L2 flushed before each replay"}
 
 
 def large_dict_measure(steps: int):
@@ -304,10 +339,18 @@ def large_dict_measure(steps: int):
 
 def serving_measure(seconds: float):
     """The serving workload: Poisson arrivals at 2,000 requests/s, 16 resident tables of
-    1,000-200,000 patterns, texts of 1 kb-10 Mb; p50/p99 latency and throughput."""
+    1,000-200,000 patterns, texts of 1 kb-10 Mb.
+
+    * served: the continuous-batching server on the stream in real time (p50/p99
+      latency, Gbases/s; at this offered load it keeps up, so its Gbases/s is the
+      offered load);
+    * per_request: the same stream in real time served one request at a time with one
+      pfac_match launch each (serving.serve_per_request);
+    * capacity: both again with every request arriving at time 0 (saturation): the
+      Gbases/s each can serve, and their ratio."""
     from paper_1811_10498_gb300 import _binding as b
     from paper_1811_10498_gb300 import datagen
-    from paper_1811_10498_gb300.serving import Server, requests_from_stream
+    from paper_1811_10498_gb300.serving import Server, requests_from_stream, serve_per_request
     st = datagen.request_stream(seed=5, duration=seconds)
     tables = [b.Table(s) for s in st.sets]
     srv = Server(tables, slot_bases=1 << 24, n_slots=3, max_reads=4096)
@@ -315,6 +358,17 @@ def serving_measure(seconds: float):
     _, _, stats = srv.run(reqs, realtime=True)
     stats["workload"] = st.name
     stats["offered_gbases_s"] = stats["bases"] / seconds / 1e9
+    _, _, per = serve_per_request(tables, reqs, realtime=True)
+    _, _, cap = srv.run(reqs, realtime=False)
+    _, _, per_cap = serve_per_request(tables, reqs, realtime=False)
+    stats["per_request"] = {k: per[k] for k in ("gbases_s", "p50_ms", "p99_ms", "wall_s", "launches")}
+    stats["capacity"] = {"all_requests_at_t0": True, "batched": {k: cap[k] for k in
+                                                                 ("gbases_s", "p50_ms", "p99_ms", "wall_s",
+                                                                  "batches")},
+                         "per_request": {k: per_cap[k] for k in ("gbases_s", "p50_ms", "p99_ms", "wall_s")}}
+    stats["capacity_gbases_s"] = cap["gbases_s"]
+    stats["per_request_gbases_s"] = per_cap["gbases_s"]
+    stats["served_vs_per_request"] = cap["gbases_s"] / per_cap["gbases_s"] if per_cap["gbases_s"] else None
     for t in tables:
         t.close()
     return stats
@@ -325,15 +379,17 @@ def paper_suite(args):
     input data sets of 0.75-3.75 M newline-separated 100-base lines (Table IV) and
     pattern sets of 1,000-5,000 100-base patterns (Table III), scanned as ASCII.
 
-    * placement: the GB300 analogues of the memory placements of Figs. 6-8 on input set
-      5 for every pattern set: one thread per offset over 16-byte rows with text and
-      table in global memory (kernel 1, the paper's kernel structure); the pipelined
-      kernel with the text staged in shared memory and the prefix filter in shared memory
-      but its rank index in global memory; the same with both in shared memory (the
-      default); and the same with the skip entries pinned in L2 by an access-policy
-      window (the texture-cache analogue);
-    * patterns: Fig. 9's sweep (pattern sets 1-5 on input set 5), kernel 1 vs default;
-    * inputs: Fig. 10's sweep (input sets 1-5 with pattern set 5), kernel 1 vs default.
+    * placement (Figs. 6-8) on input set 5 for every pattern set: the paper's kernel
+      structure (one thread per offset, kernel 1) with the transition table as its two
+      arrays (nextState, matchedPatternId) or merged into one array of pairs, the text in
+      global memory or staged per block in shared memory, table loads through the
+      default L1-cached path, the read-only (texture) path, or with L1 bypassed (the
+      paper's L1-off setting); kernel 1 over 16-byte rows; and this design's pipelined
+      kernel (prefix filter in shared memory, rank index in shared or global memory, an
+      L2 access-policy window on the skip entries);
+    * patterns: Fig. 9's sweep (pattern sets 1-5 on input set 5), the same points;
+    * inputs: Fig. 10's sweep (input sets 1-5 with pattern set 5), the paper's best
+      placement (one array, text in shared memory, texture path) vs this design.
     Prints one JSON line per point: median kernel time over the timed launches (L2
     flushed before each), Gbases/s counting every input byte as an offset, and the HBM
     roofline fraction at 5 bytes per offset (1 in, 4 out)."""
@@ -354,12 +410,25 @@ def paper_suite(args):
             texts[n_lines] = torch.from_numpy(datagen.paper_input(src, n_lines)).cuda()
         return texts[n_lines]
 
+    # Fig. 6: {two arrays, one merged array} x {GM only, GM + text in SM, GM + SM + table
+    # through the texture path}; Figs. 7-8: L1 on (default global loads) vs L1 bypassed;
+    # then this design's kernel 1 (16-byte rows) and kernel 2 placements.
     placements = {
+        "GM, two arrays": dict(kernel=1, table_layout=1, row_loads=1, text_smem=0),
+        "GM+SM, two arrays": dict(kernel=1, table_layout=1, row_loads=1, text_smem=1),
+        "GM+SM+Tex, two arrays": dict(kernel=1, table_layout=1, row_loads=0, text_smem=1),
+        "GM, one array": dict(kernel=1, table_layout=2, row_loads=1, text_smem=0),
+        "GM+SM, one array": dict(kernel=1, table_layout=2, row_loads=1, text_smem=1),
+        "GM+SM+Tex, one array": dict(kernel=1, table_layout=2, row_loads=0, text_smem=1),
+        "GM+SM, two arrays, L1 off": dict(kernel=1, table_layout=1, row_loads=2, text_smem=1),
+        "GM+SM, one array, L1 off": dict(kernel=1, table_layout=2, row_loads=2, text_smem=1),
         "global (kernel 1)": dict(kernel=1),
         "smem text + smem filter, rank in global": dict(kernel=2, rank_in_smem=-1),
         "smem text + smem filter and rank (default)": dict(kernel=0),
         "default + L2 window on skip entries": dict(kernel=2, l2_persist=1),
     }
+
+    ref_ids = {}
 
     def point(fig, n_lines, n_p, label, cfg):
         d_text = text(n_lines)
@@ -370,6 +439,11 @@ def paper_suite(args):
         for _ in range(3):
             t.match(d_text, out)
         torch.cuda.synchronize()
+        # every placement must give the same ids as the first one timed on this input
+        key = (n_lines, n_p)
+        if key not in ref_ids:
+            ref_ids[key] = out.clone()
+        same = bool(torch.equal(out, ref_ids[key]))
         ts = []
         for _ in range(min(args.steps, 20)):
             flush.zero_()
@@ -384,7 +458,8 @@ def paper_suite(args):
         line = {"suite": "paper", "figure": fig, "input_lines": n_lines, "input_bytes": n, "patterns": n_p,
                 "placement": label, "config": b.pfac_get_config(t.h, n), "ms": ms, "gbases_s": n / ms / 1e6,
                 "roofline_frac": 5.0 * n / (ms * 1e-3) / (peak * 1e9), "peak_gbs": peak, "peak_source": peak_kind,
-                "matches": int((out != 0).sum().item()), "filter_b": t.info["filter_b"], "states": t.info["n_states"]}
+                "matches": int((out != 0).sum().item()), "filter_b": t.info["filter_b"], "states": t.info["n_states"],
+                "same_ids_as_first_placement": same}
         print(json.dumps(line), flush=True)
         b.pfac_set_config(t.h, None)
         t.close()
@@ -393,7 +468,7 @@ def paper_suite(args):
         for label, cfg in placements.items():
             point("6-9", lines[-1], n_p, label, cfg)
     for n_l in lines[:-1]:                             # Fig. 10 (input set 5 is above)
-        for label in ("global (kernel 1)", "smem text + smem filter and rank (default)"):
+        for label in ("GM+SM+Tex, one array", "smem text + smem filter and rank (default)"):
             point("10", n_l, n_pats[-1], label, placements[label])
 
     # the paper's host program from files (Figs. 4-5): pattern set 5 and input set 5 written
@@ -563,24 +638,35 @@ def main():
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(local) as clocks:      # samples the warm-up and the timed steps
-        for _ in range(args.warmup):
-            flush.zero_()
-            step()
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        wall0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()                      # L2 flushed between timed steps (outside the events)
-            starts[i].record(stream)
-            step()
-            ends[i].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
-        if world > 1:
-            dist.barrier()
+    # clocks sampled every 50 ms from here to the end of the run (the timed steps, then
+    # the other legs, all of them GPU load)
+    clocks = ClockSampler(local, interval_ms=50).start()
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                      # L2 flushed between timed steps (outside the events)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter()
+    wall = wall1 - wall0
+    if world > 1:
+        dist.barrier()
+    # a bounded wait that ran out inside a timed step would leave ids unwritten: the
+    # run is void unless every kernel of the timed steps reported PFAC_OK
+    device_status = b.pfac_device_status(table.h, stream)
+    if device_status != 0:
+        clocks.stop()
+        print(f"bench: device status {device_status} ({b.lib().pfac_error_string(device_status).decode()}) "
+              "after the timed steps; no result", file=sys.stderr, flush=True)
+        sys.exit(3)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_s, value = job_throughput(sum(step_ms) * 1e-3, n, args.steps, world, dev)
     ms_per_step = 1e3 * total_s / args.steps
@@ -637,7 +723,8 @@ def main():
                        "inputs": {"seed": 2 + rank, "text_sha256": datagen.sha256(w.text),
                                   "patterns_sha256": datagen.sha256(w.blob)}},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
-            "clocks": clocks.summary(),
+            "device_status": device_status,
+            "clocks": None,
             "wall_s_timed_region": wall,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "autotune": {k: tuned.get(k) for k in ("lane_offsets", "threads", "stages", "walk_loads",
@@ -652,7 +739,13 @@ def main():
             line["batched"] = batched_measure(20)
         if not args.no_serving:
             line["serving"] = serving_measure(args.serve_seconds)
+        clocks.stop()
+        line["clocks"] = clocks.summary()
+        line["clocks"]["timed_region"] = clocks.summary(wall0, wall1)
+        line["clocks"]["sampled"] = "every 50 ms from the warm-up to the end of the run (all legs)"
         print(json.dumps(line), flush=True)
+    else:
+        clocks.stop()
     table.close()
     if world > 1:
         dist.destroy_process_group()

@@ -206,10 +206,32 @@ typedef struct {
     int32_t lane_offsets;    /* kernel 2: consecutive offsets per consumer lane, 16 or 32
                                 (0 = 32 for packed text, 16 for ASCII and batched passes);
                                 a tile is 32 x lane_offsets bases per consumer warp */
+    /* Kernel 1, dense ids: the paper's memory-placement experiments (Section V-C;
+     * Section VII, Figs. 6-8). Ignored by kernel 2 and by the match-list calls. */
+    int32_t table_layout;    /* 0 = 16-byte rows (next state with a terminal flag) and ids by
+                                state; 1 = the paper's two arrays, nextState[4 x states] and
+                                matchedPatternId[4 x states] (the id of the pattern that ends
+                                on the state an edge leads to); 2 = the two merged into one
+                                array of (nextState, matchedPatternId) pairs, 8 bytes per
+                                edge. Layouts 1 and 2 are derived on the device from the
+                                rows by the pfac_set_config call that first asks for them
+                                (one device allocation of 32 bytes per state, kept until
+                                pfac_destroy; the call synchronises the device) */
+    int32_t row_loads;       /* 0 = table loads through the read-only (texture) data path,
+                                1 = default global loads, cached in L1, 2 = L1 bypassed
+                                (loads cached in L2 only: the paper's L1-off setting) */
+    int32_t text_smem;       /* 1 = each 256-thread block first copies its text (its 256
+                                offsets plus max_len - 1 bases) into shared memory and
+                                walks from there; tables whose tile would exceed 48 KB fall
+                                back to reading the text from global memory */
+    int32_t reserved;        /* 0 */
 } pfac_config;
 
 /* Set (cfg != NULL) or reset (cfg == NULL) the launch configuration of a handle.
- * Takes effect for launches issued afterwards. */
+ * Takes effect for launches issued afterwards. Out-of-range fields give
+ * PFAC_ERR_INVALID_ARG and leave the previous configuration in place; asking for
+ * table_layout 1 or 2 on a handle with a device copy builds that layout first (device
+ * memory; PFAC_ERR_OOM or PFAC_ERR_CUDA if that fails). */
 int pfac_set_config(pfac_handle h, const pfac_config *cfg);
 /* The configuration the next packed-text launch on `n_bases` bases would use (an ASCII
  * launch differs only where the set configuration leaves stages or lane_offsets at 0:
@@ -240,10 +262,12 @@ int pfac_match_packed(pfac_handle h, const uint32_t *d_packed, int64_t n_bases,
 
 /* Match list instead of a dense array: for every offset i with a non-zero id,
  * one (d_offsets[k], d_ids[k]) pair, k < capacity, in no particular order.
- * *d_count receives the total number of matches (which may exceed capacity; then
- * only `capacity` pairs are written, which ones is unspecified, and the caller sees
- * the overflow by comparing *d_count with capacity after synchronising).
- * d_count is reset by the call itself (stream-ordered). */
+ * *d_count receives the total number of matches. When that exceeds capacity, only
+ * `capacity` pairs are written (which ones is unspecified), and the kernel records
+ * PFAC_ERR_OVERFLOW in the handle's device status word: pfac_device_status() returns
+ * it after the launch (the call itself is asynchronous, so its return value cannot).
+ * d_count is reset by the call itself (stream-ordered). Lanes of a warp that find
+ * matches together take their places in the list with one atomic add. */
 int pfac_match_compact(pfac_handle h, const uint32_t *d_packed, int64_t n_bases,
                        int64_t *d_offsets, int32_t *d_ids, int64_t capacity,
                        int64_t *d_count, void *stream);
@@ -290,8 +314,9 @@ int pfac_match_batched(const pfac_handle *sets, int32_t n_sets, const uint8_t *d
                        int32_t n_reads, int32_t *d_out_ids, void *stream);
 
 /* Read (and clear) the device status word of a handle: PFAC_OK or the first error a
- * kernel recorded (for example PFAC_ERR_TIMEOUT from a bounded wait). Synchronises
- * `stream`. */
+ * kernel recorded since the last read (PFAC_ERR_TIMEOUT from a bounded wait,
+ * PFAC_ERR_OVERFLOW from a match list that ran out of capacity, PFAC_ERR_INVALID_ARG
+ * from a batched read naming a table that does not exist). Synchronises `stream`. */
 int pfac_device_status(pfac_handle h, int32_t *status, void *stream);
 
 /* ---------------------------------------------------------------------------

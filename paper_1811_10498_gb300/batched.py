@@ -102,3 +102,28 @@ def scan_per_read(tables, d_texts, read_offsets, read_set, d_out, stream=None):
         lo, hi = int(read_offsets[r]), int(read_offsets[r + 1])
         if hi > lo:
             b.pfac_match(tables[int(read_set[r])].h, d_texts[lo:hi], d_out[lo:hi], stream)
+
+
+class PerReadGraph:
+    """The per-read baseline as device work alone: the pfac_match launches of
+    ``scan_per_read`` (one per read, each a scan and a tail kernel), captured once into
+    a CUDA graph on one stream and replayed, so that timing a replay measures the
+    launches on the GPU without the host's cost of issuing them one by one."""
+
+    def __init__(self, tables, d_texts, read_offsets, read_set, d_out):
+        import torch
+        self.torch = torch
+        self.stream = torch.cuda.Stream()
+        args = (tables, d_texts, read_offsets, read_set, d_out)
+        # first launches on the stream: the library allocates its per-stream scratch
+        with torch.cuda.stream(self.stream):
+            scan_per_read(*args, stream=self.stream)
+        self.stream.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            scan_per_read(*args, stream=self.stream)
+        self.launches = 2 * sum(1 for r in range(len(read_set)) if read_offsets[r + 1] > read_offsets[r])
+
+    def run(self):
+        with self.torch.cuda.stream(self.stream):
+            self.graph.replay()

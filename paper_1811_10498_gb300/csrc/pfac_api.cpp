@@ -26,6 +26,11 @@ struct pfac_table {
     std::mutex mu;
     bool cfg_set = false;
     pfac_config cfg{};
+    // the paper's table layouts, derived on the device when a configuration asks for
+    // them: two arrays (next, pid) and merged pairs
+    void *paper_two = nullptr;
+    void *paper_pair = nullptr;
+    pfac::PaperTables paper{};
 };
 
 namespace {
@@ -276,11 +281,78 @@ int run_scan(pfac_handle h, const void *text, bool packed, int64_t n, int32_t *o
         else if (rc != PFAC_OK) return rc == PFAC_ERR_CUDA ? cuda_fail(cudaGetLastError()) : fail(rc);
     }
     if (!tiled) {
-        rc = pfac::launch_walk_rows_any(h->dt, text, packed, n, out, c_off, c_ids, cap, (unsigned long long *)count,
-                                        st, dp, all_matches);
+        if (!compact) {
+            // dense ids: the one-thread-per-offset kernel with the handle's placement
+            pfac::PaperConfig pc{c.table_layout, c.row_loads, c.text_smem};
+            pfac::PaperTables pt{};
+            {
+                std::lock_guard<std::mutex> lk(h->mu);
+                pt = h->paper;
+            }
+            rc = pfac::launch_paper_walk(h->dt, pt, pc, text, packed, n, out, st, dp);
+            if (rc == PFAC_ERR_UNSUPPORTED && pc.text_smem) {   // tile above 48 KB: text from global memory
+                pc.text_smem = 0;
+                rc = pfac::launch_paper_walk(h->dt, pt, pc, text, packed, n, out, st, dp);
+            }
+        } else {
+            rc = pfac::launch_walk_rows_any(h->dt, text, packed, n, out, c_off, c_ids, cap,
+                                            (unsigned long long *)count, st, dp, all_matches);
+        }
         if (rc != PFAC_OK) return rc == PFAC_ERR_CUDA ? cuda_fail(cudaGetLastError()) : fail(rc);
     }
     return PFAC_OK;
+}
+
+// Derive the paper's layout `layout` (1 = two arrays, 2 = merged pairs) on the handle's
+// device, once; synchronous.
+int ensure_paper_layout(pfac_handle h, int layout)
+{
+    if (layout == 0 || h->device < 0) return PFAC_OK;
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        if ((layout == 1 && h->paper_two) || (layout == 2 && h->paper_pair)) return PFAC_OK;
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != h->device) cudaSetDevice(h->device);
+    const size_t bytes = (size_t)h->dt.n_states * 32;    // 4 cells x 8 bytes
+    void *m = nullptr;
+    cudaError_t e = cudaMalloc(&m, bytes);
+    int rc = PFAC_OK;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(e == cudaErrorMemoryAllocation ? PFAC_ERR_OOM : PFAC_ERR_CUDA);
+    } else {
+        int32_t *next = layout == 1 ? (int32_t *)m : nullptr;
+        int32_t *pid = layout == 1 ? (int32_t *)m + 4 * h->dt.n_states : nullptr;
+        int2 *pair = layout == 2 ? (int2 *)m : nullptr;
+        rc = pfac::derive_paper_tables(h->dt, next, pid, pair, nullptr);
+        if (rc == PFAC_OK) {
+            e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) rc = cuda_fail(e);
+        } else {
+            rc = cuda_fail(cudaGetLastError());
+        }
+        if (rc != PFAC_OK) {
+            cudaFree(m);
+        } else {
+            std::lock_guard<std::mutex> lk(h->mu);
+            void *&slot = layout == 1 ? h->paper_two : h->paper_pair;
+            if (slot) {
+                cudaFree(m);                       // another thread got there first
+            } else {
+                slot = m;
+                if (layout == 1) {
+                    h->paper.next = next;
+                    h->paper.pid = pid;
+                } else {
+                    h->paper.pair = pair;
+                }
+            }
+        }
+    }
+    if (cur != h->device) cudaSetDevice(cur);
+    return rc;
 }
 
 }  // namespace
@@ -431,6 +503,8 @@ int pfac_destroy(pfac_handle h)
         int cur = 0;
         cudaGetDevice(&cur);
         if (cur != h->device) cudaSetDevice(h->device);
+        if (h->paper_two) cudaFree(h->paper_two);
+        if (h->paper_pair) cudaFree(h->paper_pair);
         cudaError_t e = cudaFree(h->dmem);
         if (cur != h->device) cudaSetDevice(cur);
         if (e != cudaSuccess) rc = cuda_fail(e);
@@ -502,9 +576,13 @@ int pfac_set_config(pfac_handle h, const pfac_config *cfg)
         if (cfg->kernel < 0 || cfg->kernel > 2 || cfg->threads < 0 || (cfg->threads & 31) || cfg->threads > 1024 ||
             (cfg->threads > 0 && cfg->threads < 64) || cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32 ||
             cfg->stages < 0 || cfg->stages == 1 || cfg->stages > 8 || cfg->walk_loads < 0 ||
-            (cfg->lane_offsets != 0 && cfg->lane_offsets != 16 && cfg->lane_offsets != 32))
+            (cfg->lane_offsets != 0 && cfg->lane_offsets != 16 && cfg->lane_offsets != 32) ||
+            cfg->table_layout < 0 || cfg->table_layout > 2 || cfg->row_loads < 0 || cfg->row_loads > 2 ||
+            cfg->text_smem < 0 || cfg->text_smem > 1 || cfg->reserved != 0)
             return fail(PFAC_ERR_INVALID_ARG);
         if (cfg->kernel == 2 && !(h->skip_bytes > 0 && h->host.filter_b > 0)) return fail(PFAC_ERR_UNSUPPORTED);
+        const int rc = ensure_paper_layout(h, cfg->table_layout);
+        if (rc != PFAC_OK) return rc;
     }
     std::lock_guard<std::mutex> lk(h->mu);
     h->cfg_set = cfg != nullptr;

@@ -8,6 +8,8 @@
 
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 #include "../../include/pfac.h"
 #include "pfac_internal.h"
 
@@ -256,18 +258,36 @@ struct Sink {
     DeferItem *defer;
     int64_t defer_cap;
     unsigned long long *defer_count;
+    int32_t *status;           // device status word: PFAC_ERR_OVERFLOW when the list is full
 };
 
-// Record a non-zero result.
+// Places for the lanes that reach this call together (any subset of the warp): one
+// atomicAdd on *counter for all of them (ballot of the active lanes, popcount, the
+// leader's add, a shuffle of the base), then the lanes' ranks among them. Returns this
+// lane's place.
+__device__ __forceinline__ unsigned long long warp_aggregated_slot(unsigned long long *counter)
+{
+    namespace cg = cooperative_groups;
+    const cg::coalesced_group g = cg::coalesced_threads();
+    unsigned long long base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(counter, (unsigned long long)g.size());
+    return g.shfl(base, 0) + g.thread_rank();
+}
+
+// Record a non-zero result. In the match list the lanes that find matches together take
+// their places with one atomic; a match past the capacity is counted but not written,
+// and PFAC_ERR_OVERFLOW goes to the status word.
 template <bool COMPACT>
 __device__ __forceinline__ void emit_match(const Sink &K, int64_t gp, int32_t v)
 {
     if (!v) return;
     if (COMPACT) {
-        const unsigned long long k = atomicAdd(K.count, 1ull);
+        const unsigned long long k = warp_aggregated_slot(K.count);
         if ((int64_t)k < K.cap) {
             K.c_off[k] = gp;
             K.c_ids[k] = v;
+        } else {
+            record_error(K.status, PFAC_ERR_OVERFLOW);
         }
     } else {
         K.out[gp] = v;
@@ -464,7 +484,7 @@ __device__ __forceinline__ void walk_item(const DeviceTable &T, const Sink &K, c
     }
     if (defer) {
         // long walk: finish it in the tail kernel (or here if the list is full)
-        const unsigned long long di = atomicAdd(K.defer_count, 1ull);
+        const unsigned long long di = warp_aggregated_slot(K.defer_count);
         if ((int64_t)di < K.defer_cap) {
             DeferItem it;
             it.gp = gp;

@@ -165,6 +165,40 @@ int launch_walk_rows_any(const DeviceTable &t, const void *text, bool packed, in
                          unsigned long long *count, cudaStream_t st, const DeviceProps &dp,
                          bool all_matches = false);
 
+// The paper's transition-table layouts (Section V-B: the kernel reads the arrays
+// nextState and matchedPatternId with a pitch of four; Section VII: "array merge"
+// interleaves them), derived on the device from the 16-byte rows:
+//   next[4s + c] = the state reached from s on base c (0 = no edge)
+//   pid[4s + c]  = the id of the pattern that ends on that state (0 = none)
+//   pair[4s + c] = (next[4s + c], pid[4s + c]) in one 8-byte element
+struct PaperTables {
+    const int32_t *next;
+    const int32_t *pid;
+    const int2 *pair;
+};
+
+// Launch options of the one-thread-per-offset kernel (the paper's kernel structure):
+//   layout    0 = 16-byte rows with the terminal flag, ids by state; 1 = two arrays;
+//             2 = merged pairs
+//   loads     0 = read-only data path (ld.global.nc, the texture path); 1 = default
+//             global loads (ld.global.ca, cached in L1); 2 = L1 bypassed (ld.global.cg)
+//   text_smem 1 = each block stages its text (its 256 offsets plus max_len - 1 bases)
+//             in shared memory and walks from there
+struct PaperConfig {
+    int32_t layout;
+    int32_t loads;
+    int32_t text_smem;
+};
+
+// Dense ids with the kernel above. PFAC_ERR_UNSUPPORTED when the layout's arrays are
+// missing or the shared-memory tile would exceed 48 KB.
+int launch_paper_walk(const DeviceTable &t, const PaperTables &pt, const PaperConfig &pc, const void *text,
+                      bool packed, int64_t n, int32_t *out, cudaStream_t st, const DeviceProps &dp);
+
+// Fill the two-array layout (next, pid: 4 * n_states each) and/or the merged layout
+// (pair: 4 * n_states) from the rows and ids of `t`; either output may be null.
+int derive_paper_tables(const DeviceTable &t, int32_t *next, int32_t *pid, int2 *pair, cudaStream_t st);
+
 // Kernel 2 (and its tail kernel). Dense output when c_off == nullptr, otherwise the
 // compacted match list.
 int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n, int32_t *out,

@@ -21,7 +21,9 @@
 
 #include <algorithm>
 #include <mutex>
+#include <set>
 #include <type_traits>
+#include <utility>
 
 #include "../../include/pfac.h"
 #include "pfac_internal.h"
@@ -131,10 +133,12 @@ __global__ void __launch_bounds__(256) walk_rows_kernel(DeviceTable t, const voi
                 s = e & 0x7FFFFFFF;
                 if (e < 0) {
                     if (ALL) {
-                        const unsigned long long kk = atomicAdd(count, 1ull);
+                        const unsigned long long kk = warp_aggregated_slot(count);
                         if ((int64_t)kk < cap) {
                             c_off[kk] = i;
                             c_ids[kk] = __ldg(t.out_id + s);
+                        } else {
+                            record_error(t.status, PFAC_ERR_OVERFLOW);
                         }
                     } else {
                         best = s;
@@ -154,6 +158,7 @@ __global__ void __launch_bounds__(256) walk_rows_kernel(DeviceTable t, const voi
                 if (res) {
                     const int64_t k = (int64_t)b + __popc(m & ((1u << lane) - 1));
                     if (k < cap) { c_off[k] = i; c_ids[k] = res; }
+                    else record_error(t.status, PFAC_ERR_OVERFLOW);
                 }
             }
         }
@@ -183,6 +188,165 @@ int launch_walk_rows_any(const DeviceTable &t, const void *text, bool packed, in
     return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
 }
 
+
+// ---------------------------------------------------------------------------
+// The paper's memory-placement experiments (Section V-C; Section VII, Figs. 6-8) on the
+// one-thread-per-offset kernel: the transition table as two arrays (nextState and
+// matchedPatternId, a pitch of four) or merged into one array of pairs; table loads
+// through the read-only (texture) path, the default L1-cached path, or with L1 bypassed
+// (the paper's L1-off configuration); text read from global memory or first staged per
+// block in shared memory. Dense ids, the longest pattern per offset as everywhere else.
+// ---------------------------------------------------------------------------
+
+template <int LOADS>
+__device__ __forceinline__ int32_t ld_table(const int32_t *p)
+{
+    if (LOADS == 0) return __ldg(p);
+    if (LOADS == 1) return __ldca(p);
+    return __ldcg(p);
+}
+
+template <int LOADS>
+__device__ __forceinline__ int2 ld_table(const int2 *p)
+{
+    if (LOADS == 0) return __ldg(p);
+    if (LOADS == 1) return __ldca(p);
+    return __ldcg(p);
+}
+
+constexpr int kPaperBlock = 256;          // threads per block, as in the paper's kernel
+
+template <bool PACKED, int LAYOUT, int LOADS, bool TSMEM>
+__global__ void __launch_bounds__(kPaperBlock) paper_walk_kernel(DeviceTable t, PaperTables pt,
+                                                                 const void *__restrict__ text, int64_t n,
+                                                                 int32_t *__restrict__ out)
+{
+    extern __shared__ __align__(16) uint8_t tile[];
+    const int64_t stride = (int64_t)gridDim.x * kPaperBlock;
+    const int max_len = t.max_len;
+    for (int64_t i0 = (int64_t)blockIdx.x * kPaperBlock; i0 < n; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        // the block's text: its offsets plus the longest walk's reach past the last one
+        const int64_t tile_end = min(n, i0 + kPaperBlock + max_len - 1);
+        if (TSMEM) {
+            __syncthreads();                 // the previous tile's readers are done
+            if (PACKED) {
+                const uint32_t *src = (const uint32_t *)text + (i0 >> 4);
+                uint32_t *dst = reinterpret_cast<uint32_t *>(tile);
+                const int64_t words = ((tile_end + 15) >> 4) - (i0 >> 4);
+                for (int64_t k = threadIdx.x; k < words; k += kPaperBlock) dst[k] = __ldg(src + k);
+            } else {
+                const uint8_t *src = (const uint8_t *)text + i0;
+                for (int64_t k = threadIdx.x; k < tile_end - i0; k += kPaperBlock) tile[k] = __ldg(src + k);
+            }
+            __syncthreads();
+        }
+        if (i < n) {
+            int32_t s = 0, best = 0;
+            const int64_t end = min(n, i + (int64_t)max_len);
+            for (int64_t k = i; k < end; k++) {
+                int c;
+                if (PACKED) {
+                    const uint32_t w = TSMEM ? reinterpret_cast<const uint32_t *>(tile)[(k - i0) >> 4]
+                                             : __ldg((const uint32_t *)text + (k >> 4));
+                    c = (int)((w >> ((k & 15) * 2)) & 3u);
+                } else {
+                    c = base_code_or_neg(TSMEM ? tile[k - i0] : __ldg((const uint8_t *)text + k));
+                    if (c < 0) break;
+                }
+                const int64_t cell = 4 * (int64_t)s + c;
+                if (LAYOUT == 0) {
+                    const int32_t e = ld_table<LOADS>(t.rows + cell);
+                    if (e == 0) break;
+                    s = e & 0x7FFFFFFF;
+                    if (e < 0) best = s;
+                } else if (LAYOUT == 1) {
+                    const int32_t nx = ld_table<LOADS>(pt.next + cell);
+                    const int32_t id = ld_table<LOADS>(pt.pid + cell);
+                    if (nx == 0) break;
+                    if (id) best = id;
+                    s = nx;
+                } else {
+                    const int2 e = ld_table<LOADS>(pt.pair + cell);
+                    if (e.x == 0) break;
+                    if (e.y) best = e.y;
+                    s = e.x;
+                }
+            }
+            if (LAYOUT == 0) best = best ? __ldg(t.out_id + best) : 0;
+            out[i] = best;
+        }
+    }
+}
+
+template <bool PACKED, int LAYOUT, int LOADS>
+static void launch_paper_t(bool tsmem, int blocks, size_t smem, cudaStream_t st, const DeviceTable &t,
+                           const PaperTables &pt, const void *text, int64_t n, int32_t *out)
+{
+    if (tsmem) paper_walk_kernel<PACKED, LAYOUT, LOADS, true><<<blocks, kPaperBlock, smem, st>>>(t, pt, text, n, out);
+    else paper_walk_kernel<PACKED, LAYOUT, LOADS, false><<<blocks, kPaperBlock, 0, st>>>(t, pt, text, n, out);
+}
+
+template <bool PACKED, int LAYOUT>
+static void launch_paper_l(int loads, bool tsmem, int blocks, size_t smem, cudaStream_t st, const DeviceTable &t,
+                           const PaperTables &pt, const void *text, int64_t n, int32_t *out)
+{
+    if (loads == 1) launch_paper_t<PACKED, LAYOUT, 1>(tsmem, blocks, smem, st, t, pt, text, n, out);
+    else if (loads == 2) launch_paper_t<PACKED, LAYOUT, 2>(tsmem, blocks, smem, st, t, pt, text, n, out);
+    else launch_paper_t<PACKED, LAYOUT, 0>(tsmem, blocks, smem, st, t, pt, text, n, out);
+}
+
+template <bool PACKED>
+static void launch_paper_p(const PaperConfig &pc, int blocks, size_t smem, cudaStream_t st, const DeviceTable &t,
+                           const PaperTables &pt, const void *text, int64_t n, int32_t *out)
+{
+    const bool ts = pc.text_smem != 0;
+    if (pc.layout == 1) launch_paper_l<PACKED, 1>(pc.loads, ts, blocks, smem, st, t, pt, text, n, out);
+    else if (pc.layout == 2) launch_paper_l<PACKED, 2>(pc.loads, ts, blocks, smem, st, t, pt, text, n, out);
+    else launch_paper_l<PACKED, 0>(pc.loads, ts, blocks, smem, st, t, pt, text, n, out);
+}
+
+int launch_paper_walk(const DeviceTable &t, const PaperTables &pt, const PaperConfig &pc, const void *text,
+                      bool packed, int64_t n, int32_t *out, cudaStream_t st, const DeviceProps &dp)
+{
+    if (n == 0) return PFAC_OK;
+    if (pc.layout < 0 || pc.layout > 2 || pc.loads < 0 || pc.loads > 2) return PFAC_ERR_INVALID_ARG;
+    if ((pc.layout == 1 && (!pt.next || !pt.pid)) || (pc.layout == 2 && !pt.pair)) return PFAC_ERR_UNSUPPORTED;
+    // shared-memory tile: 256 offsets plus max_len - 1 bases (packed: whole words, one
+    // more for a tile that starts mid-word)
+    const int64_t tile_bases = kPaperBlock + (int64_t)t.max_len - 1;
+    const int64_t smem = packed ? 4 * ((tile_bases + 15) / 16 + 1) : tile_bases;
+    if (pc.text_smem && smem > 48 * 1024) return PFAC_ERR_UNSUPPORTED;
+    const int64_t want = (n + kPaperBlock - 1) / kPaperBlock;
+    const int blocks = (int)std::min<int64_t>(want, (int64_t)dp.num_sms * 8);
+    if (packed) launch_paper_p<true>(pc, blocks, (size_t)smem, st, t, pt, text, n, out);
+    else launch_paper_p<false>(pc, blocks, (size_t)smem, st, t, pt, text, n, out);
+    return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
+}
+
+__global__ void derive_paper_kernel(const int32_t *__restrict__ rows, const int32_t *__restrict__ out_id, int64_t cells,
+                                    int32_t *next, int32_t *pid, int2 *pair)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < cells; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = rows[k];
+        const int32_t nx = e & 0x7FFFFFFF;
+        const int32_t id = e < 0 ? out_id[nx] : 0;    // bit 31: the state reached is terminal
+        if (next) {
+            next[k] = nx;
+            pid[k] = id;
+        }
+        if (pair) pair[k] = make_int2(nx, id);
+    }
+}
+
+int derive_paper_tables(const DeviceTable &t, int32_t *next, int32_t *pid, int2 *pair, cudaStream_t st)
+{
+    if ((next == nullptr) != (pid == nullptr)) return PFAC_ERR_INVALID_ARG;
+    const int64_t cells = 4 * t.n_states;
+    const int blocks = (int)std::min<int64_t>((cells + 255) / 256, 4096);
+    derive_paper_kernel<<<std::max(1, blocks), 256, 0, st>>>(t.rows, t.out_id, cells, next, pid, pair);
+    return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
+}
 
 // ---------------------------------------------------------------------------
 // Kernel 2: warp-specialised pipeline.
@@ -380,6 +544,7 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
     K.defer = P.defer;
     K.defer_cap = P.defer_cap;
     K.defer_count = P.defer_count;
+    K.status = T.status;
     const void *rank_ptr = P.rank_smem ? (const void *)srank : nullptr;
     const uint32_t all = LW == 32 ? 0xFFFFFFFFu : ((1u << LW) - 1u);
     const uint32_t bmask = (uint32_t)((1ull << (2 * B)) - 1ull);
@@ -536,6 +701,7 @@ __global__ void __launch_bounds__(256) tail_kernel(const ScanParams P)
         K.c_ids = P.c_ids;
         K.cap = P.cap;
         K.count = P.count;
+        K.status = P.t.status;
         emit_match<COMPACT>(K, it.gp, walk_global<PACKED, ALL>(P.t, P.text, nullptr, it.gp + it.span, it.gp, it.s,
                                                                (int)(it.q_set & 0xFFFFu), it.best, &K));
     }
@@ -677,14 +843,29 @@ static cudaError_t launch_with_policy(Kern kern, const ScanParams &P, int grid, 
     return cudaLaunchKernelEx(&lc, kern, P);
 }
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum, once per
+// (kernel, device): later launches, including those captured into a CUDA graph, make
+// no attribute call.
+static cudaError_t allow_max_smem(const void *kern, const DeviceProps &dp)
+{
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({kern, dp.device})) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dp.smem_optin);
+    if (e == cudaSuccess) done.insert({kern, dp.device});
+    return e;
+}
+
 template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, bool ALL, bool L1F = false>
 static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t smem, int tail_grid, cudaStream_t st,
                          const TiledConfig &cfg, const DeviceProps &dp)
 {
-    auto kern = lane_width_of(cfg) == 32 ? scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, L1F>
-                                         : scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 16, ALL, L1F>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return PFAC_ERR_CUDA;
+    const bool lw32 = lane_width_of(cfg) == 32;
+    auto kern = lw32 ? scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, L1F>
+                     : scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 16, ALL, L1F>;
+    if ((int64_t)smem > (int64_t)dp.smem_optin) return PFAC_ERR_UNSUPPORTED;
+    if (allow_max_smem((const void *)kern, dp) != cudaSuccess) return PFAC_ERR_CUDA;
     if (launch_with_policy(kern, P, grid, threads, smem, st, cfg, dp) != cudaSuccess) return PFAC_ERR_CUDA;
     tail_kernel<PACKED, COMPACT, ALL><<<tail_grid, 256, 0, st>>>(P);
     return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;

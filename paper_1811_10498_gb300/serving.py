@@ -194,6 +194,57 @@ class Server:
         return lat, results, stats
 
 
+def serve_per_request(tables, requests, realtime: bool = True, max_bases: int = 1 << 24,
+                      keep_results=False):
+    """The baseline the server is measured against: one request at a time, in arrival
+    order, on one stream, with one ``pfac_match`` launch per request: its text copied in
+    from pinned memory, the scan, its ids copied out, then the next request. Same
+    latency definition as ``Server.run`` (arrival to ids on the host; with
+    realtime=False every request arrives at time 0). Returns (latency in s, results by
+    request id if keep_results, statistics)."""
+    import torch
+    stream = torch.cuda.Stream()
+    h_in = torch.empty(max_bases, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(max_bases, dtype=torch.int32).pin_memory()
+    d_in = torch.empty(max_bases, dtype=torch.uint8, device="cuda")
+    d_out = torch.empty(max_bases, dtype=torch.int32, device="cuda")
+    # first launch on the stream: the library allocates its per-stream scratch
+    with torch.cuda.stream(stream):
+        d_in[:64].fill_(ord("A"))
+        for t in tables:
+            b.pfac_match(t.h, d_in[:64], d_out[:64], stream)
+    stream.synchronize()
+    order = sorted(requests, key=lambda r: r.arrival)
+    latency, results = {}, {}
+    hin, hout = h_in.numpy(), h_out.numpy()
+    t0 = time.perf_counter()
+    for r in order:
+        n = int(r.text.shape[0])
+        if n > max_bases:
+            raise ValueError(f"request {r.rid} ({n} bases) exceeds the buffer")
+        if realtime:
+            wait = r.arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+        hin[:n] = r.text
+        with torch.cuda.stream(stream):
+            d_in[:n].copy_(h_in[:n], non_blocking=True)
+            b.pfac_match(tables[r.set_id].h, d_in[:n], d_out[:n], stream)
+            h_out[:n].copy_(d_out[:n], non_blocking=True)
+        stream.synchronize()
+        latency[r.rid] = time.perf_counter() - t0 - (r.arrival if realtime else 0.0)
+        if keep_results is True or (keep_results and r.rid in keep_results):
+            results[r.rid] = hout[:n].copy()
+    wall = time.perf_counter() - t0
+    lat = np.array([latency[r.rid] for r in requests]) if requests else np.zeros(0)
+    bases = int(sum(r.text.shape[0] for r in requests))
+    stats = {"requests": len(requests), "launches": len(requests), "bases": bases, "wall_s": wall,
+             "gbases_s": bases / wall / 1e9 if wall > 0 else 0.0,
+             "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
+             "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None}
+    return lat, results, stats
+
+
 def requests_from_stream(stream, limit: int | None = None):
     """Request objects for a datagen RequestStream."""
     n = len(stream.arrivals) if limit is None else min(limit, len(stream.arrivals))

@@ -32,7 +32,7 @@ def test_committed_summary_states_its_source_and_traffic():
 
 def test_clock_summary_counts_samples_under_load_only():
     s = bench.ClockSampler(0)
-    s.lines = [
+    s.lines = list(enumerate([
         # index, sm, max sm, power, util, active, hw, hw thermal, sw thermal, sw power cap
         "0, 1965, 2070, 300.0, 0, 0x0, Not Active, Not Active, Active, Not Active",   # idle
         "0, 2032, 2070, 900.0, 100, 0x4, Not Active, Not Active, Not Active, Active",
@@ -40,12 +40,15 @@ def test_clock_summary_counts_samples_under_load_only():
         "0, 1995, 2070, 980.0, 99, 0x0, Not Active, Not Active, Not Active, Not Active",
         "garbled line",
         "0, N/A, 2070, 0, 50, 0x0, Not Active, Not Active, Not Active, Not Active",
-    ]
+    ]))
     got = s.summary()
     assert got["samples_under_load"] == 3
     assert got["sm_mhz"] == 2010 and got["sm_max_mhz"] == 2070
     # a thermal reason seen while idle is not the timed region's
     assert got["reasons"] == ["sw_power_cap"]
+    # a window of host times keeps only the samples taken inside it
+    win = s.summary(2.5, 3.5)
+    assert win["samples_under_load"] == 1 and win["sm_mhz"] == 1995 and win["reasons"] == []
 
 
 def test_clock_summary_without_samples():

@@ -97,4 +97,5 @@ def test_overflow_reports_true_count():
     have = set(zip(ws.tolist(), wi.tolist()))
     assert all((int(x), int(y)) in have for x, y in zip(o, i))   # each written pair is real
     assert len(set(zip(o.tolist(), i.tolist()))) == cap           # and written once
+    assert b.pfac_device_status(t.h) == b.CODE["PFAC_ERR_OVERFLOW"]
     t.close()

@@ -84,6 +84,25 @@ def test_graph_replay_with_new_batches(batch):
     assert np.array_equal(got3, want), first_diff(got3, want)
 
 
+def test_per_read_graph_baseline_equals_the_oracle(batch):
+    """The baseline of the batched pass (one pfac_match per read, captured once in a CUDA
+    graph and replayed twice) gives the oracle's ids."""
+    import torch
+    from paper_1811_10498_gb300.batched import PerReadGraph
+    w, want, tables = batch
+    d_text = to_dev(w.reads)
+    out = torch.full((w.reads.size,), -3, dtype=torch.int32, device="cuda")
+    pg = PerReadGraph(tables, d_text, w.read_offsets, w.read_set, out)
+    out.fill_(-3)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        pg.run()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.array_equal(got, want), first_diff(got, want)
+    assert pg.launches == 2 * int((np.diff(w.read_offsets) > 0).sum())
+
+
 def test_reads_do_not_cross_into_each_other():
     sets = [[b"ACGT", b"GTAC", b"TT"], [b"CCCCAAAA", b"AT"]]
     tables = [b.Table(s) for s in sets]

@@ -283,13 +283,19 @@ def test_compact_list(genome_small, kernel):
     i = d_ids[:cnt].cpu().numpy()
     order = np.argsort(o, kind="stable")
     assert np.array_equal(o[order], offs_want) and np.array_equal(i[order], ids_want)
+    assert b.pfac_device_status(t.h) == b.CODE["PFAC_OK"]    # the list had room
 
 
-def test_compact_overflow(genome_small):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_compact_overflow(genome_small, kernel):
+    """A list with room for a third of the matches: the true count, every slot written
+    once with a real match, and PFAC_ERR_OVERFLOW in the handle's device status."""
     import torch
     w, want = genome_small
     t = b.Table((w.blob, w.offsets))
+    b.pfac_set_config(t.h, {"kernel": kernel})
     packed, _, _ = b.pack(to_dev(w.text))
+    assert b.pfac_device_status(t.h) == b.CODE["PFAC_OK"]
     total = int((want != 0).sum())
     cap = total // 3
     d_off = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
@@ -302,6 +308,8 @@ def test_compact_overflow(genome_small):
     i = d_ids.cpu().numpy()
     assert np.unique(o).size == cap               # every slot written once
     assert np.array_equal(want[o], i)             # each written pair is a real match
+    assert b.pfac_device_status(t.h) == b.CODE["PFAC_ERR_OVERFLOW"]
+    assert b.pfac_device_status(t.h) == b.CODE["PFAC_OK"]    # reading cleared it
 
 
 # ---- failure handling ----------------------------------------------------------

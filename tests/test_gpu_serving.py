@@ -7,7 +7,7 @@ import oracle
 from gpu_util import require_cuda
 from paper_1811_10498_gb300 import _binding as b
 from paper_1811_10498_gb300 import datagen
-from paper_1811_10498_gb300.serving import Request, Server, requests_from_stream
+from paper_1811_10498_gb300.serving import Request, Server, requests_from_stream, serve_per_request
 
 pytestmark = pytest.mark.gpu
 
@@ -59,3 +59,16 @@ def test_admission_waits_for_device_memory(workload):
     assert stats["batches"] >= 5
     for r in reqs[:10]:
         assert np.array_equal(results[r.rid], want[r.rid])
+
+
+@pytest.mark.parametrize("realtime", [True, False])
+def test_per_request_baseline_equals_the_oracle(workload, realtime):
+    """The baseline the server is compared with (one request at a time, one pfac_match
+    launch each) gives the same ids, and reports one launch per request."""
+    st, reqs, tables, want = workload
+    lat, results, stats = serve_per_request(tables, reqs, realtime=realtime, max_bases=1 << 21,
+                                            keep_results=True)
+    assert stats["requests"] == stats["launches"] == len(reqs)
+    for r in reqs:
+        assert np.array_equal(results[r.rid], want[r.rid]), r.rid
+    assert lat.size == len(reqs) and stats["p99_ms"] >= stats["p50_ms"] > 0
