@@ -728,7 +728,7 @@ def main():
             "wall_s_timed_region": wall,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "autotune": {k: tuned.get(k) for k in ("lane_offsets", "threads", "stages", "walk_loads",
-                                                   "rank_in_smem", "ms", "default_ms", "candidates")}
+                                                   "rank_in_smem", "zero_writer", "ms", "default_ms", "candidates")}
             if tuned else None,
             "extra": {"pack_gbases_s": pack_gbs, "build_s": build_s,
                       "frac_of_roofline_gbases": value / world / (peak / BYTES_PER_BASE)},

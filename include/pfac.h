@@ -224,7 +224,14 @@ typedef struct {
                                 offsets plus max_len - 1 bases) into shared memory and
                                 walks from there; tables whose tile would exceed 48 KB fall
                                 back to reading the text from global memory */
-    int32_t reserved;        /* 0 */
+    int32_t zero_writer;     /* kernel 2, dense ids of packed text with 32 offsets per lane:
+                                who stores the ids of offsets without a match (most of the
+                                output): 0 = automatic, 1 = each consumer warp stores its
+                                own, 2 = one warp of the CTA stores them all with 16-byte
+                                stores, 3 = one warp stores them with TMA bulk copies of a
+                                zero tile in shared memory. With 2 and 3 the consumer warps
+                                store a match only after the writer has published that its
+                                tile's zeros are written. */
 } pfac_config;
 
 /* Set (cfg != NULL) or reset (cfg == NULL) the launch configuration of a handle.

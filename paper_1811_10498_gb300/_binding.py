@@ -49,7 +49,7 @@ class pfac_table_info(C.Structure):
 class pfac_config(C.Structure):
     _fields_ = [("kernel", I32), ("threads", I32), ("ctas_per_sm", I32), ("stages", I32), ("rank_in_smem", I32),
                 ("l2_persist", I32), ("walk_loads", I32), ("lane_offsets", I32), ("table_layout", I32),
-                ("row_loads", I32), ("text_smem", I32), ("reserved", I32)]
+                ("row_loads", I32), ("text_smem", I32), ("zero_writer", I32)]
 
 
 _lib = None

@@ -5,7 +5,8 @@ The knobs are those of ``pfac_config`` (include/pfac.h):
 * single scans (kernel 2): offsets per consumer lane and threads per CTA (together the
   tile length, 32 x lane_offsets x consumer warps), text stages in the shared-memory
   ring, dependent table loads a walk may take before it is deferred to the tail kernel,
-  and shared memory or L2 for the prefix filter's rank index;
+  shared memory or L2 for the prefix filter's rank index, and who stores the zero ids
+  (the consumer warps, or a writer warp with 16-byte or TMA bulk stores);
 * batched passes: offsets per lane (the work-item length, 32 x lane_offsets), threads per
   SM of the persistent scan kernel, and the in-kernel walk depth.
 
@@ -35,6 +36,7 @@ SCAN_KNOBS = [
     ("stages", (2, 3, 4, 6)),
     ("walk_loads", (1, 2, 3, 4)),
     ("rank_in_smem", (0, -1)),
+    ("zero_writer", (1, 2, 3)),
 ]
 # l2_persist is not searched: the persisting set-aside is a limit of the whole context,
 # and on the genome-scale workload (skip entries 17 MB, already L2-resident) the window
@@ -136,7 +138,7 @@ def _events_median(torch, run, reps: int, flush=None) -> float:
 
 
 # What a 0 ("automatic") field of pfac_config means for the knobs tuned here.
-_AUTO = {"walk_loads": 2, "lane_offsets": 16, "l2_persist": -1}
+_AUTO = {"walk_loads": 2, "lane_offsets": 16, "l2_persist": -1, "zero_writer": 1}
 
 
 def _start(h: int, n_bases: int, knobs, packed: bool = True) -> dict:

@@ -137,6 +137,7 @@ pfac::TiledConfig tiled_config(const pfac_config &c)
     t.walk_loads = c.walk_loads;
     t.lane_offsets = c.lane_offsets;
     t.l2_persist = c.l2_persist;
+    t.zero_writer = c.zero_writer > 0 ? c.zero_writer - 1 : 0;
     t.timeout_ns = 2000000000LL;
     return t;
 }
@@ -578,7 +579,7 @@ int pfac_set_config(pfac_handle h, const pfac_config *cfg)
             cfg->stages < 0 || cfg->stages == 1 || cfg->stages > 8 || cfg->walk_loads < 0 ||
             (cfg->lane_offsets != 0 && cfg->lane_offsets != 16 && cfg->lane_offsets != 32) ||
             cfg->table_layout < 0 || cfg->table_layout > 2 || cfg->row_loads < 0 || cfg->row_loads > 2 ||
-            cfg->text_smem < 0 || cfg->text_smem > 1 || cfg->reserved != 0)
+            cfg->text_smem < 0 || cfg->text_smem > 1 || cfg->zero_writer < 0 || cfg->zero_writer > 3)
             return fail(PFAC_ERR_INVALID_ARG);
         if (cfg->kernel == 2 && !(h->skip_bytes > 0 && h->host.filter_b > 0)) return fail(PFAC_ERR_UNSUPPORTED);
         const int rc = ensure_paper_layout(h, cfg->table_layout);

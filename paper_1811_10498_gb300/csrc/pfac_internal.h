@@ -131,6 +131,9 @@ struct TiledConfig {
     int32_t lane_offsets;      // offsets per consumer lane: 16 (default) or 32
     int32_t smem_table_bytes;  // < 0: keep the rank index in global memory
     int32_t l2_persist;        // > 0: access-policy window over the skip entries
+    int32_t zero_writer;       // dense packed scans, 32 offsets per lane: 0 = consumer warps
+                               // store their zeros, 1 = a writer warp with 16-byte stores,
+                               // 2 = a writer warp with TMA bulk stores of a zero tile
     int64_t timeout_ns;        // limit of every bounded wait
 };
 

@@ -392,11 +392,92 @@ struct ScanParams {
     int32_t rank_smem;           // rank index copied into shared memory
     int32_t walk_loads;          // dependent table loads a walk may take before it is deferred
     uint32_t off_filter, off_rank, off_bar, off_queue, off_stage, stage_bytes;
+    uint32_t off_zero, zero_chunk;   // zero tile of the bulk-store writer (ZW = 2)
     int64_t timeout_ns;
 };
 
 constexpr int kMaxStages = 8;
-constexpr uint32_t kBarBytes = 256;   // full[8], empty[8], abort flag
+constexpr uint32_t kBarBytes = 256;   // full[8], empty[8], abort flag, zero-writer progress
+constexpr uint32_t kAbortAt = 128, kZeroDoneAt = 192;
+
+__device__ __forceinline__ void st_release_cta(volatile uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_addr((const void *)p)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_cta(const volatile uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr((const void *)p)) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_2() { asm volatile("cp.async.bulk.wait_group 2;" ::: "memory"); }
+
+// The zero writer of dense packed scans (a warp of its own, so that the consumer warps
+// only test, walk and store matches). For each tile round k of the CTA it writes the
+// tile's zeros and then publishes in *zdone how many rounds are complete, with release
+// semantics; a consumer stores a match of round k only after reading *zdone > k with
+// acquire semantics, so the match lands after the zero it replaces.
+//   ZW = 1: all 32 lanes, 16-byte stores (512 contiguous bytes per instruction);
+//   ZW = 2: one lane, TMA bulk stores of a zero tile in shared memory, two rounds in
+//           flight; a round counts as done once its bulk group has completed and a
+//           proxy fence orders those writes before the consumers' ordinary stores.
+template <int ZW>
+__device__ void zero_writer(const ScanParams &P, uint8_t *smem, volatile uint32_t *zdone, int lane)
+{
+    const uint64_t pol = policy_evict_first();
+    uint32_t k = 0;
+    if (ZW == 1) {
+        const int4 z = make_int4(0, 0, 0, 0);
+        for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, k++) {
+            const int64_t lo = t * P.tile, cnt = min((int64_t)P.tile, P.n - lo);
+            int32_t *o = P.out + lo;
+            const int64_t nv = cnt >> 2;
+            for (int64_t v = lane; v < nv; v += 32) st_global_v4_hint(o + 4 * v, z, pol);
+            for (int64_t i = 4 * nv + lane; i < cnt; i += 32) o[i] = 0;
+            __syncwarp();
+            if (lane == 0) st_release_cta(zdone, k + 1);
+        }
+    } else if (lane == 0) {
+        const uint32_t zb = smem_addr(smem + P.off_zero);
+        for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, k++) {
+            const int64_t lo = t * P.tile, cnt = min((int64_t)P.tile, P.n - lo);
+            uint8_t *dst = reinterpret_cast<uint8_t *>(P.out + lo);
+            const int64_t full = (cnt * 4) & ~(int64_t)15;
+            for (int64_t b = 0; b < full; b += P.zero_chunk)
+                bulk_store(dst + b, zb, (uint32_t)min((int64_t)P.zero_chunk, full - b), pol);
+            for (int64_t i = full / 4; i < cnt; i++) P.out[lo + i] = 0;    // the last < 4 ids
+            bulk_commit();
+            bulk_wait_2();                       // the groups of rounds <= k - 2 are complete
+            if (k >= 2) {
+                fence_proxy_async_global();
+                st_release_cta(zdone, k - 1);
+            }
+        }
+        bulk_wait_all();
+        fence_proxy_async_global();
+        st_release_cta(zdone, k);
+    }
+}
+
+// A consumer's wait until the zeros of its rounds < need are written (bounded; gives up
+// when the CTA aborts).
+__device__ __forceinline__ bool wait_zeros(const volatile uint32_t *zdone, uint32_t need, int64_t limit_ns,
+                                           volatile uint32_t *abort_flag)
+{
+    if (ld_acquire_cta(zdone) >= need) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        if (ld_acquire_cta(zdone) >= need) return true;
+        if (*abort_flag) return false;
+        if ((int64_t)(global_timer_ns() - t0) > limit_ns) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
 // Packed text: offsets that pass the filter wait in a per-warp ring of kQueue entries
 // until a full warp of them can be walked together. An entry is the offset coded as
 // (tile round of the CTA) << kRelBits | (offset within the tile).
@@ -450,13 +531,17 @@ __device__ __forceinline__ uint32_t filter_bits_screened(const DeviceTable &T, u
 
 // L1F (packed text, main filter in global memory): the first-level filter of order
 // kFilter1B sits in shared memory at offset 0 and screens every offset first.
-template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW, bool ALL = false, bool L1F = false>
+// ZW (dense packed scans): 0 = each consumer warp stores its own zeros; 1 or 2 = a zero
+// writer warp (warp consumers + 1) stores them (see zero_writer).
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW, bool ALL = false, bool L1F = false, int ZW = 0>
 __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
 {
+    static_assert(ZW == 0 || (PACKED && !COMPACT && !ALL), "a zero writer serves dense packed scans");
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + P.off_bar);
     uint64_t *empty = reinterpret_cast<uint64_t *>(smem + P.off_bar + 64);
-    volatile uint32_t *abort_flag = reinterpret_cast<volatile uint32_t *>(smem + P.off_bar + 128);
+    volatile uint32_t *abort_flag = reinterpret_cast<volatile uint32_t *>(smem + P.off_bar + kAbortAt);
+    volatile uint32_t *zdone = reinterpret_cast<volatile uint32_t *>(smem + P.off_bar + kZeroDoneAt);
     // the filter sits at offset 0 when it is in shared memory
     const uint32_t *sf = reinterpret_cast<const uint32_t *>(smem);
     uint8_t *stage0 = smem + P.off_stage;
@@ -475,7 +560,14 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             mbar_init(smem_addr(&empty[i]), (uint32_t)P.consumers);
         }
         *abort_flag = 0;
+        *zdone = 0;
         fence_mbar_init();
+    }
+    if (ZW == 2 && tid < 32) {
+        // the zero tile the writer's bulk stores read; made visible to the async proxy
+        for (uint32_t i = 16 * (uint32_t)tid; i < P.zero_chunk; i += 16 * 32)
+            *reinterpret_cast<int4 *>(smem + P.off_zero + i) = make_int4(0, 0, 0, 0);
+        fence_proxy_async();
     }
     {
         // filter and rank index, resident for the whole persistent kernel
@@ -506,6 +598,10 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
     const int unit = PACKED ? 4 : 1;
     const int64_t tile_units = PACKED ? (P.tile >> 4) : P.tile;
 
+    if (ZW && warp == P.consumers + 1) {
+        zero_writer<ZW>(P, smem, zdone, lane);
+        return;
+    }
     if (warp == P.consumers) {
         // ---------------- producer warp ----------------
         if (lane == 0) {
@@ -591,7 +687,7 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             // after that would come from the next fill.
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_addr(&empty[st]));
-            if (!COMPACT) zero_batch<LW>(K, warp_base, lane, valid, true, pol);
+            if (!COMPACT && !ZW) zero_batch<LW>(K, warp_base, lane, valid, true, pol);
             // Zeros stored above by one lane are ordered before matches stored by another
             // lane in a later round by the warp barriers between them (this one first).
             __syncwarp();
@@ -621,6 +717,10 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                 qcount += take;
                 total -= take;
                 __syncwarp();
+                if (ZW && qcount >= 32 && !wait_zeros(zdone, (uint32_t)k + 1, P.timeout_ns, abort_flag)) {
+                    if (lane == 0) record_error(T.status, PFAC_ERR_TIMEOUT);
+                    return;
+                }
                 while (qcount >= 32) {
                     queue_round<COMPACT, FSMEM, RANK16, ALL>(P, K, sf, rank_ptr, queue, qhead, 32, lane);
                     qhead = (qhead + 32) & (kQueue - 1);
@@ -684,7 +784,13 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                                                                 valid, true, pol);
         }
     }
-    if (PACKED && qcount) queue_round<COMPACT, FSMEM, RANK16, ALL>(P, K, sf, rank_ptr, queue, qhead, qcount, lane);
+    if (PACKED && qcount) {
+        if (ZW && !wait_zeros(zdone, (uint32_t)k, P.timeout_ns, abort_flag)) {
+            if (lane == 0) record_error(T.status, PFAC_ERR_TIMEOUT);
+            return;
+        }
+        queue_round<COMPACT, FSMEM, RANK16, ALL>(P, K, sf, rank_ptr, queue, qhead, qcount, lane);
+    }
 }
 
 // Deferred walks: one thread per item.
@@ -708,14 +814,14 @@ __global__ void __launch_bounds__(256) tail_kernel(const ScanParams P)
 }
 
 struct ScanLayout {
-    uint32_t off_filter, off_rank, off_bar, off_queue, off_stage, stage_bytes, total;
+    uint32_t off_filter, off_rank, off_bar, off_queue, off_stage, stage_bytes, off_zero, total;
     int32_t stage_units;
 };
 
 static inline uint32_t align128(uint64_t x) { return (uint32_t)((x + 127) & ~(uint64_t)127); }
 
 static ScanLayout scan_layout(int consumers, int lw, int stages, int64_t filter_smem_bytes, int64_t rank_smem_bytes,
-                              bool packed)
+                              bool packed, int64_t zero_bytes = 0)
 {
     ScanLayout L{};
     const int64_t tile = 32LL * lw * consumers;
@@ -734,11 +840,21 @@ static ScanLayout scan_layout(int consumers, int lw, int stages, int64_t filter_
     L.stage_bytes = align128((uint64_t)L.stage_units * (packed ? 4 : 1));
     L.off_stage = (uint32_t)off;
     off += (uint64_t)L.stage_bytes * stages;
+    L.off_zero = (uint32_t)off;
+    off += align128((uint64_t)zero_bytes);
     L.total = (uint32_t)off;
     return L;
 }
 
-static int consumers_of(const TiledConfig &cfg) { return cfg.threads / 32 - 1; }
+// The zero writer a launch uses: only dense scans of packed text with 32 offsets per
+// lane have one (other launches store zeros from the consumer warps).
+static int zero_writer_of(const TiledConfig &cfg, bool packed, bool compact, bool all)
+{
+    if (!packed || compact || all || cfg.lane_offsets != 32) return 0;
+    return cfg.zero_writer == 1 || cfg.zero_writer == 2 ? cfg.zero_writer : 0;
+}
+
+static int consumers_of(const TiledConfig &cfg, int zw = 0) { return cfg.threads / 32 - 1 - (zw ? 1 : 0); }
 static int lane_width_of(const TiledConfig &cfg) { return cfg.lane_offsets == 32 ? 32 : 16; }
 static int stages_of(const TiledConfig &cfg, bool packed) { return cfg.stages > 0 ? cfg.stages : (packed ? 3 : 2); }
 
@@ -748,12 +864,18 @@ struct SmemPlan {
     int64_t filter_bytes, rank_bytes;   // bytes copied into shared memory (0 = global)
     int64_t total;
     bool l1f;                           // filter_bytes hold the first-level filter
+    int zw;                             // zero writer (0 = the consumer warps)
+    int64_t zero_chunk;                 // bytes of the bulk-store zero tile (zw == 2)
 };
 
-static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool packed, const DeviceProps &dp)
+// With a bulk-store zero writer (zw == 2) the zero tile comes after the filter and before
+// the rank index: 2 KB at least (else the writer uses 16-byte stores, zw = 1), then up to
+// 16 KB from what the rank index leaves.
+static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool packed, const DeviceProps &dp,
+                          int zw = 0)
 {
     SmemPlan pl{};
-    const int C = consumers_of(cfg);
+    const int C = consumers_of(cfg, zw);
     const int LW = lane_width_of(cfg);
     const int S = stages_of(cfg, packed);
     const int64_t per_cta = (int64_t)dp.smem_per_sm / std::max(1, cfg.ctas_per_sm) - 1024;
@@ -761,11 +883,13 @@ static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool pac
     const int64_t words = t.filter_b >= 3 ? ((int64_t)1 << (2 * t.filter_b)) / 32 : 1;
     const int64_t fbytes = words * 4;
     const int64_t rbytes = words * (t.rank_wide ? 4 : 2);
-    auto total = [&](int64_t f, int64_t r) { return (int64_t)scan_layout(C, LW, S, f, r, packed).total; };
+    int64_t zb = zw == 2 ? 2048 : 0;
+    auto total = [&](int64_t f, int64_t r) { return (int64_t)scan_layout(C, LW, S, f, r, packed, zb).total; };
     if (total(0, 0) > limit) {
         pl.total = -1;
         return pl;
     }
+    pl.zw = zw;
     pl.filter_bytes = total(fbytes, 0) <= limit ? fbytes : 0;
     if (!pl.filter_bytes && packed && t.filter1_b == kFilter1B && t.filter1) {
         const int64_t f1 = ((int64_t)1 << (2 * kFilter1B)) / 8;
@@ -774,7 +898,19 @@ static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool pac
             pl.l1f = true;
         }
     }
+    if (zw == 2 && total(pl.filter_bytes, 0) > limit) {
+        zw = pl.zw = 1;                  // no room for a zero tile: 16-byte stores instead
+        zb = 0;
+    }
     pl.rank_bytes = (!pl.l1f && cfg.smem_table_bytes >= 0 && total(pl.filter_bytes, rbytes) <= limit) ? rbytes : 0;
+    if (zw == 2) {
+        for (int64_t c = 16384; c > 2048; c >>= 1) {
+            zb = c;
+            if (total(pl.filter_bytes, pl.rank_bytes) <= limit) break;
+            zb = 2048;
+        }
+        pl.zero_chunk = zb;
+    }
     pl.total = total(pl.filter_bytes, pl.rank_bytes);
     return pl;
 }
@@ -857,13 +993,23 @@ static cudaError_t allow_max_smem(const void *kern, const DeviceProps &dp)
     return e;
 }
 
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, bool ALL, bool L1F>
+static void (*scan_kernel_for(bool lw32, int zw))(const ScanParams)
+{
+    if constexpr (PACKED && !COMPACT && !ALL) {
+        if (zw == 1) return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, L1F, 1>;
+        if (zw == 2) return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, L1F, 2>;
+    }
+    return lw32 ? scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, L1F>
+                : scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 16, ALL, L1F>;
+}
+
 template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, bool ALL, bool L1F = false>
 static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t smem, int tail_grid, cudaStream_t st,
-                         const TiledConfig &cfg, const DeviceProps &dp)
+                         const TiledConfig &cfg, const DeviceProps &dp, int zw)
 {
     const bool lw32 = lane_width_of(cfg) == 32;
-    auto kern = lw32 ? scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, L1F>
-                     : scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 16, ALL, L1F>;
+    auto kern = scan_kernel_for<PACKED, COMPACT, FSMEM, RANK16, ALL, L1F>(lw32, zw);
     if ((int64_t)smem > (int64_t)dp.smem_optin) return PFAC_ERR_UNSUPPORTED;
     if (allow_max_smem((const void *)kern, dp) != cudaSuccess) return PFAC_ERR_CUDA;
     if (launch_with_policy(kern, P, grid, threads, smem, st, cfg, dp) != cudaSuccess) return PFAC_ERR_CUDA;
@@ -874,20 +1020,21 @@ static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t sm
 template <bool PACKED, bool COMPACT, bool ALL = false>
 static int launch_scan_w(const ScanParams &P, bool fsmem, bool rank16, int grid, int threads, uint32_t smem,
                          int tail_grid, cudaStream_t st, const TiledConfig &cfg, const DeviceProps &dp,
-                         bool l1f = false)
+                         bool l1f = false, int zw = 0)
 {
     if constexpr (PACKED) {
         if (l1f)
             return rank16 ? launch_scan_t<PACKED, COMPACT, false, true, ALL, true>(P, grid, threads, smem, tail_grid,
-                                                                                 st, cfg, dp)
+                                                                                 st, cfg, dp, zw)
                           : launch_scan_t<PACKED, COMPACT, false, false, ALL, true>(P, grid, threads, smem, tail_grid,
-                                                                                  st, cfg, dp);
+                                                                                  st, cfg, dp, zw);
     }
     if (fsmem)
-        return rank16 ? launch_scan_t<PACKED, COMPACT, true, true, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp)
-                      : launch_scan_t<PACKED, COMPACT, true, false, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp);
-    return rank16 ? launch_scan_t<PACKED, COMPACT, false, true, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp)
-                  : launch_scan_t<PACKED, COMPACT, false, false, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp);
+        return rank16 ? launch_scan_t<PACKED, COMPACT, true, true, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp, zw)
+                      : launch_scan_t<PACKED, COMPACT, true, false, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp,
+                                                                         zw);
+    return rank16 ? launch_scan_t<PACKED, COMPACT, false, true, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp, zw)
+                  : launch_scan_t<PACKED, COMPACT, false, false, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp, zw);
 }
 
 int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n, int32_t *out, int64_t *c_off,
@@ -897,15 +1044,18 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     const bool compact = c_off != nullptr;
     if (compact && cudaMemsetAsync(count, 0, sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     if (n == 0) return PFAC_OK;
-    const int C = consumers_of(cfg);
+    const int zw_asked = zero_writer_of(cfg, packed, compact, all_matches);
     const int LW = lane_width_of(cfg);
     const int S = stages_of(cfg, packed);
-    if (!t.skip || !t.filter || !t.rank || !t.dense || t.filter_b < 1 || t.filter_b > kMaxFilterB || C < 1 ||
-        (cfg.threads & 31) || cfg.threads > 1024 || S < 2 || S > kMaxStages || !scratch.items || !scratch.count)
+    if (!t.skip || !t.filter || !t.rank || !t.dense || t.filter_b < 1 || t.filter_b > kMaxFilterB ||
+        consumers_of(cfg, zw_asked) < 1 || (cfg.threads & 31) || cfg.threads > 1024 || S < 2 || S > kMaxStages ||
+        !scratch.items || !scratch.count)
         return PFAC_ERR_INVALID_ARG;
-    const SmemPlan pl = plan_smem(t, cfg, packed, dp);
+    const SmemPlan pl = plan_smem(t, cfg, packed, dp, zw_asked);
     if (pl.total < 0 || pl.total > dp.smem_optin) return PFAC_ERR_UNSUPPORTED;
-    const ScanLayout L = scan_layout(C, LW, S, pl.filter_bytes, pl.rank_bytes, packed);
+    const int zw = pl.zw;
+    const int C = consumers_of(cfg, zw);
+    const ScanLayout L = scan_layout(C, LW, S, pl.filter_bytes, pl.rank_bytes, packed, pl.zero_chunk);
     if (cudaMemsetAsync(scratch.count, 0, sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     ScanParams P{};
     P.t = t;
@@ -934,6 +1084,8 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     P.off_queue = L.off_queue;
     P.off_stage = L.off_stage;
     P.stage_bytes = L.stage_bytes;
+    P.off_zero = L.off_zero;
+    P.zero_chunk = (uint32_t)pl.zero_chunk;
     P.timeout_ns = cfg.timeout_ns > 0 ? cfg.timeout_ns : 2000000000LL;
     const int64_t grid64 = std::min<int64_t>(P.n_tiles, (int64_t)dp.num_sms * std::max(1, cfg.ctas_per_sm));
     const int grid = (int)std::max<int64_t>(1, grid64);
@@ -952,7 +1104,7 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
         return compact ? launch_scan_w<true, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp,
                                                    l1f)
                        : launch_scan_w<true, false>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp,
-                                                    l1f);
+                                                    l1f, zw);
     return compact ? launch_scan_w<false, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp)
                    : launch_scan_w<false, false>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp);
 }

@@ -70,6 +70,13 @@ def genome_small():
     dict(kernel=2, lane_offsets=16),
     dict(kernel=2, lane_offsets=16, stages=4),
     dict(kernel=2, lane_offsets=32, stages=3, threads=1024),
+    dict(kernel=2, zero_writer=1),
+    dict(kernel=2, zero_writer=2),
+    dict(kernel=2, zero_writer=3),
+    dict(kernel=2, zero_writer=2, threads=96, stages=2),
+    dict(kernel=2, zero_writer=3, threads=96, stages=2),
+    dict(kernel=2, zero_writer=3, rank_in_smem=-1),
+    dict(kernel=2, zero_writer=3, walk_loads=1),
 ], ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
 def test_genome_configs(genome_small, cfg, packed):
     w, want = genome_small
@@ -142,12 +149,14 @@ def test_empty_text():
     assert gpu_match(t, np.zeros(0, dtype=np.uint8)).size == 0
 
 
-@pytest.mark.parametrize("threads,lw", [(64, 16), (128, 32), (1024, 16), (1024, 32)])
-def test_matches_across_tile_edges(threads, lw):
+@pytest.mark.parametrize("threads,lw,zw", [(64, 16, 0), (128, 32, 0), (1024, 16, 0), (1024, 32, 0), (96, 32, 2),
+                                           (96, 32, 3), (1024, 32, 3)])
+def test_matches_across_tile_edges(threads, lw, zw):
     """Long patterns planted so they start just before, at and after tile edges (a tile
-    is 1024 bases per consumer warp) and end exactly at a tile edge, at a 32-base lane
-    batch edge, at a 64-base window edge, and at the text end."""
-    tile = 32 * lw * (threads // 32 - 1)
+    is 32 x lw bases per consumer warp; a zero-writer warp takes one warp from the
+    consumers) and end exactly at a tile edge, at a 32-base lane batch edge, at a 64-base
+    window edge, and at the text end."""
+    tile = 32 * lw * (threads // 32 - 1 - (zw > 1))
     rng = datagen.rng_for(99)
     n = tile * 6 + 37
     text = datagen.iid_text(n, rng)
@@ -163,9 +172,9 @@ def test_matches_across_tile_edges(threads, lw):
     want = ref(text, pats)
     t = b.Table(pats)
     for kernel in (1, 2):
-        got = gpu_match(t, text, kernel=kernel, threads=threads, lane_offsets=lw)
+        got = gpu_match(t, text, kernel=kernel, threads=threads, lane_offsets=lw, zero_writer=zw)
         assert np.array_equal(got, want), (kernel, first_diff(got, want))
-        got = gpu_match_packed(t, text, kernel=kernel, threads=threads, lane_offsets=lw)
+        got = gpu_match_packed(t, text, kernel=kernel, threads=threads, lane_offsets=lw, zero_writer=zw)
         assert np.array_equal(got, want), (kernel, first_diff(got, want))
     assert (want != 0).sum() >= len(pats) // 2
 
@@ -342,8 +351,9 @@ def test_host_pointers_rejected():
     assert rc == b.CODE["PFAC_ERR_INVALID_ARG"]
 
 
-@pytest.mark.parametrize("cfg", [dict(kernel=2, lane_offsets=32, walk_loads=8), dict(kernel=2, walk_loads=64)],
-                         ids=["lw32_loads8", "lw16_loads64"])
+@pytest.mark.parametrize("cfg", [dict(kernel=2, lane_offsets=32, walk_loads=8), dict(kernel=2, walk_loads=64),
+                                 dict(kernel=2, zero_writer=2, walk_loads=8), dict(kernel=2, zero_writer=3, walk_loads=8)],
+                         ids=["lw32_loads8", "lw16_loads64", "writer16B_loads8", "writerbulk_loads8"])
 def test_repeated_scans_with_long_walks_in_kernel(genome_small, cfg):
     """Matches found inside the scan kernel are stored by the lane that walks them,
     after the zero stores of the lane that owns the offset; repeated runs must agree
