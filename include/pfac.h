@@ -82,13 +82,17 @@ typedef struct {
     int32_t host_only;  /* 1: build the tables on the host only (no device copy; the
                            scan calls reject the handle with PFAC_ERR_HOST_ONLY). */
     int32_t filter_b;   /* order of the prefix filter: 0 = automatic (about
-                           log4(n) + 2.2, between 6 and 12), -1 = none,
-                           1..12 = that order. One bit per b-mer, clear when a walk over
+                           log4(n) + 2.2, between 6 and 12; 14 for sets of 2^19
+                           patterns or more with none shorter than 14), -1 = none,
+                           1..14 = that order. One bit per b-mer, clear when a walk over
                            those b bases ends with no pattern on the way, so the answer
                            at that offset is 0 whatever follows (an exact property of
                            the same trie). A filter above order 10 (too large for shared
                            memory) comes with a first-level filter of order 10, derived
                            from it, that the packed scan keeps in shared memory. */
+    int32_t sample;     /* sampled screen (see pfac_export_sample): 0 = built when the
+                           filter is of order 11 or more and every pattern has at least
+                           16 bases, -1 = never */
 } pfac_build_opts;
 
 pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, int32_t n,
@@ -148,6 +152,8 @@ typedef struct {
     int32_t has_skip;       /* skip entries available (fewer than 2^27 states) */
     int32_t rank_wide;      /* the filter's rank index has 32-bit entries */
     int32_t device;         /* device holding the copy, -1 if host only */
+    int32_t sample_q;       /* sampled screen: q-gram length, 0 if the table has none */
+    int32_t sample_s;       /* sampled screen: probe stride (see pfac_export_sample) */
     int32_t pad;
 } pfac_table_info;
 
@@ -179,6 +185,18 @@ int pfac_export(pfac_handle h, int32_t *rows, int32_t *out_id, int64_t *level);
  * Any output may be NULL; sizes (in uint32 words) are checked against the tables. */
 int pfac_export_shortcuts(pfac_handle h, uint32_t *skip, int64_t skip_words, uint32_t *filter,
                           int64_t filter_words, uint32_t *dense, int64_t dense_words);
+
+/* Copy the sampled screen of a host-only handle (pfac_build_opts.host_only = 1; a handle
+ * with a device copy gives PFAC_ERR_UNSUPPORTED): 4^q bits (q = sample_q of
+ * pfac_info_ex; bit g = bit g mod 32 of word g / 32, base j of g in bits 2j..2j+1), set
+ * for the q-grams at positions 0 .. s-1 (s = sample_s) of every pattern. The builder
+ * makes it for tables whose prefix filter is of order 11 or more and whose patterns all
+ * have at least q + s - 1 bases; the packed scan then probes the text at every s-th
+ * offset and walks only from offsets whose next probe (at or after them) is set, since
+ * a pattern starting at offset i has its q-gram at position (-i) mod s at that probe.
+ * `words` is the capacity of `sample` in uint32 words (0 and NULL when the table has
+ * none: nothing is copied). Not in the paper: a screen of this build. */
+int pfac_export_sample(pfac_handle h, uint32_t *sample, int64_t words);
 
 /* ---------------------------------------------------------------------------
  * Launch configuration (what the autotuner chooses). All fields 0 = automatic.
@@ -232,6 +250,13 @@ typedef struct {
                                 zero tile in shared memory. With 2 and 3 the consumer warps
                                 store a match only after the writer has published that its
                                 tile's zeros are written. */
+    int32_t screen;          /* kernel 2, packed text, prefix filter too large for shared
+                                memory: which screen picks the offsets whose filter bit is
+                                read from global memory: 0 = automatic (the sampled screen
+                                when the table has one, else the first-level filter),
+                                1 = the order-10 first-level filter in shared memory, 2 = the
+                                sampled screen (pfac_export_sample; 32 offsets per lane) */
+    int32_t reserved;        /* 0 */
 } pfac_config;
 
 /* Set (cfg != NULL) or reset (cfg == NULL) the launch configuration of a handle.

@@ -36,20 +36,20 @@ class PfacError(RuntimeError):
 
 
 class pfac_build_opts(C.Structure):
-    _fields_ = [("host_only", I32), ("filter_b", I32)]
+    _fields_ = [("host_only", I32), ("filter_b", I32), ("sample", I32)]
 
 
 class pfac_table_info(C.Structure):
     _fields_ = [("n_states", I64), ("n_patterns", I32), ("max_len", I32), ("min_len", I32),
                 ("filter_b", I32), ("n_duplicates", I64), ("table_bytes", I64), ("rows_bytes", I64),
                 ("skip_bytes", I64), ("filter_set", I64), ("has_skip", I32), ("rank_wide", I32),
-                ("device", I32), ("pad", I32)]
+                ("device", I32), ("sample_q", I32), ("sample_s", I32), ("pad", I32)]
 
 
 class pfac_config(C.Structure):
     _fields_ = [("kernel", I32), ("threads", I32), ("ctas_per_sm", I32), ("stages", I32), ("rank_in_smem", I32),
                 ("l2_persist", I32), ("walk_loads", I32), ("lane_offsets", I32), ("table_layout", I32),
-                ("row_loads", I32), ("text_smem", I32), ("zero_writer", I32)]
+                ("row_loads", I32), ("text_smem", I32), ("zero_writer", I32), ("screen", I32), ("reserved", I32)]
 
 
 _lib = None
@@ -68,6 +68,7 @@ _SIGS = {
     "pfac_info_ex": (C.c_int, [P, P]),
     "pfac_export": (C.c_int, [P, P, P, P]),
     "pfac_export_shortcuts": (C.c_int, [P, P, I64, P, I64, P, I64]),
+    "pfac_export_sample": (C.c_int, [P, P, I64]),
     "pfac_set_config": (C.c_int, [P, P]),
     "pfac_get_config": (C.c_int, [P, I64, P]),
     "pfac_pack": (C.c_int, [P, I64, P, P, P, P]),
@@ -149,11 +150,11 @@ def _patterns(patterns):
 # Calls with the C names.
 # ---------------------------------------------------------------------------
 
-def pfac_build(patterns, host_only: bool = False, filter_b: int = 0) -> int:
+def pfac_build(patterns, host_only: bool = False, filter_b: int = 0, sample: int = 0) -> int:
     """Build a table from ``(blob, offsets)`` or a list of byte strings; returns the handle."""
     L = lib()
     blob, ptrs, lengths, n = _patterns(patterns)
-    opts = pfac_build_opts(int(host_only), int(filter_b))
+    opts = pfac_build_opts(int(host_only), int(filter_b), int(sample))
     h = L.pfac_build_ex(ptrs.ctypes.data, lengths.ctypes.data, n, C.byref(opts))
     if not h:
         raise PfacError(L.pfac_last_error(), "pfac_build")
@@ -219,6 +220,16 @@ def pfac_export_shortcuts(h: int):
     _check(lib().pfac_export_shortcuts(h, ptr(skip), skip.size, ptr(filt), filt.size, ptr(dense), dense.size),
            "pfac_export_shortcuts")
     return skip, filt, dense
+
+
+def pfac_export_sample(h: int):
+    """(q, s, q-gram bit words) of a host-only handle's sampled screen; (0, 0, empty)
+    when it has none."""
+    info = pfac_info_ex(h)
+    q, s = info["sample_q"], info["sample_s"]
+    g = np.zeros(((1 << (2 * q)) // 32) if q else 0, dtype=np.uint32)
+    _check(lib().pfac_export_sample(h, g.ctypes.data if g.size else None, g.size), "pfac_export_sample")
+    return q, s, g
 
 
 def pfac_set_config(h: int, cfg: dict | None):
@@ -295,8 +306,8 @@ def pfac_debug_timeout_probe(d_status, limit_ns: int, stream=None):
 class Table:
     """Owns one table handle; destroys it when collected or closed."""
 
-    def __init__(self, patterns, host_only: bool = False, filter_b: int = 0):
-        self.h = pfac_build(patterns, host_only=host_only, filter_b=filter_b)
+    def __init__(self, patterns, host_only: bool = False, filter_b: int = 0, sample: int = 0):
+        self.h = pfac_build(patterns, host_only=host_only, filter_b=filter_b, sample=sample)
 
     @classmethod
     def from_file(cls, path: str, host_only: bool = False, filter_b: int = 0) -> "Table":

@@ -138,6 +138,7 @@ pfac::TiledConfig tiled_config(const pfac_config &c)
     t.lane_offsets = c.lane_offsets;
     t.l2_persist = c.l2_persist;
     t.zero_writer = c.zero_writer > 0 ? c.zero_writer - 1 : 0;
+    t.screen = c.screen;
     t.timeout_ns = 2000000000LL;
     return t;
 }
@@ -426,7 +427,7 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
     if (opts) o = *opts;
     pfac_table *h = new (std::nothrow) pfac_table();
     if (!h) { fail(PFAC_ERR_OOM); return nullptr; }
-    int rc = pfac::build_host_tables(patterns, lengths, n, o.filter_b, &h->host);
+    int rc = pfac::build_host_tables(patterns, lengths, n, o.filter_b, &h->host, o.sample >= 0);
     if (rc != PFAC_OK) { delete h; fail(rc); return nullptr; }
     const pfac::HostTables &T = h->host;
     h->rows_bytes = T.n_states * 16;
@@ -446,6 +447,7 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
              rank_bytes},
             {(const void **)&h->dt.dense, T.dense.data(), T.dense.size() * 4},
             {(const void **)&h->dt.filter1, T.filter1.data(), T.filter1.size() * 4},
+            {(const void **)&h->dt.sample, T.sample.data(), T.sample.size() * 4},
         };
         size_t total = 256;   // status word
         for (auto &p : parts) total += round256(p.bytes);
@@ -479,6 +481,8 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         h->dt.filter_b = T.filter_b;
         h->dt.filter1_b = T.filter1_b;
         h->dt.rank_wide = T.rank_wide;
+        h->dt.sample_q = T.sample_q;
+        h->dt.sample_s = T.sample_s;
         // The device copy is complete; the host keeps rows, ids and levels for export.
         pfac::TableVector<uint32_t>().swap(h->host.skip);
         std::vector<uint32_t>().swap(h->host.filter);
@@ -486,6 +490,7 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
         std::vector<uint32_t>().swap(h->host.rank32);
         std::vector<uint32_t>().swap(h->host.dense);
         std::vector<uint32_t>().swap(h->host.filter1);
+        std::vector<uint32_t>().swap(h->host.sample);
     }
     return h;
 }
@@ -540,6 +545,8 @@ int pfac_info_ex(pfac_handle h, pfac_table_info *info)
     i.has_skip = h->skip_bytes > 0;
     i.rank_wide = h->host.rank_wide;
     i.device = h->device;
+    i.sample_q = h->host.sample_q;
+    i.sample_s = h->host.sample_s;
     *info = i;
     return PFAC_OK;
 }
@@ -570,6 +577,16 @@ int pfac_export_shortcuts(pfac_handle h, uint32_t *skip, int64_t skip_words, uin
     return PFAC_OK;
 }
 
+int pfac_export_sample(pfac_handle h, uint32_t *sample, int64_t words)
+{
+    if (!h) return fail(PFAC_ERR_INVALID_ARG);
+    if (h->device >= 0) return fail(PFAC_ERR_UNSUPPORTED);
+    const std::vector<uint32_t> &G = h->host.sample;
+    if (sample && words < (int64_t)G.size()) return fail(PFAC_ERR_INVALID_ARG);
+    if (sample && !G.empty()) memcpy(sample, G.data(), G.size() * 4);
+    return PFAC_OK;
+}
+
 int pfac_set_config(pfac_handle h, const pfac_config *cfg)
 {
     if (!h) return fail(PFAC_ERR_INVALID_ARG);
@@ -579,7 +596,8 @@ int pfac_set_config(pfac_handle h, const pfac_config *cfg)
             cfg->stages < 0 || cfg->stages == 1 || cfg->stages > 8 || cfg->walk_loads < 0 ||
             (cfg->lane_offsets != 0 && cfg->lane_offsets != 16 && cfg->lane_offsets != 32) ||
             cfg->table_layout < 0 || cfg->table_layout > 2 || cfg->row_loads < 0 || cfg->row_loads > 2 ||
-            cfg->text_smem < 0 || cfg->text_smem > 1 || cfg->zero_writer < 0 || cfg->zero_writer > 3)
+            cfg->text_smem < 0 || cfg->text_smem > 1 || cfg->zero_writer < 0 || cfg->zero_writer > 3 ||
+            cfg->screen < 0 || cfg->screen > 2 || cfg->reserved != 0)
             return fail(PFAC_ERR_INVALID_ARG);
         if (cfg->kernel == 2 && !(h->skip_bytes > 0 && h->host.filter_b > 0)) return fail(PFAC_ERR_UNSUPPORTED);
         const int rc = ensure_paper_layout(h, cfg->table_layout);

@@ -52,8 +52,20 @@ constexpr int kSkipMaxLen = 16;
 // is dense[r]: the skip entry of the state the walk over w reaches at depth b, or an
 // entry with the special bit when a pattern ends within w (the answer then needs the
 // walk from the root).
-constexpr int kMaxFilterB = 12;
+constexpr int kMaxFilterB = 14;
 constexpr int kFilter1B = 10;      // order of the shared-memory first-level filter
+// Automatic order for large dictionaries without short patterns (see the builder).
+constexpr int kDeepFilterB = 14;
+constexpr int32_t kDeepFilterMinPatterns = 1 << 19;
+
+// Sampled screen: the q-grams (q = kSampleQ) at positions 0 .. kSampleS - 1 of every
+// pattern, one bit per q-gram (bit g = bit g mod 32 of word g / 32, base j of g in bits
+// 2j..2j+1). Built for tables whose filter lives in global memory and whose patterns
+// all have at least kSampleQ + kSampleS - 1 bases: a scan probes it at every
+// kSampleS-th offset, and an offset i can start a match only if the probe at the next
+// multiple of kSampleS at or after i finds its bit set.
+constexpr int kSampleQ = 13;
+constexpr int kSampleS = 4;
 
 // Allocator whose construction without a value leaves the element uninitialised: the
 // builder sizes its largest arrays with resize() and then writes every element from
@@ -89,11 +101,13 @@ struct HostTables {
     // b-mer whose first kFilter1B bases are w10, i.e. the order-kFilter1B filter itself.
     int32_t filter1_b = 0;
     std::vector<uint32_t> filter1;
+    int32_t sample_q = 0, sample_s = 0;   // 0 = no sampled screen
+    std::vector<uint32_t> sample;         // 4^sample_q bits
 };
 
 // Status codes match pfac.h.
 int build_host_tables(const char *const *patterns, const int32_t *lengths, int32_t n,
-                      int32_t filter_b_opt, HostTables *out);
+                      int32_t filter_b_opt, HostTables *out, bool with_sample = true);
 
 }  // namespace pfac
 
@@ -121,6 +135,8 @@ struct DeviceTable {
     int32_t filter1_b;         // 0 = no first-level filter
     int32_t rank_wide;
     int32_t *status;           // device status word (PFAC_OK or the first error)
+    const uint32_t *sample;    // sampled screen (4^sample_q bits), or nullptr
+    int32_t sample_q, sample_s;
 };
 
 struct TiledConfig {
@@ -131,6 +147,10 @@ struct TiledConfig {
     int32_t lane_offsets;      // offsets per consumer lane: 16 (default) or 32
     int32_t smem_table_bytes;  // < 0: keep the rank index in global memory
     int32_t l2_persist;        // > 0: access-policy window over the skip entries
+    int32_t screen;            // main filter in global memory, packed text: 0 = automatic
+                               // (the sampled screen when the table has one, else the
+                               // first-level filter), 1 = first-level filter, 2 = sampled
+                               // screen (when available)
     int32_t zero_writer;       // dense packed scans, 32 offsets per lane: 0 = consumer warps
                                // store their zeros, 1 = a writer warp with 16-byte stores,
                                // 2 = a writer warp with TMA bulk stores of a zero tile

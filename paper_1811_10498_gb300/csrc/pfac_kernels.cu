@@ -529,11 +529,43 @@ __device__ __forceinline__ uint32_t filter_bits_screened(const DeviceTable &T, u
     return pend;
 }
 
-// L1F (packed text, main filter in global memory): the first-level filter of order
-// kFilter1B sits in shared memory at offset 0 and screens every offset first.
+// The sampled screen of a lane's 32 offsets (packed text, window bases 0 .. 47 in x0, x1,
+// x2): probe m reads the q-gram at window offset 4m (m = 0 .. 8; the ninth is the next
+// lane's first, taken by shuffle, and probed directly by the warp's last lane). Offset r
+// can start a match only if the probe at 4 * ceil(r / 4) is set (every pattern's q-gram
+// at position (-i) mod 4 is in the set), so the result marks offset 0 with probe 0,
+// offsets 4m-3 .. 4m with probe m, and 29 .. 31 with probe 8. Probes past the text end
+// read bases that are not the text's: they can only add offsets, which the exact prefix
+// filter then rejects.
+__device__ __forceinline__ uint32_t sampled_candidates(const DeviceTable &T, uint32_t x0, uint32_t x1, uint32_t x2,
+                                                       int lane)
+{
+    static_assert(kSampleS == 4, "probes every 4th offset of a lane's 32");
+    const uint32_t qmask = (1u << (2 * kSampleQ)) - 1u;
+    uint32_t cand = 0, p0 = 0;
+#pragma unroll
+    for (int m = 0; m < 8; m++) {
+        const int j = 4 * m;
+        const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
+        const uint32_t g = win & qmask;
+        const uint32_t bit = (__ldg(T.sample + (g >> 5)) >> (g & 31u)) & 1u;
+        if (m == 0) p0 = bit;
+        cand |= (0u - bit) & (m == 0 ? 1u : (0xFu << (4 * m - 3)));
+    }
+    uint32_t p8 = __shfl_down_sync(0xFFFFFFFFu, p0, 1);
+    if (lane == 31) {
+        const uint32_t g = x2 & qmask;
+        p8 = (__ldg(T.sample + (g >> 5)) >> (g & 31u)) & 1u;
+    }
+    return cand | ((0u - p8) & 0xE0000000u);
+}
+
+// SCR (packed text, main filter in global memory): 1 = the first-level filter of order
+// kFilter1B sits in shared memory at offset 0 and screens every offset first; 2 = the
+// sampled screen (global memory) picks the offsets whose main-filter bit is read.
 // ZW (dense packed scans): 0 = each consumer warp stores its own zeros; 1 or 2 = a zero
 // writer warp (warp consumers + 1) stores them (see zero_writer).
-template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW, bool ALL = false, bool L1F = false, int ZW = 0>
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW, bool ALL = false, int SCR = 0, int ZW = 0>
 __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
 {
     static_assert(ZW == 0 || (PACKED && !COMPACT && !ALL), "a zero writer serves dense packed scans");
@@ -579,11 +611,11 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             for (int64_t i = (bytes & ~(int64_t)15) + tid; i < bytes; i += blockDim.x) dst[i] = src[i];
         };
         const int64_t words = B >= 3 ? ((int64_t)1 << (2 * B)) / 32 : 1;
-        if (FSMEM || L1F) {
+        if (FSMEM || SCR == 1) {
             // the filter's words go in bit-reversed (see filter_bits): the main filter, or
             // the first-level one
-            const uint32_t *src = L1F ? T.filter1 : T.filter;
-            const int64_t fwords = L1F ? ((int64_t)1 << (2 * kFilter1B)) / 32 : words;
+            const uint32_t *src = SCR == 1 ? T.filter1 : T.filter;
+            const int64_t fwords = SCR == 1 ? ((int64_t)1 << (2 * kFilter1B)) / 32 : words;
             uint32_t *dst = reinterpret_cast<uint32_t *>(smem + P.off_filter);
             for (int64_t i = 4 * (int64_t)tid; i + 4 <= fwords; i += 4 * (int64_t)blockDim.x) {
                 const uint4 v = __ldg(reinterpret_cast<const uint4 *>(src + i));
@@ -672,10 +704,13 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             }
             const uint32_t fast = bad ? clear_runs(bad, B) & valid : valid;   // the b-mer is readable
             uint32_t pend;
-            if constexpr (L1F) {
+            if constexpr (SCR == 1) {
                 const uint32_t bmask1 = (1u << (2 * kFilter1B)) - 1u;
                 pend = filter_bits<true, LW>(T, sf, x0, x1, x2, bmask1) & fast;
                 pend = filter_bits_screened<LW>(T, x0, x1, x2, bmask, pend);
+            } else if constexpr (SCR == 2) {
+                static_assert(LW == 32, "the sampled screen covers a lane's 32 offsets");
+                pend = filter_bits_screened<LW>(T, x0, x1, x2, bmask, sampled_candidates(T, x0, x1, x2, lane) & fast);
             } else {
                 pend = filter_bits<FSMEM, LW>(T, sf, x0, x1, x2, bmask) & fast;
             }
@@ -863,7 +898,8 @@ static int stages_of(const TiledConfig &cfg, bool packed) { return cfg.stages > 
 struct SmemPlan {
     int64_t filter_bytes, rank_bytes;   // bytes copied into shared memory (0 = global)
     int64_t total;
-    bool l1f;                           // filter_bytes hold the first-level filter
+    int scr;                            // 1: filter_bytes hold the first-level filter;
+                                        // 2: the sampled screen (global memory) is used
     int zw;                             // zero writer (0 = the consumer warps)
     int64_t zero_chunk;                 // bytes of the bulk-store zero tile (zw == 2)
 };
@@ -891,18 +927,21 @@ static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool pac
     }
     pl.zw = zw;
     pl.filter_bytes = total(fbytes, 0) <= limit ? fbytes : 0;
-    if (!pl.filter_bytes && packed && t.filter1_b == kFilter1B && t.filter1) {
+    const bool sampled = t.sample && t.sample_q == kSampleQ && t.sample_s == kSampleS && LW == 32;
+    if (!pl.filter_bytes && packed && sampled && cfg.screen != 1) {
+        pl.scr = 2;
+    } else if (!pl.filter_bytes && packed && t.filter1_b == kFilter1B && t.filter1 && cfg.screen != 2) {
         const int64_t f1 = ((int64_t)1 << (2 * kFilter1B)) / 8;
         if (total(f1, 0) <= limit) {
             pl.filter_bytes = f1;
-            pl.l1f = true;
+            pl.scr = 1;
         }
     }
     if (zw == 2 && total(pl.filter_bytes, 0) > limit) {
         zw = pl.zw = 1;                  // no room for a zero tile: 16-byte stores instead
         zb = 0;
     }
-    pl.rank_bytes = (!pl.l1f && cfg.smem_table_bytes >= 0 && total(pl.filter_bytes, rbytes) <= limit) ? rbytes : 0;
+    pl.rank_bytes = (pl.scr == 0 && cfg.smem_table_bytes >= 0 && total(pl.filter_bytes, rbytes) <= limit) ? rbytes : 0;
     if (zw == 2) {
         for (int64_t c = 16384; c > 2048; c >>= 1) {
             zb = c;
@@ -993,23 +1032,27 @@ static cudaError_t allow_max_smem(const void *kern, const DeviceProps &dp)
     return e;
 }
 
-template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, bool ALL, bool L1F>
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, bool ALL, int SCR>
 static void (*scan_kernel_for(bool lw32, int zw))(const ScanParams)
 {
     if constexpr (PACKED && !COMPACT && !ALL) {
-        if (zw == 1) return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, L1F, 1>;
-        if (zw == 2) return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, L1F, 2>;
+        if (zw == 1) return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, SCR, 1>;
+        if (zw == 2) return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, SCR, 2>;
     }
-    return lw32 ? scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, L1F>
-                : scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 16, ALL, L1F>;
+    if constexpr (SCR == 2) {
+        return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, SCR>;
+    } else {
+        return lw32 ? scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, SCR>
+                    : scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 16, ALL, SCR>;
+    }
 }
 
-template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, bool ALL, bool L1F = false>
+template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, bool ALL, int SCR = 0>
 static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t smem, int tail_grid, cudaStream_t st,
                          const TiledConfig &cfg, const DeviceProps &dp, int zw)
 {
     const bool lw32 = lane_width_of(cfg) == 32;
-    auto kern = scan_kernel_for<PACKED, COMPACT, FSMEM, RANK16, ALL, L1F>(lw32, zw);
+    auto kern = scan_kernel_for<PACKED, COMPACT, FSMEM, RANK16, ALL, SCR>(lw32, zw);
     if ((int64_t)smem > (int64_t)dp.smem_optin) return PFAC_ERR_UNSUPPORTED;
     if (allow_max_smem((const void *)kern, dp) != cudaSuccess) return PFAC_ERR_CUDA;
     if (launch_with_policy(kern, P, grid, threads, smem, st, cfg, dp) != cudaSuccess) return PFAC_ERR_CUDA;
@@ -1020,14 +1063,19 @@ static int launch_scan_t(const ScanParams &P, int grid, int threads, uint32_t sm
 template <bool PACKED, bool COMPACT, bool ALL = false>
 static int launch_scan_w(const ScanParams &P, bool fsmem, bool rank16, int grid, int threads, uint32_t smem,
                          int tail_grid, cudaStream_t st, const TiledConfig &cfg, const DeviceProps &dp,
-                         bool l1f = false, int zw = 0)
+                         int scr = 0, int zw = 0)
 {
     if constexpr (PACKED) {
-        if (l1f)
-            return rank16 ? launch_scan_t<PACKED, COMPACT, false, true, ALL, true>(P, grid, threads, smem, tail_grid,
-                                                                                 st, cfg, dp, zw)
-                          : launch_scan_t<PACKED, COMPACT, false, false, ALL, true>(P, grid, threads, smem, tail_grid,
-                                                                                  st, cfg, dp, zw);
+        if (scr == 1)
+            return rank16 ? launch_scan_t<PACKED, COMPACT, false, true, ALL, 1>(P, grid, threads, smem, tail_grid,
+                                                                              st, cfg, dp, zw)
+                          : launch_scan_t<PACKED, COMPACT, false, false, ALL, 1>(P, grid, threads, smem, tail_grid,
+                                                                               st, cfg, dp, zw);
+        if (scr == 2)
+            return rank16 ? launch_scan_t<PACKED, COMPACT, false, true, ALL, 2>(P, grid, threads, smem, tail_grid,
+                                                                              st, cfg, dp, zw)
+                          : launch_scan_t<PACKED, COMPACT, false, false, ALL, 2>(P, grid, threads, smem, tail_grid,
+                                                                               st, cfg, dp, zw);
     }
     if (fsmem)
         return rank16 ? launch_scan_t<PACKED, COMPACT, true, true, ALL>(P, grid, threads, smem, tail_grid, st, cfg, dp, zw)
@@ -1092,19 +1140,19 @@ int launch_tiled(const DeviceTable &t, const void *text, bool packed, int64_t n,
     // a queued offset codes its tile round in 32 - kRelBits bits
     if (packed && (P.n_tiles + grid - 1) / grid > ((int64_t)1 << (32 - kRelBits))) return PFAC_ERR_UNSUPPORTED;
     const int tail_grid = dp.num_sms * 4;
-    const bool fsmem = pl.filter_bytes > 0 && !pl.l1f;
-    const bool l1f = pl.l1f;
+    const bool fsmem = pl.filter_bytes > 0 && pl.scr == 0;
+    const int scr = pl.scr;
     const bool rank16 = !t.rank_wide;
     if (all_matches) {   // the match list of every pattern on every walk (packed text only)
         if (!packed || !compact) return PFAC_ERR_INVALID_ARG;
         return launch_scan_w<true, true, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp,
-                                               l1f);
+                                               scr);
     }
     if (packed)
         return compact ? launch_scan_w<true, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp,
-                                                   l1f)
+                                                   scr)
                        : launch_scan_w<true, false>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp,
-                                                    l1f, zw);
+                                                    scr, zw);
     return compact ? launch_scan_w<false, true>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp)
                    : launch_scan_w<false, false>(P, fsmem, rank16, grid, cfg.threads, L.total, tail_grid, st, cfg, dp);
 }

@@ -177,7 +177,7 @@ int run_parallel(size_t count, int threads, Fn fn)
 }  // namespace
 
 int build_host_tables(const char *const *patterns, const int32_t *lengths, int32_t n,
-                      int32_t filter_b_opt, HostTables *out)
+                      int32_t filter_b_opt, HostTables *out, bool with_sample)
 {
     if (n <= 0 || !patterns || !lengths || !out) return PFAC_ERR_INVALID_ARG;
     if (filter_b_opt > kMaxFilterB) return PFAC_ERR_INVALID_ARG;
@@ -395,10 +395,63 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
         // Automatic order: about log4(patterns) + 2.2, so that a few percent of the
         // b-mers of a random text pass (a b-mer passes when it is a path of the trie,
         // about min(1, patterns / 4^b) of them), between 6 and 12.
+        // Dictionaries of kDeepFilterMinPatterns patterns or more, none shorter than
+        // kDeepFilterB, get the order-kDeepFilterB filter: too large for shared memory
+        // either way, and the deeper the order, the fewer offsets start a walk.
         const double auto_b = std::ceil(std::log((double)n) / std::log(4.0) + 2.2);
-        const int32_t b = filter_b_opt == 0 ? (int32_t)std::min(12.0, std::max(6.0, auto_b))
-                                            : (filter_b_opt < 0 ? 0 : filter_b_opt);
-        if (b > 0 && !T.skip.empty()) {
+        int32_t b = filter_b_opt == 0 ? (int32_t)std::min(12.0, std::max(6.0, auto_b))
+                                      : (filter_b_opt < 0 ? 0 : filter_b_opt);
+        if (filter_b_opt == 0 && n >= kDeepFilterMinPatterns && min_len >= kDeepFilterB) b = kDeepFilterB;
+        if (b > 0 && !T.skip.empty() && min_len >= b) {
+            // No pattern ends before depth b, so no bit stands for a range of b-mers: the
+            // set bits are the codes of the states of depth b, one dense entry each (the
+            // special entry for a state where a pattern ends).
+            T.filter_b = b;
+            const size_t E = (size_t)1 << (2 * b);
+            const int64_t lo = T.level[(size_t)b], hi = T.level[(size_t)b + 1];
+            std::vector<uint64_t> code((size_t)hi, 0);      // b-mer code << 32 | state
+            for (int32_t d = 0; d < b; d++)
+                for (int64_t st = T.level[(size_t)d]; st < T.level[(size_t)d + 1]; st++)
+                    for (int c = 0; c < 4; c++) {
+                        const uint32_t e = (uint32_t)T.rows[(size_t)(4 * st + c)];
+                        if (e) code[e & 0x7FFFFFFFu] = code[(size_t)st] | ((uint64_t)c << (32 + 2 * d));
+                    }
+            std::vector<uint64_t> at_b((size_t)(hi - lo));
+            for (int64_t st = lo; st < hi; st++) at_b[(size_t)(st - lo)] = code[(size_t)st] | (uint64_t)st;
+            std::vector<uint64_t>().swap(code);
+            std::sort(at_b.begin(), at_b.end());
+            const size_t words = E >= 32 ? E / 32 : 1;
+            T.filter.assign(words, 0u);
+            T.dense.resize(4 * at_b.size());
+            for (size_t r = 0; r < at_b.size(); r++) {
+                const uint32_t w = (uint32_t)(at_b[r] >> 32), st = (uint32_t)at_b[r];
+                T.filter[w >> 5] |= 1u << (w & 31);
+                if (T.out_id[st]) {
+                    const uint32_t special[4] = {0u, kSkipSpecial, 0u, 0u};
+                    memcpy(&T.dense[4 * r], special, 16);
+                } else {
+                    memcpy(&T.dense[4 * r], &T.skip[(size_t)(4 * (int64_t)st)], 16);
+                }
+            }
+            std::vector<uint32_t> rank(words, 0u);
+            uint64_t count = 0;
+            for (size_t w = 0; w < words; w++) {
+                rank[w] = (uint32_t)count;
+                count += (uint64_t)__builtin_popcount(T.filter[w]);
+            }
+            T.rank_wide = count > 65535;
+            if (T.rank_wide) T.rank32.swap(rank);
+            else T.rank16.assign(rank.begin(), rank.end());
+            if (b > kFilter1B) {
+                const size_t E1 = (size_t)1 << (2 * kFilter1B);
+                T.filter1_b = kFilter1B;
+                T.filter1.assign(E1 / 32, 0u);
+                for (const uint64_t v : at_b) {
+                    const size_t w1 = (size_t)(v >> 32) & (E1 - 1);   // the first kFilter1B bases
+                    T.filter1[w1 >> 5] |= 1u << (w1 & 31);
+                }
+            }
+        } else if (b > 0 && !T.skip.empty()) {
             T.filter_b = b;
             const size_t E = (size_t)1 << (2 * b);
             const uint32_t kNone = 0xFFFFFFFFu, kSpecialVal = 0xFFFFFFFEu;
@@ -469,6 +522,26 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
                         const size_t w1 = w & (E1 - 1);   // the first kFilter1B bases
                         T.filter1[w1 >> 5] |= 1u << (w1 & 31);
                     }
+            }
+        }
+
+        // ---- step 3d: sampled screen -----------------------------------------------
+        // When every pattern has at least kSampleQ + kSampleS - 1 bases, a match at
+        // offset i puts the pattern's q-gram at position d = (-i) mod s at the offset
+        // i + d, a multiple of s. So a bit set of the q-grams at positions 0 .. s-1 of
+        // every pattern, probed at every s-th offset, lists a superset of the offsets
+        // where a pattern can start (the s offsets up to each probe whose q-gram is set).
+        if (with_sample && T.filter_b > kFilter1B && min_len >= kSampleQ + kSampleS - 1) {
+            T.sample_q = kSampleQ;
+            T.sample_s = kSampleS;
+            T.sample.assign(((size_t)1 << (2 * kSampleQ)) / 32, 0u);
+            for (int32_t j = 0; j < n; j++) {
+                const unsigned char *p = (const unsigned char *)patterns[j];
+                for (int d = 0; d < kSampleS; d++) {
+                    uint32_t g = 0;
+                    for (int k = 0; k < kSampleQ; k++) g |= (uint32_t)base_code(p[d + k]) << (2 * k);
+                    T.sample[g >> 5] |= 1u << (g & 31);
+                }
             }
         }
         return PFAC_OK;

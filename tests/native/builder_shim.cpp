@@ -11,14 +11,15 @@
 
 extern "C" {
 
-void *shim_build(const char *const *patterns, const int32_t *lengths, int32_t n, int32_t filter_b, int32_t *status)
+void *shim_build(const char *const *patterns, const int32_t *lengths, int32_t n, int32_t filter_b, int32_t sample,
+                 int32_t *status)
 {
     pfac::HostTables *T = new (std::nothrow) pfac::HostTables();
     if (!T) {
         *status = PFAC_ERR_OOM;
         return nullptr;
     }
-    *status = pfac::build_host_tables(patterns, lengths, n, filter_b, T);
+    *status = pfac::build_host_tables(patterns, lengths, n, filter_b, T, sample >= 0);
     if (*status != PFAC_OK) {
         delete T;
         return nullptr;
@@ -48,6 +49,15 @@ void shim_export(void *h, int32_t *rows, int32_t *out_id, int64_t *level)
     memcpy(rows, T.rows.data(), T.rows.size() * 4);
     memcpy(out_id, T.out_id.data(), T.out_id.size() * 4);
     memcpy(level, T.level.data(), T.level.size() * 8);
+}
+
+// sample_q, sample_s, and the sampled screen's words (when `sample` is not NULL)
+void shim_export_sample(void *h, int32_t *qs, uint32_t *sample)
+{
+    const pfac::HostTables &T = *(const pfac::HostTables *)h;
+    qs[0] = T.sample_q;
+    qs[1] = T.sample_s;
+    if (sample && !T.sample.empty()) memcpy(sample, T.sample.data(), T.sample.size() * 4);
 }
 
 void shim_export_shortcuts(void *h, uint32_t *skip, uint32_t *filter, uint32_t *dense)

@@ -60,6 +60,22 @@ MUTANTS = {
     "filter_pattern_end_not_inherited": (
         "seen[child] = (uint8_t)(seen[(size_t)s] | (e >> 31));",
         "seen[child] = (uint8_t)(e >> 31);"),
+    # Without short patterns: dense entries follow the b-mer codes, not the state ids.
+    "deep_filter_dense_in_state_order": (
+        "            std::sort(at_b.begin(), at_b.end());\n",
+        ""),
+    # Without short patterns: a state's code holds its first base in the low bits.
+    "deep_filter_code_reversed": (
+        "code[(size_t)st] | ((uint64_t)c << (32 + 2 * d));",
+        "code[(size_t)st] | ((uint64_t)c << (32 + 2 * (b - 1 - d)));"),
+    # The sampled screen holds the q-grams at every position 0 .. s-1.
+    "sample_misses_last_position": (
+        "for (int d = 0; d < kSampleS; d++) {",
+        "for (int d = 0; d < kSampleS - 1; d++) {"),
+    # ... with the first base of a q-gram in its low bits.
+    "sample_qgram_reversed": (
+        "g |= (uint32_t)base_code(p[d + k]) << (2 * k);",
+        "g |= (uint32_t)base_code(p[d + k]) << (2 * (kSampleQ - 1 - k));"),
 }
 
 
@@ -71,17 +87,18 @@ class BuilderOnly:
         L = C.CDLL(so)
         P, I32 = C.c_void_p, C.c_int32
         L.shim_build.restype = P
-        L.shim_build.argtypes = [P, P, I32, I32, P]
+        L.shim_build.argtypes = [P, P, I32, I32, I32, P]
         L.shim_destroy.argtypes = [P]
         L.shim_info.argtypes = [P, P]
         L.shim_export.argtypes = [P, P, P, P]
         L.shim_export_shortcuts.argtypes = [P, P, P, P]
+        L.shim_export_sample.argtypes = [P, P, P]
         self.L = L
 
-    def pfac_build(self, patterns, host_only=True, filter_b=0):
+    def pfac_build(self, patterns, host_only=True, filter_b=0, sample=0):
         blob, ptrs, lengths, n = _binding._patterns(patterns)
         st = C.c_int32(0)
-        h = self.L.shim_build(ptrs.ctypes.data, lengths.ctypes.data, n, filter_b, C.byref(st))
+        h = self.L.shim_build(ptrs.ctypes.data, lengths.ctypes.data, n, filter_b, sample, C.byref(st))
         if not h:
             raise _binding.PfacError(st.value, "build")
         self._keep = blob
@@ -104,6 +121,14 @@ class BuilderOnly:
         self.L.shim_export(h, rows.ctypes.data, out_id.ctypes.data, level.ctypes.data)
         return rows, out_id, level
 
+    def pfac_export_sample(self, h):
+        qs = np.zeros(2, dtype=np.int32)
+        self.L.shim_export_sample(h, qs.ctypes.data, None)
+        q, smp = int(qs[0]), int(qs[1])
+        g = np.zeros(((1 << (2 * q)) // 32) if q else 1, dtype=np.uint32)
+        self.L.shim_export_sample(h, qs.ctypes.data, g.ctypes.data)
+        return q, smp, (g if q else g[:0])
+
     def pfac_export_shortcuts(self, h):
         i = self.pfac_info_ex(h)
         S, b, F = i["n_states"], i["filter_b"], i["filter_set"]
@@ -124,6 +149,10 @@ CHECKS = [
     *[(f"chain_cap_{i}", (lambda c=c: thb.test_skip_entries_at_the_chain_cap(c)))
       for i, c in enumerate([(15, 16, 17, 33), (16, 32, 48), (1, 17, 34, 40), (31, 32, 47), ()])],
     ("threaded_numbering", lambda: thb.test_threaded_build_numbers_prefixes_by_length_then_lexicographically()),
+    *[(f"long_patterns_{s}_{b}", (lambda s=s, b=b: thb.test_filter_when_no_pattern_ends_inside_a_bmer(s, b)))
+      for s, b in [(7, 4), (8, 6), (9, 7)]],
+    ("sampled_screen", lambda: thb.test_sampled_screen_definition(11)),
+    ("order14", lambda: thb.test_order_14_filter_of_long_patterns()),
 ]
 
 

@@ -162,6 +162,120 @@ def test_skip_filter_dense_definition(seed, b):
             assert np.array_equal(dense[r], skip[new[st]])
 
 
+@pytest.mark.parametrize("seed,b", [(7, 4), (8, 6), (9, 7)])
+def test_filter_when_no_pattern_ends_inside_a_bmer(seed, b):
+    """Patterns no shorter than b (the builder's path without range fills): filter bits,
+    dense entries in b-mer order and skip entries against their definitions."""
+    rng = datagen.rng_for(seed)
+    text = datagen.iid_text(4000, rng)
+    blob, offs = datagen.pattern_set(text, rng, 120, (b, b + 20), 0.6)
+    go, term = oracle.Trie((blob, offs)).export()
+    order = bfs_relabel(go)
+    new = np.empty(go.shape[0], dtype=np.int64)
+    new[np.array(order)] = np.arange(go.shape[0])
+    h = b_.pfac_build((blob, offs), host_only=True, filter_b=b)
+    try:
+        skip, filt, dense = b_.pfac_export_shortcuts(h)
+        info = b_.pfac_info_ex(h)
+    finally:
+        b_.pfac_destroy(h)
+    assert info["min_len"] >= b and info["filter_b"] == b
+    bits, state = reference_shortcuts(go, term, b)
+    got = [(int(filt[w >> 5]) >> (w & 31)) & 1 for w in range(1 << (2 * b))]
+    assert got == bits
+    on = [st for st in state if st is not None]
+    assert dense.shape[0] == len(on) == info["filter_set"]
+    for r, st in enumerate(on):
+        if st == "special":                      # a pattern of exactly b bases ends there
+            assert dense[r, 1] & (1 << 9)
+        else:
+            assert np.array_equal(dense[r], skip[new[st]])
+
+
+def qgram_codes(pats, q, start):
+    """Code of each pattern's q-gram at position `start` (base j in bits 2j..2j+1)."""
+    lut = np.zeros(256, dtype=np.uint64)
+    for i, ch in enumerate(b"ACGT"):
+        lut[ch] = i
+    codes = []
+    for p in pats:
+        a = lut[np.frombuffer(p[start:start + q], dtype=np.uint8)]
+        codes.append(int((a << (2 * np.arange(q, dtype=np.uint64))).sum()))
+    return codes
+
+
+def set_bits(words):
+    """Indices of the set bits of a little-endian bit array held in uint32 words."""
+    nz = np.flatnonzero(words)
+    out = [int(w) * 32 + j for w in nz for j in range(32) if (int(words[w]) >> j) & 1]
+    return np.array(out, dtype=np.int64)
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_sampled_screen_definition(seed):
+    """The sampled screen of a table whose filter lives in global memory and whose
+    patterns have 16 bases or more: exactly the 13-grams at positions 0..3 of every
+    pattern. Tables with a shorter pattern, a filter of order 10 or less, or the option
+    off have none."""
+    rng = datagen.rng_for(seed)
+    text = datagen.iid_text(20000, rng)
+    blob, offs = datagen.pattern_set(text, rng, 400, (16, 40), 0.5)
+    pats = datagen.pattern_list(blob, offs)
+    h = b_.pfac_build(pats, host_only=True, filter_b=11)
+    try:
+        q, smp, g = b_.pfac_export_sample(h)
+    finally:
+        b_.pfac_destroy(h)
+    assert (q, smp) == (13, 4) and g.size == (1 << 26) // 32
+    want = sorted({c for d in range(smp) for c in qgram_codes(pats, q, d)})
+    assert set_bits(g).tolist() == want
+    for kw, ps in [(dict(filter_b=11), pats + [pats[0][:15]]), (dict(filter_b=10), pats),
+                   (dict(filter_b=11, sample=-1), pats)]:
+        h = b_.pfac_build(ps, host_only=True, **kw)
+        try:
+            assert b_.pfac_export_sample(h)[0] == 0, kw
+        finally:
+            b_.pfac_destroy(h)
+
+
+def test_order_14_filter_of_long_patterns():
+    """An order-14 filter (the automatic order for large sets without short patterns) of
+    a set with patterns of 14-40 bases: its set bits are the codes of the patterns'
+    14-base prefixes, and dense entry r is the skip entry of the state that the r-th of
+    them (in code order) reaches, or the special entry when a 14-base pattern ends
+    there."""
+    rng = datagen.rng_for(21)
+    text = datagen.iid_text(50000, rng)
+    blob, offs = datagen.pattern_set(text, rng, 3000, (14, 40), 0.5)
+    pats = datagen.pattern_list(blob, offs)
+    h = b_.pfac_build(pats, host_only=True, filter_b=14)
+    try:
+        rows, out_id, _ = b_.pfac_export(h)
+        skip, filt, dense = b_.pfac_export_shortcuts(h)
+        info = b_.pfac_info_ex(h)
+    finally:
+        b_.pfac_destroy(h)
+    assert info["filter_b"] == 14
+    lut = {ch: i for i, ch in enumerate(b"ACGT")}
+    by_code = {}
+    for p in pats:
+        s, code = 0, 0
+        for j in range(14):
+            c = lut[p[j]]
+            code |= c << (2 * j)
+            s = int(rows[s, c]) & 0x7FFFFFFF
+        by_code[code] = s
+    codes = sorted(by_code)
+    assert set_bits(filt).tolist() == codes
+    assert dense.shape[0] == len(codes) == info["filter_set"]
+    assert any(len(p) == 14 for p in pats)
+    for r, code in enumerate(codes):
+        if out_id[by_code[code]]:
+            assert dense[r, 1] & (1 << 9)
+        else:
+            assert np.array_equal(dense[r], skip[by_code[code]])
+
+
 @pytest.mark.parametrize("cuts", [(15, 16, 17, 33), (16, 32, 48), (1, 17, 34, 40), (31, 32, 47), ()])
 def test_skip_entries_at_the_chain_cap(cuts):
     """Single-child chains far longer than the 16-base cap, with pattern ends just
