@@ -98,6 +98,27 @@ typedef struct {
 pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, int32_t n,
                           const pfac_build_opts *opts);
 
+/* Build the same table on the GPU from patterns already in device memory (the paper
+ * builds its table on the host, Section V-A; this is the same insertion-order trie with
+ * the same breadth-first numbering, computed one depth at a time: at depth d every
+ * pattern longer than d marks the pair (its state, its base d), and a prefix sum over
+ * the marks, state by state and base by base, numbers the new states).
+ *   d_blob[...]        : DEVICE bytes of all patterns, concatenated (ASCII A/C/G/T)
+ *   d_offsets[n + 1]   : DEVICE int64 offsets: pattern j is d_blob[d_offsets[j] ..
+ *                        d_offsets[j + 1]); the caller guarantees they lie in d_blob
+ *   opts               : as for pfac_build_ex (filter_b, sample); host_only must be 0
+ *   stream             : the construction runs on it and the call returns when it is done
+ * The handle's tables (rows, ids, levels, skip entries, prefix filter, rank index, dense
+ * entries, first-level filter, sampled screen) equal, element for element, those of
+ * pfac_build_ex on the same patterns; the handle is used and destroyed like any other.
+ * Device scratch of about 20 bytes per pattern base plus 16 per pattern is allocated and
+ * freed inside the call. Returns NULL on error with pfac_last_error():
+ * PFAC_ERR_INVALID_ARG (n <= 0, host pointers, host_only, an offset going backwards),
+ * PFAC_ERR_EMPTY_PATTERN, PFAC_ERR_BAD_SYMBOL, PFAC_ERR_TOO_MANY_STATES, PFAC_ERR_OOM or
+ * PFAC_ERR_CUDA. */
+pfac_handle pfac_build_device(const uint8_t *d_blob, const int64_t *d_offsets, int32_t n,
+                              const pfac_build_opts *opts, void *stream);
+
 /* File front end (the paper's host program reads its patterns and its text from files,
  * Section V-B, Figs. 4 and 5).
  *
@@ -167,9 +188,10 @@ int pfac_info_ex(pfac_handle h, pfac_table_info *info);
  * Any output may be NULL. S = n_states from pfac_info. */
 int pfac_export(pfac_handle h, int32_t *rows, int32_t *out_id, int64_t *level);
 
-/* Copy the device-side encodings of a host-only handle (pfac_build_opts.host_only =
- * 1) for inspection; a handle with a device copy has dropped its host copy and gives
- * PFAC_ERR_UNSUPPORTED. All three describe the same trie as pfac_export:
+/* Copy the device-side encodings of a handle for inspection (from the host copy of a
+ * host-only handle, else from the device copy, synchronously). All three describe the
+ * same trie as pfac_export (which, for a handle built by pfac_build_device, also reads
+ * the device copy):
  *   skip[4*S]      : per state s, (label, meta, last, node): the chain of single-child
  *                    edges below s. meta bits 0..4 = chain length L (0..16), bit 8 = s
  *                    is terminal, bit 10 = the chain's last state is terminal; label
@@ -186,8 +208,8 @@ int pfac_export(pfac_handle h, int32_t *rows, int32_t *out_id, int64_t *level);
 int pfac_export_shortcuts(pfac_handle h, uint32_t *skip, int64_t skip_words, uint32_t *filter,
                           int64_t filter_words, uint32_t *dense, int64_t dense_words);
 
-/* Copy the sampled screen of a host-only handle (pfac_build_opts.host_only = 1; a handle
- * with a device copy gives PFAC_ERR_UNSUPPORTED): 4^q bits (q = sample_q of
+/* Copy the sampled screen of a handle (from its host copy, or from its device copy when
+ * it has one): 4^q bits (q = sample_q of
  * pfac_info_ex; bit g = bit g mod 32 of word g / 32, base j of g in bits 2j..2j+1), set
  * for the q-grams at positions 0 .. s-1 (s = sample_s) of every pattern. The builder
  * makes it for tables whose prefix filter is of order 11 or more and whose patterns all

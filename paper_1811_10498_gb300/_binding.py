@@ -59,6 +59,7 @@ _SIGS = {
     "pfac_build": (P, [P, P, I32]),
     "pfac_build_ex": (P, [P, P, I32, P]),
     "pfac_build_file": (P, [C.c_char_p, P]),
+    "pfac_build_device": (P, [P, P, I32, P, P]),
     "pfac_read_text_file": (C.c_int, [C.c_char_p, I32, P, I64, P]),
     "pfac_last_error": (C.c_int, []),
     "pfac_error_string": (C.c_char_p, [C.c_int]),
@@ -158,6 +159,17 @@ def pfac_build(patterns, host_only: bool = False, filter_b: int = 0, sample: int
     h = L.pfac_build_ex(ptrs.ctypes.data, lengths.ctypes.data, n, C.byref(opts))
     if not h:
         raise PfacError(L.pfac_last_error(), "pfac_build")
+    return h
+
+
+def pfac_build_device(d_blob, d_offsets, filter_b: int = 0, sample: int = 0, stream=None) -> int:
+    """Build a table on the GPU from device tensors: the patterns' bytes concatenated
+    (uint8) and int64 offsets (n + 1 entries)."""
+    n = int(d_offsets.numel()) - 1
+    opts = pfac_build_opts(0, int(filter_b), int(sample))
+    h = lib().pfac_build_device(_dptr(d_blob), _dptr(d_offsets), n, C.byref(opts), _stream(stream))
+    if not h:
+        raise PfacError(lib().pfac_last_error(), "pfac_build_device")
     return h
 
 
@@ -308,6 +320,13 @@ class Table:
 
     def __init__(self, patterns, host_only: bool = False, filter_b: int = 0, sample: int = 0):
         self.h = pfac_build(patterns, host_only=host_only, filter_b=filter_b, sample=sample)
+
+    @classmethod
+    def from_device(cls, d_blob, d_offsets, filter_b: int = 0, sample: int = 0, stream=None) -> "Table":
+        """A table built on the GPU (pfac_build_device) from device tensors."""
+        t = cls.__new__(cls)
+        t.h = pfac_build_device(d_blob, d_offsets, filter_b=filter_b, sample=sample, stream=stream)
+        return t
 
     @classmethod
     def from_file(cls, path: str, host_only: bool = False, filter_b: int = 0) -> "Table":

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpfac.so")
 SOURCES = ["pfac_kernels.cu", "pfac_batched.cu", "pfac_api.cpp", "trie_build.cpp", "pfac_io.cpp",
-           "pfac_noalloc.cu"]
+           "pfac_noalloc.cu", "pfac_gpubuild.cu"]
 HEADERS = ["pfac_internal.h", "pfac_device.cuh", os.path.join("..", "..", "include", "pfac.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -500,6 +500,55 @@ pfac_handle pfac_build(const char *const *patterns, const int32_t *lengths, int3
     return pfac_build_ex(patterns, lengths, n, nullptr);
 }
 
+pfac_handle pfac_build_device(const uint8_t *d_blob, const int64_t *d_offsets, int32_t n,
+                              const pfac_build_opts *opts, void *stream)
+{
+    g_last_error = PFAC_OK;
+    pfac_build_opts o{};
+    if (opts) o = *opts;
+    if (n <= 0 || o.host_only || o.filter_b > 14 || !is_device_ptr(d_blob) || !is_device_ptr(d_offsets)) {
+        fail(PFAC_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    pfac::DeviceProps dp{};
+    if (device_props(&dp) != PFAC_OK) return nullptr;
+    pfac_table *h = new (std::nothrow) pfac_table();
+    if (!h) { fail(PFAC_ERR_OOM); return nullptr; }
+    pfac::DeviceBuild B;
+    int rc = PFAC_OK;
+    try {
+        rc = pfac::build_device_tables(d_blob, d_offsets, n, o.filter_b, o.sample >= 0, (cudaStream_t)stream, dp, &B);
+    } catch (const std::bad_alloc &) {
+        rc = PFAC_ERR_OOM;
+    }
+    if (rc != PFAC_OK) {
+        delete h;
+        if (rc == PFAC_ERR_CUDA) cuda_fail(cudaGetLastError());
+        else fail(rc);
+        return nullptr;
+    }
+    h->device = dp.device;
+    h->dmem = B.mem;
+    h->dbytes = B.bytes;
+    h->dt = B.dt;
+    pfac::HostTables &T = h->host;
+    T.n_states = B.dt.n_states;
+    T.n_patterns = n;
+    T.max_len = B.dt.max_len;
+    T.min_len = B.dt.min_len;
+    T.n_duplicates = B.n_duplicates;
+    T.level = std::move(B.level);
+    T.filter_b = B.dt.filter_b;
+    T.filter1_b = B.dt.filter1_b;
+    T.rank_wide = B.dt.rank_wide;
+    T.sample_q = B.dt.sample_q;
+    T.sample_s = B.dt.sample_s;
+    h->rows_bytes = B.dt.n_states * 16;
+    h->skip_bytes = B.skip_bytes;
+    h->filter_set = B.filter_set;
+    return h;
+}
+
 int pfac_destroy(pfac_handle h)
 {
     if (!h) return PFAC_OK;
@@ -555,9 +604,16 @@ int pfac_export(pfac_handle h, int32_t *rows, int32_t *out_id, int64_t *level)
 {
     if (!h) return fail(PFAC_ERR_INVALID_ARG);
     const pfac::HostTables &T = h->host;
+    if (level) memcpy(level, T.level.data(), T.level.size() * 8);
+    if (T.rows.empty() && T.n_states > 0) {
+        // built on the device: the rows and ids live there only
+        cudaError_t e = cudaSuccess;
+        if (rows) e = cudaMemcpy(rows, h->dt.rows, (size_t)T.n_states * 16, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && out_id) e = cudaMemcpy(out_id, h->dt.out_id, (size_t)T.n_states * 4, cudaMemcpyDeviceToHost);
+        return e == cudaSuccess ? PFAC_OK : cuda_fail(e);
+    }
     if (rows) memcpy(rows, T.rows.data(), T.rows.size() * 4);
     if (out_id) memcpy(out_id, T.out_id.data(), T.out_id.size() * 4);
-    if (level) memcpy(level, T.level.data(), T.level.size() * 8);
     return PFAC_OK;
 }
 
@@ -565,25 +621,42 @@ int pfac_export_shortcuts(pfac_handle h, uint32_t *skip, int64_t skip_words, uin
                           uint32_t *dense, int64_t dense_words)
 {
     if (!h) return fail(PFAC_ERR_INVALID_ARG);
-    if (h->device >= 0) return fail(PFAC_ERR_UNSUPPORTED);
     const pfac::HostTables &T = h->host;
-    struct Out { uint32_t *dst; int64_t cap; const uint32_t *src; size_t words; } outs[] = {
-        {skip, skip_words, T.skip.data(), T.skip.size()}, {filter, filter_words, T.filter.data(), T.filter.size()},
-        {dense, dense_words, T.dense.data(), T.dense.size()}};
+    const bool on_device = h->device >= 0;       // the host copies were dropped after the upload
+    const size_t fwords = T.filter_b ? std::max<size_t>(1, ((size_t)1 << (2 * T.filter_b)) / 32) : 0;
+    struct Out { uint32_t *dst; int64_t cap; const void *src; size_t words; } outs[] = {
+        {skip, skip_words, on_device ? (const void *)h->dt.skip : T.skip.data(),
+         on_device ? (size_t)h->skip_bytes / 4 : T.skip.size()},
+        {filter, filter_words, on_device ? (const void *)h->dt.filter : T.filter.data(),
+         on_device ? fwords : T.filter.size()},
+        {dense, dense_words, on_device ? (const void *)h->dt.dense : T.dense.data(),
+         on_device ? (size_t)h->filter_set * 4 : T.dense.size()}};
     for (auto &o : outs)
         if (o.dst && o.cap < (int64_t)o.words) return fail(PFAC_ERR_INVALID_ARG);
-    for (auto &o : outs)
-        if (o.dst && o.words) memcpy(o.dst, o.src, o.words * 4);
+    for (auto &o : outs) {
+        if (!o.dst || !o.words || !o.src) continue;
+        if (on_device) {
+            const cudaError_t e = cudaMemcpy(o.dst, o.src, o.words * 4, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e);
+        } else {
+            memcpy(o.dst, o.src, o.words * 4);
+        }
+    }
     return PFAC_OK;
 }
 
 int pfac_export_sample(pfac_handle h, uint32_t *sample, int64_t words)
 {
     if (!h) return fail(PFAC_ERR_INVALID_ARG);
-    if (h->device >= 0) return fail(PFAC_ERR_UNSUPPORTED);
-    const std::vector<uint32_t> &G = h->host.sample;
-    if (sample && words < (int64_t)G.size()) return fail(PFAC_ERR_INVALID_ARG);
-    if (sample && !G.empty()) memcpy(sample, G.data(), G.size() * 4);
+    const int32_t q = h->host.sample_q;
+    const size_t have = q ? ((size_t)1 << (2 * q)) / 32 : 0;
+    if (sample && words < (int64_t)have) return fail(PFAC_ERR_INVALID_ARG);
+    if (!sample || !have) return PFAC_OK;
+    if (h->device >= 0) {
+        const cudaError_t e = cudaMemcpy(sample, h->dt.sample, have * 4, cudaMemcpyDeviceToHost);
+        return e == cudaSuccess ? PFAC_OK : cuda_fail(e);
+    }
+    memcpy(sample, h->host.sample.data(), have * 4);
     return PFAC_OK;
 }
 

@@ -259,6 +259,19 @@ int launch_timeout_probe(int32_t *status, int64_t limit_ns, cudaStream_t st);
 int scan_packed_with_scratch(struct ::pfac_table *h, const uint32_t *d_packed, int64_t n_bases,
                              int32_t *d_out_ids, const DeferScratch &scratch, cudaStream_t st);
 
+// Table construction on the device (pfac_gpubuild.cu): the tables of build_host_tables
+// for the same patterns, in one device allocation laid out as pfac_build_ex lays out its
+// upload. Synchronous on `st`.
+struct DeviceBuild {
+    DeviceTable dt{};
+    void *mem = nullptr;
+    size_t bytes = 0;
+    std::vector<int64_t> level;
+    int64_t n_duplicates = 0, filter_set = 0, skip_bytes = 0;
+};
+int build_device_tables(const uint8_t *d_blob, const int64_t *d_off, int32_t n, int32_t filter_b_opt, bool with_sample,
+                        cudaStream_t st, const DeviceProps &dp, DeviceBuild *out);
+
 // Record a status (or a CUDA error) as this thread's last error; returns the status.
 int set_last_error(int code);
 int set_last_cuda_error(cudaError_t e);
