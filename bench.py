@@ -325,6 +325,23 @@ def large_dict_measure(steps: int):
     compact_ms = timed(lambda: b.pfac_match_compact(table.h, packed, n, d_off, d_ids, d_cnt))
     matches = int(d_cnt.item())
     same = matches <= cap and int((out != 0).sum().item()) == matches
+    # the same table built on the GPU from the patterns in device memory (after one small
+    # build that loads the construction kernels), and a scan with it
+    d_blob = torch.from_numpy(w.blob).cuda()
+    d_offs = torch.from_numpy(w.offsets.astype(np.int64)).cuda()
+    b.Table.from_device(d_blob[:64], torch.tensor([0, 16, 32], dtype=torch.int64, device="cuda")).close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tdev = b.Table.from_device(d_blob, d_offs)
+    dev_build_s = time.perf_counter() - t0
+    keys = ("n_states", "n_duplicates", "filter_b", "filter_set", "table_bytes", "sample_q")
+    same_info = all(tdev.info[k] == info[k] for k in keys)
+    out2 = torch.empty_like(out)
+    b.pfac_match_packed(tdev.h, packed, n, out2)
+    torch.cuda.synchronize()
+    same_dev_ids = bool(torch.equal(out, out2))
+    tdev.close()
+    del out2, d_blob, d_offs
     peak, _ = measured_hbm()
     res = {"workload": w.name, "bases": n, "n_states": info["n_states"], "filter_b": info["filter_b"],
            "table_bytes": info["table_bytes"], "table_build_s": build_s,
@@ -332,6 +349,8 @@ def large_dict_measure(steps: int):
            "dense_roofline_frac": BYTES_PER_BASE * n / (dense_ms * 1e-3) / (peak * 1e9),
            "compact_ms": compact_ms, "compact_gbases_s": n / compact_ms / 1e6, "matches": matches,
            "compact_count_equals_dense_nonzeros": same,
+           "device_build_s": dev_build_s, "device_build_same_counts": same_info,
+           "device_build_same_ids": same_dev_ids, "sample_q": info["sample_q"],
            "config": b.pfac_get_config(table.h, n)}
     table.close()
     return res
