@@ -46,6 +46,9 @@ struct BatchParams {
     int64_t defer_cap;
     unsigned long long *defer_count;
     int32_t walk_loads;
+    int32_t smem_plan;           // each CTA numbers the work items itself, in shared memory
+    int32_t smem_sets;           // each CTA keeps the table descriptors in shared memory
+    uint32_t off_sets;           // byte offset of the descriptors in shared memory
 };
 
 __global__ void pack_bits_kernel(const uint8_t *__restrict__ text, int64_t len, uint32_t *__restrict__ packed,
@@ -139,12 +142,26 @@ struct ItemMeta {
     int32_t set;
 };
 
-// The metadata of work item `it` (the read from the plan's map, or by search past its
-// capacity: the last r with item_start[r] <= it).
+// The metadata of work item `it`: its read is the last r with start[r] <= it, found by a
+// binary search of the CTA's shared-memory numbering (s_start), or read from the plan's
+// map (or searched in the plan's item_start past the map's capacity).
 template <int LW>
-__device__ __forceinline__ ItemMeta item_meta(const BatchParams &P, int64_t it)
+__device__ __forceinline__ ItemMeta item_meta(const BatchParams &P, int64_t it, const int32_t *s_start)
 {
     int32_t r = 0;
+    if (s_start) {
+        int32_t hi = P.n_reads - 1;
+        while (r < hi) {
+            const int32_t mid = (r + hi + 1) >> 1;
+            if ((int64_t)s_start[mid] <= it) r = mid;
+            else hi = mid - 1;
+        }
+        ItemMeta m;
+        read_bounds(P.read_off, r, P.n, &m.rs, &m.re);
+        m.set = P.read_set[r];
+        m.base = m.rs + (it - s_start[r]) * (32 * LW);
+        return m;
+    }
     if (it < P.item_cap) {
         r = P.item_read[it];
     } else {
@@ -165,13 +182,73 @@ __device__ __forceinline__ ItemMeta item_meta(const BatchParams &P, int64_t it)
 // Warp w takes work items w, w + W, w + 2W, ... (W warps in the grid); the metadata of
 // its next item is loaded before the current one is scanned, so those dependent loads
 // overlap the scan instead of preceding it.
+// The CTA's own numbering of the work items (P.smem_plan): s_start[r] = items of the reads
+// before r (an exclusive prefix sum over the reads, 256 threads with consecutive runs of
+// reads each), s_start[n_reads] = all items. The caller guarantees n_reads <= the shared
+// memory reserved for it and fewer than 2^31 items.
+__device__ void number_items(const BatchParams &P, int32_t *s_start, int32_t *s_warp)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t per = (P.n_reads + 255) / 256;
+    const int32_t r0 = min(P.n_reads, tid * per), r1 = min(P.n_reads, r0 + per);
+    int32_t mine = 0;
+    for (int32_t r = r0; r < r1; r++) {
+        int64_t rs, re;
+        read_bounds(P.read_off, r, P.n, &rs, &re);
+        const int32_t items = (int32_t)((re - rs + P.item - 1) / P.item);
+        s_start[r] = mine;                 // within this thread's run, for now
+        mine += items;
+    }
+    int32_t incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += o;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int32_t ws = lane < 8 ? s_warp[lane] : 0;
+        int32_t wi = ws;
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+            const int32_t o = __shfl_up_sync(0xFFFFFFFFu, wi, d);
+            if (lane >= d) wi += o;
+        }
+        if (lane < 8) s_warp[8 + lane] = wi - ws;
+        if (lane == 7) s_warp[16] = wi;
+    }
+    __syncthreads();
+    const int32_t before = s_warp[8 + warp] + incl - mine;
+    for (int32_t r = r0; r < r1; r++) s_start[r] += before;
+    if (tid == 0) s_start[P.n_reads] = s_warp[16];
+    __syncthreads();
+}
+
 template <int LW>
 __global__ void __launch_bounds__(256, 4) batched_scan_kernel(const BatchParams P)
 {
     constexpr int kItem = 32 * LW;
     constexpr uint32_t kAll = LW == 32 ? 0xFFFFFFFFu : ((1u << LW) - 1u);
+    extern __shared__ __align__(16) uint8_t bsm[];
+    __shared__ int32_t s_warp[24];
     const int lane = threadIdx.x & 31;
-    const int64_t total = P.item_start[P.n_reads];
+    const int32_t *s_start = nullptr;
+    const DeviceTable *sets = P.sets;
+    if (P.smem_sets) {
+        DeviceTable *s_sets = reinterpret_cast<DeviceTable *>(bsm + P.off_sets);
+        const int words = (int)(P.n_sets * sizeof(DeviceTable) / 4);
+        for (int i = threadIdx.x; i < words; i += blockDim.x)
+            reinterpret_cast<uint32_t *>(s_sets)[i] = reinterpret_cast<const uint32_t *>(P.sets)[i];
+        sets = s_sets;
+    }
+    if (P.smem_plan) {
+        number_items(P, reinterpret_cast<int32_t *>(bsm), s_warp);
+        s_start = reinterpret_cast<const int32_t *>(bsm);
+    } else {
+        __syncthreads();
+    }
+    const int64_t total = s_start ? (int64_t)s_start[P.n_reads] : P.item_start[P.n_reads];
     const uint64_t pol = policy_evict_first();
     Sink K{};
     K.out = P.out;
@@ -183,16 +260,16 @@ __global__ void __launch_bounds__(256, 4) batched_scan_kernel(const BatchParams 
     const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     ItemMeta m{};
-    if (it < total) m = item_meta<LW>(P, it);
+    if (it < total) m = item_meta<LW>(P, it, s_start);
     while (it < total) {
         const int64_t nxt = it + stride;
         ItemMeta mn{};
-        if (nxt < total) mn = item_meta<LW>(P, nxt);
+        if (nxt < total) mn = item_meta<LW>(P, nxt, s_start);
         const int32_t set = m.set;
         if (set < 0 || set >= P.n_sets) {
-            if (lane == 0) record_error(P.sets[0].status, PFAC_ERR_INVALID_ARG);
+            if (lane == 0) record_error(sets[0].status, PFAC_ERR_INVALID_ARG);
         } else {
-            const DeviceTable T = P.sets[set];
+            const DeviceTable T = sets[set];
             const int64_t base = m.base, re = m.re;
             const int64_t item_end = min(base + kItem, re);
             // this lane's LW offsets and the 64 bases from its first one
@@ -274,7 +351,16 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
     if (cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     const int pack_blocks = (int)std::min<int64_t>((bw + 255) / 256, (int64_t)dp.num_sms * 16);
     pack_bits_kernel<<<std::max(1, pack_blocks), 256, 0, st>>>(texts, n, packed, invalid);
-    plan_kernel<<<1, 1024, 0, st>>>(read_off, n_reads, n, 32 * lw, item_start, item_read, item_cap);
+    // Shared memory of a scan CTA (blocks_per_sm of them per SM, 48 KB at most each): the
+    // items' numbering when the reads fit (else the one-CTA plan kernel numbers them in
+    // global memory first), then the table descriptors when they fit too.
+    const int64_t per_cta = std::min<int64_t>(48 * 1024, (int64_t)dp.smem_per_sm / blocks_per_sm - 1024);
+    const int64_t plan_bytes = (((int64_t)n_reads + 1) * 4 + 15) & ~15LL;
+    const bool smem_plan = plan_bytes <= per_cta && item_cap < 0x7FFFFFFFLL;
+    const int64_t sets_bytes = (int64_t)n_sets * (int64_t)sizeof(DeviceTable);
+    const bool smem_sets = (smem_plan ? plan_bytes : 0) + sets_bytes <= per_cta;
+    const int64_t smem = (smem_plan ? plan_bytes : 0) + (smem_sets ? sets_bytes : 0);
+    if (!smem_plan) plan_kernel<<<1, 1024, 0, st>>>(read_off, n_reads, n, 32 * lw, item_start, item_read, item_cap);
     BatchParams P{};
     P.sets = d_sets;
     P.n_sets = n_sets;
@@ -293,8 +379,11 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
     P.defer_count = counters + 1;
     P.item = 32 * lw;
     P.walk_loads = bc.walk_loads > 0 ? bc.walk_loads : 2;
-    if (lw == 32) batched_scan_kernel<32><<<dp.num_sms * blocks_per_sm, 256, 0, st>>>(P);
-    else batched_scan_kernel<16><<<dp.num_sms * blocks_per_sm, 256, 0, st>>>(P);
+    P.smem_plan = smem_plan;
+    P.smem_sets = smem_sets;
+    P.off_sets = (uint32_t)(smem_plan ? plan_bytes : 0);
+    if (lw == 32) batched_scan_kernel<32><<<dp.num_sms * blocks_per_sm, 256, (size_t)smem, st>>>(P);
+    else batched_scan_kernel<16><<<dp.num_sms * blocks_per_sm, 256, (size_t)smem, st>>>(P);
     batched_tail_kernel<<<dp.num_sms * 4, 256, 0, st>>>(P);
     return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
 }

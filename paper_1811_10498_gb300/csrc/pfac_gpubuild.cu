@@ -318,14 +318,14 @@ __global__ void dense_kernel(const int32_t *__restrict__ rows, const uint32_t *_
 }
 
 // Sampled screen: the q-grams at positions 0 .. s-1 of every pattern.
-__global__ void sample_kernel(const uint8_t *__restrict__ blob, const int64_t *__restrict__ off, int32_t n,
+__global__ void sample_kernel(const uint8_t *__restrict__ blob, const int64_t *__restrict__ off, int32_t n, int q,
                               uint32_t *sample)
 {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         const uint8_t *p = blob + off[j];
         for (int d = 0; d < kSampleS; d++) {
             uint32_t g = 0;
-            for (int k = 0; k < kSampleQ; k++) g |= (uint32_t)dev_base_code(p[d + k]) << (2 * k);
+            for (int k = 0; k < q; k++) g |= (uint32_t)dev_base_code(p[d + k]) << (2 * k);
             atomicOr(sample + (g >> 5), 1u << (g & 31u));
         }
     }
@@ -473,12 +473,13 @@ int build_device_tables(const uint8_t *d_blob, const int64_t *d_off, int32_t n, 
 
     // ---- sampled screen -------------------------------------------------------------
     uint32_t *sample = nullptr;
-    const bool sampled = with_sample && filter_b > kFilter1B && min_len >= kSampleQ + kSampleS - 1;
-    const size_t sample_bytes = sampled ? ((size_t)1 << (2 * kSampleQ)) / 8 : 0;
+    const int32_t q = with_sample ? sample_q_for(filter_b, min_len) : 0;
+    const bool sampled = q > 0;
+    const size_t sample_bytes = sampled ? ((size_t)1 << (2 * q)) / 8 : 0;
     if (sampled) {
         PFAC_CK(tmp.get(&sample, sample_bytes));
         PFAC_CK(cudaMemsetAsync(sample, 0, sample_bytes, st));
-        sample_kernel<<<g, 256, 0, st>>>(d_blob, d_off, n, sample);
+        sample_kernel<<<g, 256, 0, st>>>(d_blob, d_off, n, q, sample);
         PFAC_CK(cudaGetLastError());
     }
     PFAC_CK(cudaMemcpyAsync(&hs, d_stats, sizeof hs, cudaMemcpyDeviceToHost, st));
@@ -529,7 +530,7 @@ int build_device_tables(const uint8_t *d_blob, const int64_t *d_off, int32_t n, 
     out->dt.filter_b = filter_b;
     out->dt.filter1_b = filter1_b;
     out->dt.rank_wide = rank_wide;
-    out->dt.sample_q = sampled ? kSampleQ : 0;
+    out->dt.sample_q = q;
     out->dt.sample_s = sampled ? kSampleS : 0;
     out->level = std::move(level);
     out->n_duplicates = (int64_t)n - (int64_t)hs.terminals;

@@ -66,6 +66,18 @@ constexpr int32_t kDeepFilterMinPatterns = 1 << 19;
 // multiple of kSampleS at or after i finds its bit set.
 constexpr int kSampleQ = 13;
 constexpr int kSampleS = 4;
+// A table whose filter (order kFilter1B) fits in shared memory gets a sampled screen of
+// 10-grams instead, kept in shared memory in its place (the filter is then read from
+// global memory, for the offsets the screen lets through).
+constexpr int kSampleQSmem = kFilter1B;
+
+// q-gram length of the sampled screen a table gets (0 = none).
+inline int32_t sample_q_for(int32_t filter_b, int32_t min_len)
+{
+    if (filter_b > kFilter1B && min_len >= kSampleQ + kSampleS - 1) return kSampleQ;
+    if (filter_b == kFilter1B && min_len >= kSampleQSmem + kSampleS - 1) return kSampleQSmem;
+    return 0;
+}
 
 // Allocator whose construction without a value leaves the element uninitialised: the
 // builder sizes its largest arrays with resize() and then writes every element from

@@ -529,6 +529,22 @@ __device__ __forceinline__ uint32_t filter_bits_screened(const DeviceTable &T, u
     return pend;
 }
 
+// One probe of the sampled screen: the bit of the q-gram that starts the window `win`.
+// SCR 2: 13-grams in global memory; SCR 3: 10-grams in shared memory at offset 0, each
+// word bit-reversed as the prefix filter's copy is (see filter_bits).
+template <int SCR>
+__device__ __forceinline__ uint32_t probe_bit(const DeviceTable &T, const uint8_t *fb, uint32_t win)
+{
+    if constexpr (SCR == 2) {
+        const uint32_t g = win & ((1u << (2 * kSampleQ)) - 1u);
+        return (__ldg(T.sample + (g >> 5)) >> (g & 31u)) & 1u;
+    } else {
+        constexpr uint32_t amask = ((((1u << (2 * kSampleQSmem)) - 1u) >> 3) & ~3u);
+        const uint32_t word = *reinterpret_cast<const uint32_t *>(fb + ((win >> 3) & amask));
+        return __funnelshift_l(word, word, win) >> 31;
+    }
+}
+
 // The sampled screen of a lane's 32 offsets (packed text, window bases 0 .. 47 in x0, x1,
 // x2): probe m reads the q-gram at window offset 4m (m = 0 .. 8; the ninth is the next
 // lane's first, taken by shuffle, and probed directly by the warp's last lane). Offset r
@@ -537,32 +553,47 @@ __device__ __forceinline__ uint32_t filter_bits_screened(const DeviceTable &T, u
 // offsets 4m-3 .. 4m with probe m, and 29 .. 31 with probe 8. Probes past the text end
 // read bases that are not the text's: they can only add offsets, which the exact prefix
 // filter then rejects.
-__device__ __forceinline__ uint32_t sampled_candidates(const DeviceTable &T, uint32_t x0, uint32_t x1, uint32_t x2,
-                                                       int lane)
+template <int SCR>
+__device__ __forceinline__ uint32_t sampled_candidates(const DeviceTable &T, const uint8_t *fb, uint32_t x0,
+                                                       uint32_t x1, uint32_t x2, int lane)
 {
     static_assert(kSampleS == 4, "probes every 4th offset of a lane's 32");
-    const uint32_t qmask = (1u << (2 * kSampleQ)) - 1u;
     uint32_t cand = 0, p0 = 0;
 #pragma unroll
     for (int m = 0; m < 8; m++) {
         const int j = 4 * m;
         const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
-        const uint32_t g = win & qmask;
-        const uint32_t bit = (__ldg(T.sample + (g >> 5)) >> (g & 31u)) & 1u;
+        const uint32_t bit = probe_bit<SCR>(T, fb, win);
         if (m == 0) p0 = bit;
         cand |= (0u - bit) & (m == 0 ? 1u : (0xFu << (4 * m - 3)));
     }
     uint32_t p8 = __shfl_down_sync(0xFFFFFFFFu, p0, 1);
-    if (lane == 31) {
-        const uint32_t g = x2 & qmask;
-        p8 = (__ldg(T.sample + (g >> 5)) >> (g & 31u)) & 1u;
-    }
+    if (lane == 31) p8 = probe_bit<SCR>(T, fb, x2);
     return cand | ((0u - p8) & 0xE0000000u);
 }
 
-// SCR (packed text, main filter in global memory): 1 = the first-level filter of order
-// kFilter1B sits in shared memory at offset 0 and screens every offset first; 2 = the
-// sampled screen (global memory) picks the offsets whose main-filter bit is read.
+// Main-filter bits (global memory) of the offsets in `m`, one at a time (a lane's few
+// candidates: the warp runs as many rounds as its busiest lane has candidates).
+__device__ __forceinline__ uint32_t filter_bits_of(const DeviceTable &T, uint32_t x0, uint32_t x1, uint32_t x2,
+                                                   uint32_t bmask, uint32_t m)
+{
+    uint32_t pend = 0;
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1u;
+        const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
+        const uint32_t kmer = win & bmask;
+        pend |= ((__ldg(T.filter + (kmer >> 5)) >> (kmer & 31u)) & 1u) << j;
+    }
+    return pend;
+}
+
+// SCR (packed text): 1 = the main filter is in global memory and the first-level filter
+// of order kFilter1B sits in shared memory at offset 0 and screens every offset first;
+// 2 = the main filter is in global memory and the sampled 13-gram screen (global memory)
+// picks the offsets whose main-filter bit is read; 3 = the sampled 10-gram screen sits in
+// shared memory at offset 0 in place of the order-10 filter, which is read from global
+// memory for the offsets the screen lets through.
 // ZW (dense packed scans): 0 = each consumer warp stores its own zeros; 1 or 2 = a zero
 // writer warp (warp consumers + 1) stores them (see zero_writer).
 template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW, bool ALL = false, int SCR = 0, int ZW = 0>
@@ -611,11 +642,12 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             for (int64_t i = (bytes & ~(int64_t)15) + tid; i < bytes; i += blockDim.x) dst[i] = src[i];
         };
         const int64_t words = B >= 3 ? ((int64_t)1 << (2 * B)) / 32 : 1;
-        if (FSMEM || SCR == 1) {
+        if (FSMEM || SCR == 1 || SCR == 3) {
             // the filter's words go in bit-reversed (see filter_bits): the main filter, or
             // the first-level one
-            const uint32_t *src = SCR == 1 ? T.filter1 : T.filter;
-            const int64_t fwords = SCR == 1 ? ((int64_t)1 << (2 * kFilter1B)) / 32 : words;
+            const uint32_t *src = SCR == 1 ? T.filter1 : (SCR == 3 ? T.sample : T.filter);
+            const int64_t fwords = SCR == 1 ? ((int64_t)1 << (2 * kFilter1B)) / 32
+                                            : (SCR == 3 ? ((int64_t)1 << (2 * kSampleQSmem)) / 32 : words);
             uint32_t *dst = reinterpret_cast<uint32_t *>(smem + P.off_filter);
             for (int64_t i = 4 * (int64_t)tid; i + 4 <= fwords; i += 4 * (int64_t)blockDim.x) {
                 const uint4 v = __ldg(reinterpret_cast<const uint4 *>(src + i));
@@ -710,7 +742,12 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                 pend = filter_bits_screened<LW>(T, x0, x1, x2, bmask, pend);
             } else if constexpr (SCR == 2) {
                 static_assert(LW == 32, "the sampled screen covers a lane's 32 offsets");
-                pend = filter_bits_screened<LW>(T, x0, x1, x2, bmask, sampled_candidates(T, x0, x1, x2, lane) & fast);
+                pend = filter_bits_screened<LW>(T, x0, x1, x2, bmask,
+                                                sampled_candidates<2>(T, nullptr, x0, x1, x2, lane) & fast);
+            } else if constexpr (SCR == 3) {
+                static_assert(LW == 32, "the sampled screen covers a lane's 32 offsets");
+                const uint8_t *fb = reinterpret_cast<const uint8_t *>(sf);
+                pend = filter_bits_of(T, x0, x1, x2, bmask, sampled_candidates<3>(T, fb, x0, x1, x2, lane) & fast);
             } else {
                 pend = filter_bits<FSMEM, LW>(T, sf, x0, x1, x2, bmask) & fast;
             }
@@ -928,7 +965,13 @@ static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool pac
     pl.zw = zw;
     pl.filter_bytes = total(fbytes, 0) <= limit ? fbytes : 0;
     const bool sampled = t.sample && t.sample_q == kSampleQ && t.sample_s == kSampleS && LW == 32;
-    if (!pl.filter_bytes && packed && sampled && cfg.screen != 1) {
+    const int64_t g10 = ((int64_t)1 << (2 * kSampleQSmem)) / 8;
+    const bool sampled10 = t.sample && t.sample_q == kSampleQSmem && t.sample_s == kSampleS && LW == 32 && packed &&
+                           total(g10, 0) <= limit;
+    if (sampled10 && cfg.screen == 2) {
+        pl.filter_bytes = g10;           // the 10-gram screen in place of the filter
+        pl.scr = 3;
+    } else if (!pl.filter_bytes && packed && sampled && cfg.screen != 1) {
         pl.scr = 2;
     } else if (!pl.filter_bytes && packed && t.filter1_b == kFilter1B && t.filter1 && cfg.screen != 2) {
         const int64_t f1 = ((int64_t)1 << (2 * kFilter1B)) / 8;
@@ -941,7 +984,8 @@ static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool pac
         zw = pl.zw = 1;                  // no room for a zero tile: 16-byte stores instead
         zb = 0;
     }
-    pl.rank_bytes = (pl.scr == 0 && cfg.smem_table_bytes >= 0 && total(pl.filter_bytes, rbytes) <= limit) ? rbytes : 0;
+    pl.rank_bytes = ((pl.scr == 0 || pl.scr == 3) && cfg.smem_table_bytes >= 0 &&
+                     total(pl.filter_bytes, rbytes) <= limit) ? rbytes : 0;
     if (zw == 2) {
         for (int64_t c = 16384; c > 2048; c >>= 1) {
             zb = c;
@@ -1039,7 +1083,7 @@ static void (*scan_kernel_for(bool lw32, int zw))(const ScanParams)
         if (zw == 1) return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, SCR, 1>;
         if (zw == 2) return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, SCR, 2>;
     }
-    if constexpr (SCR == 2) {
+    if constexpr (SCR >= 2) {
         return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, SCR>;
     } else {
         return lw32 ? scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, SCR>
@@ -1075,6 +1119,11 @@ static int launch_scan_w(const ScanParams &P, bool fsmem, bool rank16, int grid,
             return rank16 ? launch_scan_t<PACKED, COMPACT, false, true, ALL, 2>(P, grid, threads, smem, tail_grid,
                                                                               st, cfg, dp, zw)
                           : launch_scan_t<PACKED, COMPACT, false, false, ALL, 2>(P, grid, threads, smem, tail_grid,
+                                                                               st, cfg, dp, zw);
+        if (scr == 3)
+            return rank16 ? launch_scan_t<PACKED, COMPACT, false, true, ALL, 3>(P, grid, threads, smem, tail_grid,
+                                                                              st, cfg, dp, zw)
+                          : launch_scan_t<PACKED, COMPACT, false, false, ALL, 3>(P, grid, threads, smem, tail_grid,
                                                                                st, cfg, dp, zw);
     }
     if (fsmem)

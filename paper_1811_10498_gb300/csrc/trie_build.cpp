@@ -526,20 +526,22 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
         }
 
         // ---- step 3d: sampled screen -----------------------------------------------
-        // When every pattern has at least kSampleQ + kSampleS - 1 bases, a match at
-        // offset i puts the pattern's q-gram at position d = (-i) mod s at the offset
-        // i + d, a multiple of s. So a bit set of the q-grams at positions 0 .. s-1 of
-        // every pattern, probed at every s-th offset, lists a superset of the offsets
-        // where a pattern can start (the s offsets up to each probe whose q-gram is set).
-        if (with_sample && T.filter_b > kFilter1B && min_len >= kSampleQ + kSampleS - 1) {
-            T.sample_q = kSampleQ;
+        // When every pattern has at least q + s - 1 bases, a match at offset i puts the
+        // pattern's q-gram at position d = (-i) mod s at the offset i + d, a multiple of
+        // s. So a bit set of the q-grams at positions 0 .. s-1 of every pattern, probed at
+        // every s-th offset, lists a superset of the offsets where a pattern can start
+        // (the s offsets up to each probe whose q-gram is set). q = 13 for filters in
+        // global memory, 10 for an order-10 filter (see sample_q_for).
+        const int32_t q = with_sample ? sample_q_for(T.filter_b, min_len) : 0;
+        if (q) {
+            T.sample_q = q;
             T.sample_s = kSampleS;
-            T.sample.assign(((size_t)1 << (2 * kSampleQ)) / 32, 0u);
+            T.sample.assign(((size_t)1 << (2 * q)) / 32, 0u);
             for (int32_t j = 0; j < n; j++) {
                 const unsigned char *p = (const unsigned char *)patterns[j];
                 for (int d = 0; d < kSampleS; d++) {
                     uint32_t g = 0;
-                    for (int k = 0; k < kSampleQ; k++) g |= (uint32_t)base_code(p[d + k]) << (2 * k);
+                    for (int k = 0; k < q; k++) g |= (uint32_t)base_code(p[d + k]) << (2 * k);
                     T.sample[g >> 5] |= 1u << (g & 31);
                 }
             }

@@ -75,7 +75,7 @@ MUTANTS = {
     # ... with the first base of a q-gram in its low bits.
     "sample_qgram_reversed": (
         "g |= (uint32_t)base_code(p[d + k]) << (2 * k);",
-        "g |= (uint32_t)base_code(p[d + k]) << (2 * (kSampleQ - 1 - k));"),
+        "g |= (uint32_t)base_code(p[d + k]) << (2 * (q - 1 - k));"),
 }
 
 

@@ -77,6 +77,10 @@ def genome_small():
     dict(kernel=2, zero_writer=3, threads=96, stages=2),
     dict(kernel=2, zero_writer=3, rank_in_smem=-1),
     dict(kernel=2, zero_writer=3, walk_loads=1),
+    dict(kernel=2, screen=2),
+    dict(kernel=2, screen=2, rank_in_smem=-1),
+    dict(kernel=2, screen=2, walk_loads=1, zero_writer=2),
+    dict(kernel=2, screen=1),
 ], ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
 def test_genome_configs(genome_small, cfg, packed):
     w, want = genome_small

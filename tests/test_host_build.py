@@ -215,8 +215,9 @@ def set_bits(words):
 def test_sampled_screen_definition(seed):
     """The sampled screen of a table whose filter lives in global memory and whose
     patterns have 16 bases or more: exactly the 13-grams at positions 0..3 of every
-    pattern. Tables with a shorter pattern, a filter of order 10 or less, or the option
-    off have none."""
+    pattern; of a table with an order-10 filter and patterns of 13 bases or more: the
+    10-grams at positions 0..3. Tables with a shorter pattern, a filter of order 9 or
+    less, or the option off have none."""
     rng = datagen.rng_for(seed)
     text = datagen.iid_text(20000, rng)
     blob, offs = datagen.pattern_set(text, rng, 400, (16, 40), 0.5)
@@ -229,8 +230,18 @@ def test_sampled_screen_definition(seed):
     assert (q, smp) == (13, 4) and g.size == (1 << 26) // 32
     want = sorted({c for d in range(smp) for c in qgram_codes(pats, q, d)})
     assert set_bits(g).tolist() == want
-    for kw, ps in [(dict(filter_b=11), pats + [pats[0][:15]]), (dict(filter_b=10), pats),
-                   (dict(filter_b=11, sample=-1), pats)]:
+    # an order-10 filter (it fits in shared memory) gets a screen of 10-grams instead
+    h = b_.pfac_build(pats, host_only=True, filter_b=10)
+    try:
+        q, smp, g = b_.pfac_export_sample(h)
+    finally:
+        b_.pfac_destroy(h)
+    assert (q, smp) == (10, 4) and g.size == (1 << 20) // 32
+    want = sorted({c for d in range(smp) for c in qgram_codes(pats, q, d)})
+    assert set_bits(g).tolist() == want
+    short13 = [p for p in pats if len(p) >= 13] + [pats[0][:12]]
+    for kw, ps in [(dict(filter_b=11), pats + [pats[0][:15]]), (dict(filter_b=10), short13),
+                   (dict(filter_b=9), pats), (dict(filter_b=11, sample=-1), pats)]:
         h = b_.pfac_build(ps, host_only=True, **kw)
         try:
             assert b_.pfac_export_sample(h)[0] == 0, kw
