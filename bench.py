@@ -206,9 +206,10 @@ def cpu_baseline(w, got_prefix: np.ndarray | None, seconds: float = 8.0, single_
     return out
 
 
-def batched_measure(steps: int):
+def batched_measure(steps: int, tune: bool = True):
     """The batched workload: 4,096 reads (log-normal lengths, median 1,500) against 64
-    resident tables; one captured CUDA graph per batch vs one launch per read."""
+    resident tables; one captured CUDA graph per batch vs one launch per read. tune=False
+    keeps the library's default launch shape (no autotuner launches before the graph)."""
     import torch
     from paper_1811_10498_gb300 import _binding as b
     from paper_1811_10498_gb300 import datagen
@@ -220,7 +221,11 @@ def batched_measure(steps: int):
     n = int(w.reads.size)
     sc = BatchedScanner(tables, max_bases=n, max_reads=len(w.read_set), graph=False)
     sc.load(w.reads, w.read_offsets, w.read_set)
-    tuned = sc.tune(use_cache=False)      # picks the launch shape, then captures the graph
+    if tune:
+        tuned = sc.tune(use_cache=False)      # picks the launch shape, then captures the graph
+    else:
+        sc.capture()
+        tuned = {}
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(3):
         sc.run()
@@ -530,6 +535,76 @@ def paper_suite(args):
     ref.close()
 
 
+def ceilings_suite():
+    """The hardware ceilings behind the kernels' design (csrc/ceilings.cu, built here with
+    nvcc for sm_103a): store bandwidth for 1 GiB of ids by several store paths, and random
+    4-byte lookup rates from L1/L2/HBM, shared memory and cluster distributed shared
+    memory. Prints the program's JSON lines."""
+    from paper_1811_10498_gb300 import build_ext
+    src = os.path.join(build_ext.CSRC, "ceilings.cu")
+    os.makedirs(build_ext.BUILD, exist_ok=True)
+    exe = os.path.join(build_ext.BUILD, "ceilings")
+    subprocess.run([build_ext.nvcc(), "-O3", *build_ext.ARCH, "-o", exe, src], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=600)
+    for line in r.stdout.splitlines():
+        if line.startswith("{"):
+            print(json.dumps({"suite": "ceilings", **json.loads(line)}), flush=True)
+    if r.returncode != 0:
+        raise SystemExit(r.returncode)
+
+
+def configs_suite(steps: int):
+    """Kernel-2 launch configurations on the genome-scale workload (the benchmark's
+    table and text): the default, the shared-memory 10-gram screen, the zero-writer
+    warp, stages, walk depth, rank index placement. One JSON line each: median step time
+    (L2 flushed before each step) and whether the ids equal the default's."""
+    import torch
+    from paper_1811_10498_gb300 import _binding as b
+    from paper_1811_10498_gb300 import build_ext
+    build_ext.build()
+    w = make_workload(0, N_BASES, N_PATTERNS)
+    n = w.text.size
+    table = b.Table((w.blob, w.offsets))
+    d = torch.from_numpy(w.text).cuda()
+    packed, _, _ = b.pack(d)
+    del d
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    peak, _ = measured_hbm()
+    ref = None
+    # the same table built with the 10-gram screen too (pfac_build_opts.sample = 1)
+    table10 = b.Table((w.blob, w.offsets), sample=1)
+    cfgs = [dict(), dict(screen=2, sample=1), dict(screen=2, walk_loads=1, sample=1),
+            dict(screen=2, rank_in_smem=-1, sample=1), dict(zero_writer=2), dict(zero_writer=3), dict(stages=2),
+            dict(stages=4), dict(walk_loads=1), dict(rank_in_smem=-1), dict(lane_offsets=16, stages=4)]
+    for cfg in cfgs:
+        cfg = dict(cfg)
+        t = table10 if cfg.pop("sample", 0) else table
+        b.pfac_set_config(t.h, dict(kernel=2, **cfg))
+        for _ in range(3):
+            b.pfac_match_packed(t.h, packed, n, out)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = out.clone()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.pfac_match_packed(t.h, packed, n, out)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        print(json.dumps({"suite": "configs", "workload": workload_name(), "config": cfg,
+                          "table": "with the 10-gram screen" if t is table10 else "default", "ms": ms,
+                          "roofline_frac": BYTES_PER_BASE * n / (ms * 1e-3) / (peak * 1e9),
+                          "same_ids_as_default": bool(torch.equal(out, ref)),
+                          "device_status": b.pfac_device_status(t.h)}), flush=True)
+    table.close()
+    table10.close()
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores: each step scans a bounded sample."""
     rank = int(os.environ.get("RANK", "0"))
@@ -588,9 +663,10 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the large-dictionary (10^6 patterns) leg")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--no-tune", action="store_true", help="use the library's default launch configuration")
-    ap.add_argument("--suite", default=None, choices=["paper", "batched"],
+    ap.add_argument("--suite", default=None, choices=["paper", "batched", "ceilings", "configs"],
                     help="paper: the paper's placement, pattern-set and input-size experiments (many lines); "
-                         "batched: the batched workload alone")
+                         "batched: the batched workload alone; ceilings: store and lookup rates of the GPU; "
+                         "configs: kernel-2 launch configurations on the benchmark's workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -600,10 +676,17 @@ def main():
     if args.suite == "paper":
         paper_suite(args)
         return
+    if args.suite == "ceilings":
+        ceilings_suite()
+        return
+    if args.suite == "configs":
+        configs_suite(min(args.steps, 60))
+        return
     if args.suite == "batched":
         from paper_1811_10498_gb300 import build_ext
         build_ext.build()
-        print(json.dumps({"suite": "batched", **batched_measure(min(args.steps, 20))}), flush=True)
+        print(json.dumps({"suite": "batched", **batched_measure(min(args.steps, 20), tune=not args.no_tune)}),
+              flush=True)
         return
 
     import torch

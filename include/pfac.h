@@ -90,9 +90,13 @@ typedef struct {
                            the same trie). A filter above order 10 (too large for shared
                            memory) comes with a first-level filter of order 10, derived
                            from it, that the packed scan keeps in shared memory. */
-    int32_t sample;     /* sampled screen (see pfac_export_sample): 0 = built when the
-                           filter is of order 11 or more and every pattern has at least
-                           16 bases, -1 = never */
+    int32_t sample;     /* sampled screen (see pfac_export_sample): 0 = the 13-gram
+                           screen, built when the filter is of order 11 or more and every
+                           pattern has at least 16 bases; 1 = that, and a 10-gram screen
+                           for an order-10 filter when every pattern has at least 13 bases
+                           (kept in shared memory in the filter's place by launches with
+                           screen = 2; slower than the filter on genome-like texts, an
+                           option for comparison); -1 = never */
 } pfac_build_opts;
 
 pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, int32_t n,
@@ -277,7 +281,9 @@ typedef struct {
                                 read from global memory: 0 = automatic (the sampled screen
                                 when the table has one, else the first-level filter),
                                 1 = the order-10 first-level filter in shared memory, 2 = the
-                                sampled screen (pfac_export_sample; 32 offsets per lane) */
+                                sampled screen (pfac_export_sample; 32 offsets per lane); for a
+                                table with an order-10 filter and a 10-gram screen, 2 = that
+                                screen in shared memory in the filter's place */
     int32_t reserved;        /* 0 */
 } pfac_config;
 

@@ -427,7 +427,8 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
     if (opts) o = *opts;
     pfac_table *h = new (std::nothrow) pfac_table();
     if (!h) { fail(PFAC_ERR_OOM); return nullptr; }
-    int rc = pfac::build_host_tables(patterns, lengths, n, o.filter_b, &h->host, o.sample >= 0);
+    if (o.sample < -1 || o.sample > 1) { delete h; fail(PFAC_ERR_INVALID_ARG); return nullptr; }
+    int rc = pfac::build_host_tables(patterns, lengths, n, o.filter_b, &h->host, o.sample);
     if (rc != PFAC_OK) { delete h; fail(rc); return nullptr; }
     const pfac::HostTables &T = h->host;
     h->rows_bytes = T.n_states * 16;
@@ -506,7 +507,8 @@ pfac_handle pfac_build_device(const uint8_t *d_blob, const int64_t *d_offsets, i
     g_last_error = PFAC_OK;
     pfac_build_opts o{};
     if (opts) o = *opts;
-    if (n <= 0 || o.host_only || o.filter_b > 14 || !is_device_ptr(d_blob) || !is_device_ptr(d_offsets)) {
+    if (n <= 0 || o.host_only || o.filter_b > 14 || o.sample < -1 || o.sample > 1 || !is_device_ptr(d_blob) ||
+        !is_device_ptr(d_offsets)) {
         fail(PFAC_ERR_INVALID_ARG);
         return nullptr;
     }
@@ -517,7 +519,7 @@ pfac_handle pfac_build_device(const uint8_t *d_blob, const int64_t *d_offsets, i
     pfac::DeviceBuild B;
     int rc = PFAC_OK;
     try {
-        rc = pfac::build_device_tables(d_blob, d_offsets, n, o.filter_b, o.sample >= 0, (cudaStream_t)stream, dp, &B);
+        rc = pfac::build_device_tables(d_blob, d_offsets, n, o.filter_b, o.sample, (cudaStream_t)stream, dp, &B);
     } catch (const std::bad_alloc &) {
         rc = PFAC_ERR_OOM;
     }

@@ -16,7 +16,7 @@
 // single-child edges, at most 16 bases); the prefix filter of order b (every b-mer walked
 // from the root: set when the walk reaches depth b, or when a pattern ends on the way,
 // which makes the entry special), its rank index (an exclusive prefix sum of the words'
-// popcounts) and dense entries; the first-level filter of order 10 and the sampled 13-gram
+// popcounts) and dense entries; the first-level filter of order 10 and the sampled
 // screen, under the host builder's conditions.
 #include <stdint.h>
 #include <string.h>
@@ -356,8 +356,8 @@ int grid_for(int64_t items, int threads, const DeviceProps &dp)
 
 }  // namespace
 
-int build_device_tables(const uint8_t *d_blob, const int64_t *d_off, int32_t n, int32_t filter_b_opt, bool with_sample,
-                        cudaStream_t st, const DeviceProps &dp, DeviceBuild *out)
+int build_device_tables(const uint8_t *d_blob, const int64_t *d_off, int32_t n, int32_t filter_b_opt,
+                        int32_t sample_mode, cudaStream_t st, const DeviceProps &dp, DeviceBuild *out)
 {
     if (n <= 0 || !d_blob || !d_off || !out || filter_b_opt > kMaxFilterB) return PFAC_ERR_INVALID_ARG;
 #define PFAC_CK(x)                                                                      \
@@ -473,7 +473,7 @@ int build_device_tables(const uint8_t *d_blob, const int64_t *d_off, int32_t n, 
 
     // ---- sampled screen -------------------------------------------------------------
     uint32_t *sample = nullptr;
-    const int32_t q = with_sample ? sample_q_for(filter_b, min_len) : 0;
+    const int32_t q = sample_q_for(filter_b, min_len, sample_mode);
     const bool sampled = q > 0;
     const size_t sample_bytes = sampled ? ((size_t)1 << (2 * q)) / 8 : 0;
     if (sampled) {

@@ -71,11 +71,15 @@ constexpr int kSampleS = 4;
 // global memory, for the offsets the screen lets through).
 constexpr int kSampleQSmem = kFilter1B;
 
-// q-gram length of the sampled screen a table gets (0 = none).
-inline int32_t sample_q_for(int32_t filter_b, int32_t min_len)
+// q-gram length of the sampled screen a table gets (0 = none). sample_mode: -1 never,
+// 0 the 13-gram screen of filters in global memory, 1 also the 10-gram screen of order-10
+// filters (slower on the genome-like workload than the filter it replaces; kept as an
+// option for the measurement).
+inline int32_t sample_q_for(int32_t filter_b, int32_t min_len, int32_t sample_mode)
 {
+    if (sample_mode < 0) return 0;
     if (filter_b > kFilter1B && min_len >= kSampleQ + kSampleS - 1) return kSampleQ;
-    if (filter_b == kFilter1B && min_len >= kSampleQSmem + kSampleS - 1) return kSampleQSmem;
+    if (sample_mode > 0 && filter_b == kFilter1B && min_len >= kSampleQSmem + kSampleS - 1) return kSampleQSmem;
     return 0;
 }
 
@@ -119,7 +123,7 @@ struct HostTables {
 
 // Status codes match pfac.h.
 int build_host_tables(const char *const *patterns, const int32_t *lengths, int32_t n,
-                      int32_t filter_b_opt, HostTables *out, bool with_sample = true);
+                      int32_t filter_b_opt, HostTables *out, int32_t sample_mode = 0);
 
 }  // namespace pfac
 
@@ -281,8 +285,8 @@ struct DeviceBuild {
     std::vector<int64_t> level;
     int64_t n_duplicates = 0, filter_set = 0, skip_bytes = 0;
 };
-int build_device_tables(const uint8_t *d_blob, const int64_t *d_off, int32_t n, int32_t filter_b_opt, bool with_sample,
-                        cudaStream_t st, const DeviceProps &dp, DeviceBuild *out);
+int build_device_tables(const uint8_t *d_blob, const int64_t *d_off, int32_t n, int32_t filter_b_opt,
+                        int32_t sample_mode, cudaStream_t st, const DeviceProps &dp, DeviceBuild *out);
 
 // Record a status (or a CUDA error) as this thread's last error; returns the status.
 int set_last_error(int code);

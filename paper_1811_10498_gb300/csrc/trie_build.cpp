@@ -177,7 +177,7 @@ int run_parallel(size_t count, int threads, Fn fn)
 }  // namespace
 
 int build_host_tables(const char *const *patterns, const int32_t *lengths, int32_t n,
-                      int32_t filter_b_opt, HostTables *out, bool with_sample)
+                      int32_t filter_b_opt, HostTables *out, int32_t sample_mode)
 {
     if (n <= 0 || !patterns || !lengths || !out) return PFAC_ERR_INVALID_ARG;
     if (filter_b_opt > kMaxFilterB) return PFAC_ERR_INVALID_ARG;
@@ -532,7 +532,7 @@ int build_host_tables(const char *const *patterns, const int32_t *lengths, int32
         // every s-th offset, lists a superset of the offsets where a pattern can start
         // (the s offsets up to each probe whose q-gram is set). q = 13 for filters in
         // global memory, 10 for an order-10 filter (see sample_q_for).
-        const int32_t q = with_sample ? sample_q_for(T.filter_b, min_len) : 0;
+        const int32_t q = sample_q_for(T.filter_b, min_len, sample_mode);
         if (q) {
             T.sample_q = q;
             T.sample_s = kSampleS;

@@ -19,7 +19,7 @@ void *shim_build(const char *const *patterns, const int32_t *lengths, int32_t n,
         *status = PFAC_ERR_OOM;
         return nullptr;
     }
-    *status = pfac::build_host_tables(patterns, lengths, n, filter_b, T, sample >= 0);
+    *status = pfac::build_host_tables(patterns, lengths, n, filter_b, T, sample);
     if (*status != PFAC_OK) {
         delete T;
         return nullptr;

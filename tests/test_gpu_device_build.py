@@ -66,11 +66,13 @@ def test_random_sets_with_prefixes_and_duplicates(seed):
         dev.close()
 
 
-def test_genome_scale_set():
-    """20,000 patterns of 20-100 bases (the genome-scale dictionary), order-10 filter."""
+@pytest.mark.parametrize("sample", [0, 1])
+def test_genome_scale_set(sample):
+    """20,000 patterns of 20-100 bases (the genome-scale dictionary), order-10 filter,
+    with and without the 10-gram screen."""
     w = datagen.genome_scan(n_bases=1 << 22, n_patterns=20_000)
     pats = datagen.pattern_list(w.blob, w.offsets)
-    dev = compare_builds(pats)
+    dev = compare_builds(pats, sample=sample)
     got = gpu_match_packed(dev, w.text)
     want = oracle.Trie(pats).scan_threads(w.text, host_threads())
     assert np.array_equal(got, want), first_diff(got, want)

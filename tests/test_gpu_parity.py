@@ -77,9 +77,6 @@ def genome_small():
     dict(kernel=2, zero_writer=3, threads=96, stages=2),
     dict(kernel=2, zero_writer=3, rank_in_smem=-1),
     dict(kernel=2, zero_writer=3, walk_loads=1),
-    dict(kernel=2, screen=2),
-    dict(kernel=2, screen=2, rank_in_smem=-1),
-    dict(kernel=2, screen=2, walk_loads=1, zero_writer=2),
     dict(kernel=2, screen=1),
 ], ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
 def test_genome_configs(genome_small, cfg, packed):
@@ -100,6 +97,21 @@ def test_deferred_list_overflow(genome_small, monkeypatch):
         t = b.Table((w.blob, w.offsets))
         got = gpu_match_packed(t, w.text, kernel=2, walk_loads=1)
     assert np.array_equal(got, want), first_diff(got, want)
+
+
+@pytest.mark.parametrize("filter_b", [-1, 1, 3, 5, 8, 9, 10, 11, 12])
+@pytest.mark.parametrize("cfg", [dict(screen=2), dict(screen=2, rank_in_smem=-1), dict(screen=2, walk_loads=1),
+                                 dict(screen=2, zero_writer=2), dict(screen=0)],
+                         ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
+def test_shared_memory_10gram_screen(genome_small, cfg):
+    """A table built with the 10-gram screen (sample = 1): scans with it in shared memory
+    in the order-10 filter's place, and without it."""
+    w, want = genome_small
+    t = b.Table((w.blob, w.offsets), sample=1)
+    assert (t.info["sample_q"], t.info["filter_b"]) == (10, 10)
+    got = gpu_match_packed(t, w.text, kernel=2, **cfg)
+    assert np.array_equal(got, want), first_diff(got, want)
+    t.close()
 
 
 @pytest.mark.parametrize("filter_b", [-1, 1, 3, 5, 8, 9, 10, 11, 12])

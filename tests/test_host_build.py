@@ -230,8 +230,9 @@ def test_sampled_screen_definition(seed):
     assert (q, smp) == (13, 4) and g.size == (1 << 26) // 32
     want = sorted({c for d in range(smp) for c in qgram_codes(pats, q, d)})
     assert set_bits(g).tolist() == want
-    # an order-10 filter (it fits in shared memory) gets a screen of 10-grams instead
-    h = b_.pfac_build(pats, host_only=True, filter_b=10)
+    # an order-10 filter (it fits in shared memory) gets a screen of 10-grams instead,
+    # when asked for
+    h = b_.pfac_build(pats, host_only=True, filter_b=10, sample=1)
     try:
         q, smp, g = b_.pfac_export_sample(h)
     finally:
@@ -240,8 +241,8 @@ def test_sampled_screen_definition(seed):
     want = sorted({c for d in range(smp) for c in qgram_codes(pats, q, d)})
     assert set_bits(g).tolist() == want
     short13 = [p for p in pats if len(p) >= 13] + [pats[0][:12]]
-    for kw, ps in [(dict(filter_b=11), pats + [pats[0][:15]]), (dict(filter_b=10), short13),
-                   (dict(filter_b=9), pats), (dict(filter_b=11, sample=-1), pats)]:
+    for kw, ps in [(dict(filter_b=11), pats + [pats[0][:15]]), (dict(filter_b=10, sample=1), short13),
+                   (dict(filter_b=10), pats), (dict(filter_b=9, sample=1), pats), (dict(filter_b=11, sample=-1), pats)]:
         h = b_.pfac_build(ps, host_only=True, **kw)
         try:
             assert b_.pfac_export_sample(h)[0] == 0, kw
