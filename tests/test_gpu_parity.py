@@ -99,7 +99,6 @@ def test_deferred_list_overflow(genome_small, monkeypatch):
     assert np.array_equal(got, want), first_diff(got, want)
 
 
-@pytest.mark.parametrize("filter_b", [-1, 1, 3, 5, 8, 9, 10, 11, 12])
 @pytest.mark.parametrize("cfg", [dict(screen=2), dict(screen=2, rank_in_smem=-1), dict(screen=2, walk_loads=1),
                                  dict(screen=2, zero_writer=2), dict(screen=0)],
                          ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
