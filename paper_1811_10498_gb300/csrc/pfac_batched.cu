@@ -17,13 +17,12 @@ namespace pfac {
 // persistent launch (plus the pack, plan and tail kernels around it).
 //   pack_bits_kernel    ASCII reads -> 2-bit words + one invalid bit per base
 //   plan_kernel         reads -> first work item of each read (512 or 1024 offsets per
-//                       item), in global memory; only for batches whose numbering does
-//                       not fit in a scan CTA's shared memory
-//   batched_scan_kernel every CTA numbers the items itself in shared memory (and keeps the
-//                       table descriptors there); each warp takes a contiguous range of
-//                       items and runs, for each, the same per-warp filter test and skip
-//                       walks as kernel 2, with its read's table and every walk bounded
-//                       by its read's end
+//                       item), and the read of every work item
+//   batched_scan_kernel each warp takes every W-th item (W warps in the grid), with the
+//                       next item's read and bounds loaded while it scans the current
+//                       one; each item runs the same per-warp filter test and skip walks
+//                       as kernel 2, with its read's table and every walk bounded by its
+//                       read's end
 //   batched_tail_kernel deferred long walks, with the table recorded in each item
 // ---------------------------------------------------------------------------
 
@@ -39,15 +38,14 @@ struct BatchParams {
     const int32_t *read_set;
     int32_t n_reads;
     const int64_t *item_start;
+    const int32_t *item_read;    // read of each work item, for the first item_cap items
+    int64_t item_cap;
     int32_t item;                // offsets per work item (32 x LW)
     int32_t *out;
     DeferItem *defer;
     int64_t defer_cap;
     unsigned long long *defer_count;
     int32_t walk_loads;
-    int32_t smem_plan;           // each CTA numbers the work items itself, in shared memory
-    int32_t smem_sets;           // each CTA keeps the table descriptors in shared memory
-    uint32_t off_sets;           // byte offset of the descriptors in shared memory
 };
 
 __global__ void pack_bits_kernel(const uint8_t *__restrict__ text, int64_t len, uint32_t *__restrict__ packed,
@@ -87,7 +85,8 @@ __device__ __forceinline__ void read_bounds(const int64_t *read_off, int32_t r, 
 
 // One CTA: exclusive prefix of the number of work items per read.
 __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ read_off, int32_t n_reads, int64_t n,
-                                                    int32_t item, int64_t *__restrict__ item_start)
+                                                    int32_t item, int64_t *__restrict__ item_start,
+                                                    int32_t *__restrict__ item_read, int64_t item_cap)
 {
     __shared__ int64_t warp_sum[32];
     __shared__ int64_t carry;
@@ -122,6 +121,10 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         if (r < n_reads) {
             const int64_t k0 = carry + before;
             item_start[r] = k0;
+            // the read of each of this read's work items (items past item_cap are found
+            // by search instead)
+            const int64_t k1 = min(k0 + v, item_cap);
+            for (int64_t k = k0; k < k1; k++) item_read[k] = (int32_t)r;
         }
         __syncthreads();
         if (tid == 0) carry += warp_sum[(blockDim.x >> 5) - 1];
@@ -130,76 +133,45 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     if (tid == 0) item_start[n_reads] = carry;
 }
 
-// Each warp scans a contiguous range of work items; each item runs the per-warp filter
-// test and skip walks of kernel 2 with its read's table, every walk bounded by the read's
-// end.
-// The CTA's own numbering of the work items (P.smem_plan): s_start[r] = items of the reads
-// before r (an exclusive prefix sum over the reads, 256 threads with consecutive runs of
-// reads each), s_start[n_reads] = all items. The caller guarantees n_reads <= the shared
-// memory reserved for it and fewer than 2^31 items.
-__device__ void number_items(const BatchParams &P, int32_t *s_start, int32_t *s_warp)
+// Where a work item lies: its read, the read's bounds and table, the item's first offset.
+struct ItemMeta {
+    int64_t rs, re, base;
+    int32_t set;
+};
+
+// The metadata of work item `it` (the read from the plan's map, or by search past its
+// capacity: the last r with item_start[r] <= it).
+template <int LW>
+__device__ __forceinline__ ItemMeta item_meta(const BatchParams &P, int64_t it)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int32_t per = (P.n_reads + 255) / 256;
-    const int32_t r0 = min(P.n_reads, tid * per), r1 = min(P.n_reads, r0 + per);
-    int32_t mine = 0;
-    for (int32_t r = r0; r < r1; r++) {
-        int64_t rs, re;
-        read_bounds(P.read_off, r, P.n, &rs, &re);
-        const int32_t items = (int32_t)((re - rs + P.item - 1) / P.item);
-        s_start[r] = mine;                 // within this thread's run, for now
-        mine += items;
-    }
-    int32_t incl = mine;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if (lane >= d) incl += o;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const int32_t ws = lane < 8 ? s_warp[lane] : 0;
-        int32_t wi = ws;
-#pragma unroll
-        for (int d = 1; d < 8; d <<= 1) {
-            const int32_t o = __shfl_up_sync(0xFFFFFFFFu, wi, d);
-            if (lane >= d) wi += o;
+    int32_t r = 0;
+    if (it < P.item_cap) {
+        r = P.item_read[it];
+    } else {
+        int32_t hi = P.n_reads - 1;
+        while (r < hi) {
+            const int32_t mid = (int32_t)(((int64_t)r + hi + 1) >> 1);
+            if (P.item_start[mid] <= it) r = mid;
+            else hi = mid - 1;
         }
-        if (lane < 8) s_warp[8 + lane] = wi - ws;
-        if (lane == 7) s_warp[16] = wi;
     }
-    __syncthreads();
-    const int32_t before = s_warp[8 + warp] + incl - mine;
-    for (int32_t r = r0; r < r1; r++) s_start[r] += before;
-    if (tid == 0) s_start[P.n_reads] = s_warp[16];
-    __syncthreads();
+    ItemMeta m;
+    read_bounds(P.read_off, r, P.n, &m.rs, &m.re);
+    m.set = P.read_set[r];
+    m.base = m.rs + (it - P.item_start[r]) * (32 * LW);
+    return m;
 }
 
+// Warp w takes work items w, w + W, w + 2W, ... (W warps in the grid); the metadata of
+// its next item is loaded before the current one is scanned, so those dependent loads
+// overlap the scan instead of preceding it.
 template <int LW>
 __global__ void __launch_bounds__(256, 4) batched_scan_kernel(const BatchParams P)
 {
     constexpr int kItem = 32 * LW;
     constexpr uint32_t kAll = LW == 32 ? 0xFFFFFFFFu : ((1u << LW) - 1u);
-    extern __shared__ __align__(16) uint8_t bsm[];
-    __shared__ int32_t s_warp[24];
     const int lane = threadIdx.x & 31;
-    const int32_t *s_start = nullptr;
-    const DeviceTable *sets = P.sets;
-    if (P.smem_sets) {
-        DeviceTable *s_sets = reinterpret_cast<DeviceTable *>(bsm + P.off_sets);
-        const int words = (int)(P.n_sets * sizeof(DeviceTable) / 4);
-        for (int i = threadIdx.x; i < words; i += blockDim.x)
-            reinterpret_cast<uint32_t *>(s_sets)[i] = reinterpret_cast<const uint32_t *>(P.sets)[i];
-        sets = s_sets;
-    }
-    if (P.smem_plan) {
-        number_items(P, reinterpret_cast<int32_t *>(bsm), s_warp);
-        s_start = reinterpret_cast<const int32_t *>(bsm);
-    } else {
-        __syncthreads();
-    }
-    const int64_t total = s_start ? (int64_t)s_start[P.n_reads] : P.item_start[P.n_reads];
+    const int64_t total = P.item_start[P.n_reads];
     const uint64_t pol = policy_evict_first();
     Sink K{};
     K.out = P.out;
@@ -208,73 +180,47 @@ __global__ void __launch_bounds__(256, 4) batched_scan_kernel(const BatchParams 
     K.defer_count = P.defer_count;
     const int64_t n_words = (P.n + 15) >> 4;
     const int64_t n_bw = (P.n + 31) >> 5;
-    // Warp g takes the contiguous items [g * per, (g + 1) * per): consecutive items mostly
-    // continue one read, so the read index only moves forward and the read's bounds and
-    // table are loaded again only when the read changes.
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t per = (total + warps - 1) / warps;
-    int64_t it = gw * per;
-    const int64_t it_end = min(total, it + per);
-    if (it >= it_end) return;
-    auto start_of = [&](int32_t r) -> int64_t { return s_start ? (int64_t)s_start[r] : P.item_start[r]; };
-    int32_t r = 0;
-    {
-        int32_t hi = P.n_reads - 1;                 // the last read r with start_of(r) <= it
-        while (r < hi) {
-            const int32_t mid = (r + hi + 1) >> 1;
-            if (start_of(mid) <= it) r = mid;
-            else hi = mid - 1;
-        }
-    }
-    int64_t rs, re;
-    read_bounds(P.read_off, r, P.n, &rs, &re);
-    int64_t r_start = start_of(r), r_next = start_of(r + 1);
-    int32_t set = P.read_set[r];
-    bool ok = set >= 0 && set < P.n_sets;
-    const DeviceTable *Tp = ok ? sets + set : sets;     // fields read where used (shared memory when cached)
-    for (; it < it_end; it++) {
-        while (it >= r_next) {                      // the next read with items (r_next <= total)
-            r++;
-            r_start = r_next;
-            r_next = start_of(r + 1);
-            read_bounds(P.read_off, r, P.n, &rs, &re);
-            const int32_t ns = P.read_set[r];
-            if (ns != set) {
-                set = ns;
-                ok = set >= 0 && set < P.n_sets;
-                Tp = ok ? sets + set : sets;
-            }
-        }
-        if (!ok) {
-            if (lane == 0) record_error(sets[0].status, PFAC_ERR_INVALID_ARG);
-            continue;
-        }
-        const int64_t base = rs + (it - r_start) * kItem;
-        const int64_t item_end = min(base + kItem, re);
-        // this lane's LW offsets and the 64 bases from its first one
-        const int64_t p0 = base + LW * lane;
-        const int64_t wi = p0 >> 4;
-        const uint32_t sh = (uint32_t)(p0 & 15) * 2;
-        uint32_t w[5];
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    ItemMeta m{};
+    if (it < total) m = item_meta<LW>(P, it);
+    while (it < total) {
+        const int64_t nxt = it + stride;
+        ItemMeta mn{};
+        if (nxt < total) mn = item_meta<LW>(P, nxt);
+        const int32_t set = m.set;
+        if (set < 0 || set >= P.n_sets) {
+            if (lane == 0) record_error(P.sets[0].status, PFAC_ERR_INVALID_ARG);
+        } else {
+            const DeviceTable T = P.sets[set];
+            const int64_t base = m.base, re = m.re;
+            const int64_t item_end = min(base + kItem, re);
+            // this lane's LW offsets and the 64 bases from its first one
+            const int64_t p0 = base + LW * lane;
+            const int64_t wi = p0 >> 4;
+            const uint32_t sh = (uint32_t)(p0 & 15) * 2;
+            uint32_t w[5];
 #pragma unroll
-        for (int k = 0; k < 5; k++) w[k] = (wi + k < n_words) ? __ldg(P.packed + wi + k) : 0u;
-        const uint32_t x0 = __funnelshift_r(w[0], w[1], sh), x1 = __funnelshift_r(w[1], w[2], sh);
-        const uint32_t x2 = __funnelshift_r(w[2], w[3], sh), x3 = __funnelshift_r(w[3], w[4], sh);
-        const int64_t bi = p0 >> 5;
-        const uint32_t sb = (uint32_t)(p0 & 31);
-        uint32_t iv[3];
+            for (int k = 0; k < 5; k++) w[k] = (wi + k < n_words) ? __ldg(P.packed + wi + k) : 0u;
+            const uint32_t x0 = __funnelshift_r(w[0], w[1], sh), x1 = __funnelshift_r(w[1], w[2], sh);
+            const uint32_t x2 = __funnelshift_r(w[2], w[3], sh), x3 = __funnelshift_r(w[3], w[4], sh);
+            const int64_t bi = p0 >> 5;
+            const uint32_t sb = (uint32_t)(p0 & 31);
+            uint32_t iv[3];
 #pragma unroll
-        for (int k = 0; k < 3; k++) iv[k] = (bi + k < n_bw) ? __ldg(P.invalid + bi + k) : 0xFFFFFFFFu;
-        uint64_t bad = ((uint64_t)__funnelshift_r(iv[1], iv[2], sb) << 32) | __funnelshift_r(iv[0], iv[1], sb);
-        const int64_t rem_read = re - p0;   // walks stop at the read's end
-        if (rem_read < 64) bad |= rem_read > 0 ? (~0ull << rem_read) : ~0ull;
-        const int64_t rem_item = item_end - p0;
-        const uint32_t valid = rem_item >= LW ? kAll : (rem_item > 0 ? ((1u << rem_item) - 1u) : 0u);
-        const bool vec_ok = (((uintptr_t)(P.out + base)) & 15u) == 0;
-        scan_lane_batch<true, false, false, true, LW>(*Tp, K, nullptr, nullptr, P.walk_loads, (uint32_t)set, P.packed,
-                                                      P.invalid, re, base, lane, x0, x1, x2, x3, bad, valid, vec_ok,
-                                                      pol);
+            for (int k = 0; k < 3; k++) iv[k] = (bi + k < n_bw) ? __ldg(P.invalid + bi + k) : 0xFFFFFFFFu;
+            uint64_t bad = ((uint64_t)__funnelshift_r(iv[1], iv[2], sb) << 32) | __funnelshift_r(iv[0], iv[1], sb);
+            const int64_t rem_read = re - p0;   // walks stop at the read's end
+            if (rem_read < 64) bad |= rem_read > 0 ? (~0ull << rem_read) : ~0ull;
+            const int64_t rem_item = item_end - p0;
+            const uint32_t valid = rem_item >= LW ? kAll : (rem_item > 0 ? ((1u << rem_item) - 1u) : 0u);
+            const bool vec_ok = (((uintptr_t)(P.out + base)) & 15u) == 0;
+            scan_lane_batch<true, false, false, true, LW>(T, K, nullptr, nullptr, P.walk_loads, (uint32_t)set,
+                                                          P.packed, P.invalid, re, base, lane, x0, x1, x2, x3, bad,
+                                                          valid, vec_ok, pol);
+        }
+        it = nxt;
+        m = mn;
     }
 }
 
@@ -300,7 +246,8 @@ int64_t batch_scratch_bytes(int64_t n, int32_t n_reads, int64_t defer_cap)
 {
     const int64_t words = (n + 15) / 16, bw = (n + 31) / 32;
     return 256 + ((words * 4 + 255) & ~255LL) + (((bw + 1) * 4 + 255) & ~255LL) +
-           ((((int64_t)n_reads + 1) * 8 + 255) & ~255LL) + defer_cap * (int64_t)sizeof(DeferItem);
+           ((((int64_t)n_reads + 1) * 8 + 255) & ~255LL) + ((item_capacity(n, n_reads) * 4 + 255) & ~255LL) +
+           defer_cap * (int64_t)sizeof(DeferItem);
 }
 
 int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *texts, int64_t n, const int64_t *read_off,
@@ -321,20 +268,13 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
     int64_t *item_start = (int64_t *)p;
     p += ((((int64_t)n_reads + 1) * 8) + 255) & ~255LL;
     const int64_t item_cap = item_capacity(n, n_reads);
+    int32_t *item_read = (int32_t *)p;
+    p += (item_cap * 4 + 255) & ~255LL;
     DeferItem *defer = (DeferItem *)p;
     if (cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     const int pack_blocks = (int)std::min<int64_t>((bw + 255) / 256, (int64_t)dp.num_sms * 16);
     pack_bits_kernel<<<std::max(1, pack_blocks), 256, 0, st>>>(texts, n, packed, invalid);
-    // Shared memory of a scan CTA (blocks_per_sm of them per SM, 48 KB at most each): the
-    // items' numbering when the reads fit (else the one-CTA plan kernel numbers them in
-    // global memory first), then the table descriptors when they fit too.
-    const int64_t per_cta = std::min<int64_t>(48 * 1024, (int64_t)dp.smem_per_sm / blocks_per_sm - 1024);
-    const int64_t plan_bytes = (((int64_t)n_reads + 1) * 4 + 15) & ~15LL;
-    const bool smem_plan = plan_bytes <= per_cta && item_cap < 0x7FFFFFFFLL;
-    const int64_t sets_bytes = (int64_t)n_sets * (int64_t)sizeof(DeviceTable);
-    const bool smem_sets = (smem_plan ? plan_bytes : 0) + sets_bytes <= per_cta;
-    const int64_t smem = (smem_plan ? plan_bytes : 0) + (smem_sets ? sets_bytes : 0);
-    if (!smem_plan) plan_kernel<<<1, 1024, 0, st>>>(read_off, n_reads, n, 32 * lw, item_start);
+    plan_kernel<<<1, 1024, 0, st>>>(read_off, n_reads, n, 32 * lw, item_start, item_read, item_cap);
     BatchParams P{};
     P.sets = d_sets;
     P.n_sets = n_sets;
@@ -345,17 +285,16 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
     P.read_set = read_set;
     P.n_reads = n_reads;
     P.item_start = item_start;
+    P.item_read = item_read;
+    P.item_cap = item_cap;
     P.out = out;
     P.defer = defer;
     P.defer_cap = defer_cap;
     P.defer_count = counters + 1;
     P.item = 32 * lw;
     P.walk_loads = bc.walk_loads > 0 ? bc.walk_loads : 2;
-    P.smem_plan = smem_plan;
-    P.smem_sets = smem_sets;
-    P.off_sets = (uint32_t)(smem_plan ? plan_bytes : 0);
-    if (lw == 32) batched_scan_kernel<32><<<dp.num_sms * blocks_per_sm, 256, (size_t)smem, st>>>(P);
-    else batched_scan_kernel<16><<<dp.num_sms * blocks_per_sm, 256, (size_t)smem, st>>>(P);
+    if (lw == 32) batched_scan_kernel<32><<<dp.num_sms * blocks_per_sm, 256, 0, st>>>(P);
+    else batched_scan_kernel<16><<<dp.num_sms * blocks_per_sm, 256, 0, st>>>(P);
     batched_tail_kernel<<<dp.num_sms * 4, 256, 0, st>>>(P);
     return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
 }
