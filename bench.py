@@ -575,7 +575,8 @@ def configs_suite(steps: int):
     # the same table built with the 10-gram screen too (pfac_build_opts.sample = 1)
     table10 = b.Table((w.blob, w.offsets), sample=1)
     cfgs = [dict(), dict(screen=2, sample=1), dict(screen=2, walk_loads=1, sample=1),
-            dict(screen=2, rank_in_smem=-1, sample=1), dict(zero_writer=2), dict(zero_writer=3), dict(stages=2),
+            dict(screen=2, rank_in_smem=-1, sample=1), dict(zero_writer=2), dict(zero_writer=3), dict(zero_writer=4),
+            dict(zero_writer=4, walk_loads=1), dict(zero_writer=4, stages=4), dict(stages=2),
             dict(stages=4), dict(walk_loads=1), dict(rank_in_smem=-1), dict(lane_offsets=16, stages=4)]
     for cfg in cfgs:
         cfg = dict(cfg)

@@ -273,9 +273,12 @@ typedef struct {
                                 output): 0 = automatic, 1 = each consumer warp stores its
                                 own, 2 = one warp of the CTA stores them all with 16-byte
                                 stores, 3 = one warp stores them with TMA bulk copies of a
-                                zero tile in shared memory. With 2 and 3 the consumer warps
-                                store a match only after the writer has published that its
-                                tile's zeros are written. */
+                                zero tile in shared memory, 4 = each consumer warp stores its
+                                own with TMA bulk copies of that tile. With 2 and 3 the
+                                consumer warps store a match only after the writer has
+                                published that its tile's zeros are written; with 4 a warp
+                                stores the matches of a tile only once that tile's bulk
+                                copies have completed. */
     int32_t screen;          /* kernel 2, packed text, prefix filter too large for shared
                                 memory: which screen picks the offsets whose filter bit is
                                 read from global memory: 0 = automatic (the sampled screen

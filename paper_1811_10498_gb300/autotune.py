@@ -36,7 +36,7 @@ SCAN_KNOBS = [
     ("stages", (2, 3, 4, 6)),
     ("walk_loads", (1, 2, 3, 4)),
     ("rank_in_smem", (0, -1)),
-    ("zero_writer", (1, 2, 3)),
+    ("zero_writer", (1, 2, 3, 4)),
 ]
 # l2_persist is not searched: the persisting set-aside is a limit of the whole context,
 # and on the genome-scale workload (skip entries 17 MB, already L2-resident) the window

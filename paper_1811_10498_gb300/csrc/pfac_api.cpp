@@ -671,7 +671,7 @@ int pfac_set_config(pfac_handle h, const pfac_config *cfg)
             cfg->stages < 0 || cfg->stages == 1 || cfg->stages > 8 || cfg->walk_loads < 0 ||
             (cfg->lane_offsets != 0 && cfg->lane_offsets != 16 && cfg->lane_offsets != 32) ||
             cfg->table_layout < 0 || cfg->table_layout > 2 || cfg->row_loads < 0 || cfg->row_loads > 2 ||
-            cfg->text_smem < 0 || cfg->text_smem > 1 || cfg->zero_writer < 0 || cfg->zero_writer > 3 ||
+            cfg->text_smem < 0 || cfg->text_smem > 1 || cfg->zero_writer < 0 || cfg->zero_writer > 4 ||
             cfg->screen < 0 || cfg->screen > 2 || cfg->reserved != 0)
             return fail(PFAC_ERR_INVALID_ARG);
         if (cfg->kernel == 2 && !(h->skip_bytes > 0 && h->host.filter_b > 0)) return fail(PFAC_ERR_UNSUPPORTED);

@@ -169,7 +169,8 @@ struct TiledConfig {
                                // screen (when available)
     int32_t zero_writer;       // dense packed scans, 32 offsets per lane: 0 = consumer warps
                                // store their zeros, 1 = a writer warp with 16-byte stores,
-                               // 2 = a writer warp with TMA bulk stores of a zero tile
+                               // 2 = a writer warp with TMA bulk stores of a zero tile,
+                               // 3 = consumer warps with TMA bulk stores of a zero tile
     int64_t timeout_ns;        // limit of every bounded wait
 };
 

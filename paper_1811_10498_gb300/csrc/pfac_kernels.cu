@@ -414,6 +414,7 @@ __device__ __forceinline__ uint32_t ld_acquire_cta(const volatile uint32_t *p)
 
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_2() { asm volatile("cp.async.bulk.wait_group 2;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_1() { asm volatile("cp.async.bulk.wait_group 1;" ::: "memory"); }
 
 // The zero writer of dense packed scans (a warp of its own, so that the consumer warps
 // only test, walk and store matches). For each tile round k of the CTA it writes the
@@ -595,7 +596,9 @@ __device__ __forceinline__ uint32_t filter_bits_of(const DeviceTable &T, uint32_
 // shared memory at offset 0 in place of the order-10 filter, which is read from global
 // memory for the offsets the screen lets through.
 // ZW (dense packed scans): 0 = each consumer warp stores its own zeros; 1 or 2 = a zero
-// writer warp (warp consumers + 1) stores them (see zero_writer).
+// writer warp (warp consumers + 1) stores them (see zero_writer); 3 = each consumer warp
+// stores its own zeros with TMA bulk copies of a zero tile, and stores the matches of a
+// tile only once that tile's bulk group has completed.
 template <bool PACKED, bool COMPACT, bool FSMEM, bool RANK16, int LW, bool ALL = false, int SCR = 0, int ZW = 0>
 __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
 {
@@ -626,7 +629,7 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
         *zdone = 0;
         fence_mbar_init();
     }
-    if (ZW == 2 && tid < 32) {
+    if ((ZW == 2 || ZW == 3) && tid < 32) {
         // the zero tile the writer's bulk stores read; made visible to the async proxy
         for (uint32_t i = 16 * (uint32_t)tid; i < P.zero_chunk; i += 16 * 32)
             *reinterpret_cast<int4 *>(smem + P.off_zero + i) = make_int4(0, 0, 0, 0);
@@ -662,7 +665,7 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
     const int unit = PACKED ? 4 : 1;
     const int64_t tile_units = PACKED ? (P.tile >> 4) : P.tile;
 
-    if (ZW && warp == P.consumers + 1) {
+    if ((ZW == 1 || ZW == 2) && warp == P.consumers + 1) {
         zero_writer<ZW>(P, smem, zdone, lane);
         return;
     }
@@ -714,7 +717,10 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
     for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, k++) {
         const int st = k % S;
         if (!wait_or_abort(smem_addr(&full[st]), (uint32_t)((k / S) & 1), P.timeout_ns, abort_flag)) {
-            if (lane == 0) record_error(T.status, PFAC_ERR_TIMEOUT);
+            if (lane == 0) {
+                record_error(T.status, PFAC_ERR_TIMEOUT);
+                if (ZW == 3) bulk_wait_all();
+            }
             return;
         }
         const uint8_t *stage = stage0 + (size_t)st * P.stage_bytes;
@@ -760,9 +766,26 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_addr(&empty[st]));
             if (!COMPACT && !ZW) zero_batch<LW>(K, warp_base, lane, valid, true, pol);
+            if constexpr (ZW == 3) {
+                // the warp's zeros as bulk copies, one bulk group per tile (empty past the
+                // text's end), the last < 4 ids by plain stores
+                const int64_t cnt = min((int64_t)(32 * LW), n - warp_base);
+                if (lane == 0) {
+                    if (cnt > 0) {
+                        uint8_t *dst = reinterpret_cast<uint8_t *>(P.out + warp_base);
+                        const int64_t full = (cnt * 4) & ~(int64_t)15;
+                        const uint32_t zb = smem_addr(smem + P.off_zero);
+                        for (int64_t bb = 0; bb < full; bb += P.zero_chunk)
+                            bulk_store(dst + bb, zb, (uint32_t)min((int64_t)P.zero_chunk, full - bb), pol);
+                        for (int64_t i = full / 4; i < cnt; i++) P.out[warp_base + i] = 0;
+                    }
+                    bulk_commit();
+                }
+            }
             // Zeros stored above by one lane are ordered before matches stored by another
             // lane in a later round by the warp barriers between them (this one first).
             __syncwarp();
+            uint32_t qold = qcount;          // queued offsets of earlier tiles
 
             // Queue the offsets that pass: lane l's items take the places after those of
             // lanes 0 .. l-1 (exclusive prefix of the counts, by ballots).
@@ -789,9 +812,22 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                 qcount += take;
                 total -= take;
                 __syncwarp();
-                if (ZW && qcount >= 32 && !wait_zeros(zdone, (uint32_t)k + 1, P.timeout_ns, abort_flag)) {
+                if ((ZW == 1 || ZW == 2) && qcount >= 32 &&
+                    !wait_zeros(zdone, (uint32_t)k + 1, P.timeout_ns, abort_flag)) {
                     if (lane == 0) record_error(T.status, PFAC_ERR_TIMEOUT);
                     return;
+                }
+                if (ZW == 3 && qcount >= 32) {
+                    // rounds of earlier tiles need their bulk groups complete (all but this
+                    // tile's); a round with this tile's offsets needs this tile's too
+                    const uint32_t taken = qcount & ~31u;
+                    if (lane == 0) {
+                        if (taken <= qold) bulk_wait_1();
+                        else bulk_wait_all();
+                        fence_proxy_async_global();
+                    }
+                    __syncwarp();
+                    qold -= min(qold, taken);
                 }
                 while (qcount >= 32) {
                     queue_round<COMPACT, FSMEM, RANK16, ALL>(P, K, sf, rank_ptr, queue, qhead, 32, lane);
@@ -856,8 +892,13 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
                                                                 valid, true, pol);
         }
     }
+    if (ZW == 3 && lane == 0) {
+        bulk_wait_all();                 // every bulk copy of the warp has read its source
+        fence_proxy_async_global();
+    }
+    __syncwarp();
     if (PACKED && qcount) {
-        if (ZW && !wait_zeros(zdone, (uint32_t)k, P.timeout_ns, abort_flag)) {
+        if ((ZW == 1 || ZW == 2) && !wait_zeros(zdone, (uint32_t)k, P.timeout_ns, abort_flag)) {
             if (lane == 0) record_error(T.status, PFAC_ERR_TIMEOUT);
             return;
         }
@@ -923,10 +964,13 @@ static ScanLayout scan_layout(int consumers, int lw, int stages, int64_t filter_
 static int zero_writer_of(const TiledConfig &cfg, bool packed, bool compact, bool all)
 {
     if (!packed || compact || all || cfg.lane_offsets != 32) return 0;
-    return cfg.zero_writer == 1 || cfg.zero_writer == 2 ? cfg.zero_writer : 0;
+    return cfg.zero_writer >= 1 && cfg.zero_writer <= 3 ? cfg.zero_writer : 0;
 }
 
-static int consumers_of(const TiledConfig &cfg, int zw = 0) { return cfg.threads / 32 - 1 - (zw ? 1 : 0); }
+static int consumers_of(const TiledConfig &cfg, int zw = 0)
+{
+    return cfg.threads / 32 - 1 - ((zw == 1 || zw == 2) ? 1 : 0);
+}
 static int lane_width_of(const TiledConfig &cfg) { return cfg.lane_offsets == 32 ? 32 : 16; }
 static int stages_of(const TiledConfig &cfg, bool packed) { return cfg.stages > 0 ? cfg.stages : (packed ? 3 : 2); }
 
@@ -938,7 +982,7 @@ struct SmemPlan {
     int scr;                            // 1: filter_bytes hold the first-level filter;
                                         // 2: the sampled screen (global memory) is used
     int zw;                             // zero writer (0 = the consumer warps)
-    int64_t zero_chunk;                 // bytes of the bulk-store zero tile (zw == 2)
+    int64_t zero_chunk;                 // bytes of the bulk-store zero tile (zw == 2 or 3)
 };
 
 // With a bulk-store zero writer (zw == 2) the zero tile comes after the filter and before
@@ -956,7 +1000,7 @@ static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool pac
     const int64_t words = t.filter_b >= 3 ? ((int64_t)1 << (2 * t.filter_b)) / 32 : 1;
     const int64_t fbytes = words * 4;
     const int64_t rbytes = words * (t.rank_wide ? 4 : 2);
-    int64_t zb = zw == 2 ? 2048 : 0;
+    int64_t zb = (zw == 2 || zw == 3) ? 2048 : 0;
     auto total = [&](int64_t f, int64_t r) { return (int64_t)scan_layout(C, LW, S, f, r, packed, zb).total; };
     if (total(0, 0) > limit) {
         pl.total = -1;
@@ -980,12 +1024,13 @@ static SmemPlan plan_smem(const DeviceTable &t, const TiledConfig &cfg, bool pac
             pl.scr = 1;
         }
     }
-    if (zw == 2 && total(pl.filter_bytes, 0) > limit) {
-        zw = pl.zw = 1;                  // no room for a zero tile: 16-byte stores instead
+    if ((zw == 2 || zw == 3) && total(pl.filter_bytes, 0) > limit) {
+        zw = pl.zw = zw == 2 ? 1 : 0;    // no room for a zero tile: 16-byte stores instead
         zb = 0;
     }
     pl.rank_bytes = ((pl.scr == 0 || pl.scr == 3) && cfg.smem_table_bytes >= 0 &&
                      total(pl.filter_bytes, rbytes) <= limit) ? rbytes : 0;
+    if (zw == 3) pl.zero_chunk = zb;
     if (zw == 2) {
         for (int64_t c = 16384; c > 2048; c >>= 1) {
             zb = c;
@@ -1082,6 +1127,7 @@ static void (*scan_kernel_for(bool lw32, int zw))(const ScanParams)
     if constexpr (PACKED && !COMPACT && !ALL) {
         if (zw == 1) return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, SCR, 1>;
         if (zw == 2) return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, SCR, 2>;
+        if (zw == 3) return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, SCR, 3>;
     }
     if constexpr (SCR >= 2) {
         return scan_kernel<PACKED, COMPACT, FSMEM, RANK16, 32, ALL, SCR>;

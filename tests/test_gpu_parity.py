@@ -77,6 +77,9 @@ def genome_small():
     dict(kernel=2, zero_writer=3, threads=96, stages=2),
     dict(kernel=2, zero_writer=3, rank_in_smem=-1),
     dict(kernel=2, zero_writer=3, walk_loads=1),
+    dict(kernel=2, zero_writer=4),
+    dict(kernel=2, zero_writer=4, threads=96, stages=2),
+    dict(kernel=2, zero_writer=4, walk_loads=1, rank_in_smem=-1),
     dict(kernel=2, screen=1),
 ], ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
 def test_genome_configs(genome_small, cfg, packed):
@@ -165,13 +168,13 @@ def test_empty_text():
 
 
 @pytest.mark.parametrize("threads,lw,zw", [(64, 16, 0), (128, 32, 0), (1024, 16, 0), (1024, 32, 0), (96, 32, 2),
-                                           (96, 32, 3), (1024, 32, 3)])
+                                           (96, 32, 3), (1024, 32, 3), (64, 32, 4), (1024, 32, 4)])
 def test_matches_across_tile_edges(threads, lw, zw):
     """Long patterns planted so they start just before, at and after tile edges (a tile
     is 32 x lw bases per consumer warp; a zero-writer warp takes one warp from the
     consumers) and end exactly at a tile edge, at a 32-base lane batch edge, at a 64-base
     window edge, and at the text end."""
-    tile = 32 * lw * (threads // 32 - 1 - (zw > 1))
+    tile = 32 * lw * (threads // 32 - 1 - (zw in (2, 3)))
     rng = datagen.rng_for(99)
     n = tile * 6 + 37
     text = datagen.iid_text(n, rng)
@@ -367,8 +370,9 @@ def test_host_pointers_rejected():
 
 
 @pytest.mark.parametrize("cfg", [dict(kernel=2, lane_offsets=32, walk_loads=8), dict(kernel=2, walk_loads=64),
-                                 dict(kernel=2, zero_writer=2, walk_loads=8), dict(kernel=2, zero_writer=3, walk_loads=8)],
-                         ids=["lw32_loads8", "lw16_loads64", "writer16B_loads8", "writerbulk_loads8"])
+                                 dict(kernel=2, zero_writer=2, walk_loads=8), dict(kernel=2, zero_writer=3, walk_loads=8),
+                                 dict(kernel=2, zero_writer=4, walk_loads=8)],
+                         ids=["lw32_loads8", "lw16_loads64", "writer16B_loads8", "writerbulk_loads8", "warpbulk_loads8"])
 def test_repeated_scans_with_long_walks_in_kernel(genome_small, cfg):
     """Matches found inside the scan kernel are stored by the lane that walks them,
     after the zero stores of the lane that owns the offset; repeated runs must agree
