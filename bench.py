@@ -535,6 +535,48 @@ def paper_suite(args):
     ref.close()
 
 
+def large_suite(args):
+    """The large-dictionary workload at `--n-bases` bases (10^6 patterns of 16-64 bases),
+    scanned `--steps` times (dense ids, L2 flushed before each), with the table built
+    the default way (order-14 filter, sampled 13-gram screen) or as round 1 built it
+    (`--large-structure order12`: order-12 filter behind the order-10 first-level
+    filter). One JSON line."""
+    import torch
+    from paper_1811_10498_gb300 import _binding as b
+    from paper_1811_10498_gb300 import build_ext, datagen
+    build_ext.build()
+    w = datagen.large_dict_scan(seed=3, n_bases=args.n_bases)
+    n = int(w.text.size)
+    kw = dict(filter_b=12, sample=-1) if args.large_structure == "order12" else {}
+    table = b.Table((w.blob, w.offsets), **kw)
+    d = torch.from_numpy(w.text).cuda()
+    packed, _, _ = b.pack(d)
+    del d
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    b.pfac_match_packed(table.h, packed, n, out)
+    ts = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.pfac_match_packed(table.h, packed, n, out)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    peak, _ = measured_hbm()
+    info = table.info
+    print(json.dumps({"suite": "large", "workload": w.name, "structure": args.large_structure, "bases": n,
+                      "filter_b": info["filter_b"], "sample_q": info["sample_q"], "n_states": info["n_states"],
+                      "ms": ms, "gbases_s": n / ms / 1e6,
+                      "roofline_frac": BYTES_PER_BASE * n / (ms * 1e-3) / (peak * 1e9),
+                      "matches": int((out != 0).sum().item()), "device_status": b.pfac_device_status(table.h),
+                      "launches": 1 + args.steps}), flush=True)
+    table.close()
+
+
 def ceilings_suite():
     """The hardware ceilings behind the kernels' design (csrc/ceilings.cu, built here with
     nvcc for sm_103a): store bandwidth for 1 GiB of ids by several store paths, and random
@@ -664,10 +706,13 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the large-dictionary (10^6 patterns) leg")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--no-tune", action="store_true", help="use the library's default launch configuration")
-    ap.add_argument("--suite", default=None, choices=["paper", "batched", "ceilings", "configs"],
+    ap.add_argument("--large-structure", default="default", choices=["default", "order12"],
+                    help="--suite large: the table's filter structure")
+    ap.add_argument("--suite", default=None, choices=["paper", "batched", "ceilings", "configs", "large"],
                     help="paper: the paper's placement, pattern-set and input-size experiments (many lines); "
                          "batched: the batched workload alone; ceilings: store and lookup rates of the GPU; "
-                         "configs: kernel-2 launch configurations on the benchmark's workload")
+                         "configs: kernel-2 launch configurations on the benchmark's workload; "
+                         "large: the large-dictionary workload at --n-bases")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -676,6 +721,9 @@ def main():
         return
     if args.suite == "paper":
         paper_suite(args)
+        return
+    if args.suite == "large":
+        large_suite(args)
         return
     if args.suite == "ceilings":
         ceilings_suite()
