@@ -549,6 +549,8 @@ def large_suite(args):
     n = int(w.text.size)
     kw = dict(filter_b=12, sample=-1) if args.large_structure == "order12" else {}
     table = b.Table((w.blob, w.offsets), **kw)
+    if args.large_config:
+        b.pfac_set_config(table.h, json.loads(args.large_config))
     d = torch.from_numpy(w.text).cuda()
     packed, _, _ = b.pack(d)
     del d
@@ -568,7 +570,8 @@ def large_suite(args):
     ms = statistics.median(ts)
     peak, _ = measured_hbm()
     info = table.info
-    print(json.dumps({"suite": "large", "workload": w.name, "structure": args.large_structure, "bases": n,
+    print(json.dumps({"suite": "large", "workload": w.name, "structure": args.large_structure,
+                      "config": b.pfac_get_config(table.h, n), "bases": n,
                       "filter_b": info["filter_b"], "sample_q": info["sample_q"], "n_states": info["n_states"],
                       "ms": ms, "gbases_s": n / ms / 1e6,
                       "roofline_frac": BYTES_PER_BASE * n / (ms * 1e-3) / (peak * 1e9),
@@ -708,6 +711,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="use the library's default launch configuration")
     ap.add_argument("--large-structure", default="default", choices=["default", "order12"],
                     help="--suite large: the table's filter structure")
+    ap.add_argument("--large-config", default="", help="--suite large: a launch configuration (JSON of pfac_config "
+                                                        "fields) applied to the table")
     ap.add_argument("--suite", default=None, choices=["paper", "batched", "ceilings", "configs", "large"],
                     help="paper: the paper's placement, pattern-set and input-size experiments (many lines); "
                          "batched: the batched workload alone; ceilings: store and lookup rates of the GPU; "

@@ -242,9 +242,11 @@ typedef struct {
     int32_t rank_in_smem;    /* kernel 2: -1 = keep the filter's rank index in global
                                 memory, 0 = in shared memory when it fits */
     int32_t l2_persist;      /* 1 = keep the skip entries in L2 with an access-policy
-                                window (this sets the context's persisting-L2 limit,
-                                which the next launch without the window gives back),
-                                -1 or 0 = no window */
+                                window, 2 = keep the prefix filter and the sampled screen
+                                in L2 (tables with a sampled screen; both sit side by side
+                                in the table's memory) (either sets the context's
+                                persisting-L2 limit, which the next launch without a window
+                                gives back), -1 or 0 = no window */
     int32_t walk_loads;      /* kernel 2: dependent table loads a walk may take before it
                                 is handed to the tail kernel (0 = 2) */
     int32_t lane_offsets;    /* kernel 2: consecutive offsets per consumer lane, 16 or 32

@@ -443,12 +443,13 @@ pfac_handle pfac_build_ex(const char *const *patterns, const int32_t *lengths, i
             {(const void **)&h->dt.rows, T.rows.data(), T.rows.size() * 4},
             {(const void **)&h->dt.out_id, T.out_id.data(), T.out_id.size() * 4},
             {(const void **)&h->dt.skip, T.skip.data(), T.skip.size() * 4},
+            // the filter and the sampled screen side by side: one L2 window can cover both
             {(const void **)&h->dt.filter, T.filter.data(), T.filter.size() * 4},
+            {(const void **)&h->dt.sample, T.sample.data(), T.sample.size() * 4},
             {(const void **)&h->dt.rank, T.rank_wide ? (const void *)T.rank32.data() : (const void *)T.rank16.data(),
              rank_bytes},
             {(const void **)&h->dt.dense, T.dense.data(), T.dense.size() * 4},
             {(const void **)&h->dt.filter1, T.filter1.data(), T.filter1.size() * 4},
-            {(const void **)&h->dt.sample, T.sample.data(), T.sample.size() * 4},
         };
         size_t total = 256;   // status word
         for (auto &p : parts) total += round256(p.bytes);
@@ -672,7 +673,7 @@ int pfac_set_config(pfac_handle h, const pfac_config *cfg)
             (cfg->lane_offsets != 0 && cfg->lane_offsets != 16 && cfg->lane_offsets != 32) ||
             cfg->table_layout < 0 || cfg->table_layout > 2 || cfg->row_loads < 0 || cfg->row_loads > 2 ||
             cfg->text_smem < 0 || cfg->text_smem > 1 || cfg->zero_writer < 0 || cfg->zero_writer > 4 ||
-            cfg->screen < 0 || cfg->screen > 2 || cfg->reserved != 0)
+            cfg->screen < 0 || cfg->screen > 2 || cfg->reserved != 0 || cfg->l2_persist < -1 || cfg->l2_persist > 2)
             return fail(PFAC_ERR_INVALID_ARG);
         if (cfg->kernel == 2 && !(h->skip_bytes > 0 && h->host.filter_b > 0)) return fail(PFAC_ERR_UNSUPPORTED);
         const int rc = ensure_paper_layout(h, cfg->table_layout);

@@ -495,18 +495,18 @@ int build_device_tables(const uint8_t *d_blob, const int64_t *d_off, int32_t n, 
                  {out_id, (size_t)S * 4},
                  {skip, with_skip ? (size_t)S * 16 : 0},
                  {filter, (size_t)words * 4},
+                 {sample, sample_bytes},
                  {rank_wide ? (const void *)rank32 : (const void *)rank16, filter_b ? rank_bytes : 0},
                  {dense, (size_t)count * 16},
-                 {filter1, filter1 ? ((size_t)1 << (2 * kFilter1B)) / 8 : 0},
-                 {sample, sample_bytes}};
+                 {filter1, filter1 ? ((size_t)1 << (2 * kFilter1B)) / 8 : 0}};
     size_t total = 256;
     for (auto &p : parts) total += r256(p.bytes);
     void *mem = nullptr;
     PFAC_CK(cudaMalloc(&mem, total));
     uint8_t *base = (uint8_t *)mem;
     const void **dst[] = {(const void **)&out->dt.rows, (const void **)&out->dt.out_id, (const void **)&out->dt.skip,
-                          (const void **)&out->dt.filter, (const void **)&out->dt.rank, (const void **)&out->dt.dense,
-                          (const void **)&out->dt.filter1, (const void **)&out->dt.sample};
+                          (const void **)&out->dt.filter, (const void **)&out->dt.sample, (const void **)&out->dt.rank,
+                          (const void **)&out->dt.dense, (const void **)&out->dt.filter1};
     cudaError_t e = cudaMemsetAsync(base, 0, 256, st);
     size_t o = 256;
     for (size_t i = 0; i < sizeof(parts) / sizeof(parts[0]); i++) {

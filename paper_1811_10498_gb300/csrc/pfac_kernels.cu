@@ -1078,8 +1078,19 @@ static cudaError_t launch_with_policy(Kern kern, const ScanParams &P, int grid, 
     cudaLaunchAttribute attr[1];
     lc.attrs = attr;
     lc.numAttrs = 0;
+    // the window: the skip entries (l2_persist 1), or the prefix filter and the sampled
+    // screen, adjacent in the table's allocation (l2_persist 2, tables with a screen)
     const int64_t skip_bytes = P.t.n_states * 16;
-    if (cfg.l2_persist > 0 && dp.persist_l2_max > 0 && skip_bytes > 0) {
+    const void *win_base = P.t.skip;
+    int64_t win_bytes = skip_bytes;
+    if (cfg.l2_persist == 2) {
+        win_base = P.t.filter;
+        win_bytes = P.t.sample && P.t.filter
+                        ? (int64_t)((const uint8_t *)P.t.sample - (const uint8_t *)P.t.filter) +
+                              ((int64_t)1 << (2 * P.t.sample_q)) / 8
+                        : 0;
+    }
+    if (cfg.l2_persist > 0 && dp.persist_l2_max > 0 && win_bytes > 0) {
         const int dev = dp.device;
         {
             std::lock_guard<std::mutex> lk(g_persist_mu);
@@ -1091,9 +1102,9 @@ static cudaError_t launch_with_policy(Kern kern, const ScanParams &P, int grid, 
         }
         int max_win = 0;
         cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, dev);
-        const int64_t win = std::min<int64_t>(skip_bytes, max_win);
+        const int64_t win = std::min<int64_t>(win_bytes, max_win);
         attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-        attr[0].val.accessPolicyWindow.base_ptr = (void *)P.t.skip;
+        attr[0].val.accessPolicyWindow.base_ptr = (void *)win_base;
         attr[0].val.accessPolicyWindow.num_bytes = (size_t)win;
         attr[0].val.accessPolicyWindow.hitRatio =
             (float)std::min<double>(1.0, (double)dp.persist_l2_max / (double)std::max<int64_t>(win, 1));

@@ -82,7 +82,7 @@ def test_launch_configuration_checks(cuda_lib_path):
         for field, bad in [("kernel", 3), ("kernel", -1), ("threads", 100), ("threads", 32), ("threads", 2048),
                            ("ctas_per_sm", 33), ("stages", 1), ("stages", 9), ("walk_loads", -1),
                            ("lane_offsets", 8), ("lane_offsets", 64), ("table_layout", 3), ("table_layout", -1),
-                           ("row_loads", 3), ("text_smem", 2), ("zero_writer", 5), ("zero_writer", -1)]:
+                           ("row_loads", 3), ("text_smem", 2), ("zero_writer", 5), ("zero_writer", -1), ("l2_persist", 3), ("l2_persist", -2)]:
             with pytest.raises(b.PfacError) as e:
                 b.pfac_set_config(h, dict(good, **{field: bad}))
             assert e.value.code == b.CODE["PFAC_ERR_INVALID_ARG"], (field, bad)

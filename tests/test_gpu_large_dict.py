@@ -31,7 +31,7 @@ def dictionary():
 
 
 @pytest.mark.parametrize("filter_b", [14, 12, 11])
-@pytest.mark.parametrize("cfg", [dict(), dict(screen=1), dict(screen=2), dict(screen=2, zero_writer=2),
+@pytest.mark.parametrize("cfg", [dict(), dict(screen=1), dict(screen=2), dict(screen=2, zero_writer=2), dict(l2_persist=2),
                                  dict(screen=2, rank_in_smem=-1, walk_loads=1), dict(lane_offsets=16)],
                          ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()) or "auto")
 def test_dense_ids(dictionary, filter_b, cfg):
