@@ -83,7 +83,11 @@ __device__ __forceinline__ void read_bounds(const int64_t *read_off, int32_t r, 
     *re = b;
 }
 
-// One CTA: exclusive prefix of the number of work items per read.
+// One CTA: exclusive prefix of the number of work items per read. The reads' bounds are
+// loaded kPlanRounds rounds of 1,024 reads at a time, all loads in flight together, before
+// the rounds' block scans run one after another.
+constexpr int kPlanRounds = 8;
+
 __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ read_off, int32_t n_reads, int64_t n,
                                                     int32_t item, int64_t *__restrict__ item_start,
                                                     int32_t *__restrict__ item_read, int64_t item_cap)
@@ -93,42 +97,53 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) carry = 0;
     __syncthreads();
-    for (int64_t base = 0; base < n_reads; base += blockDim.x) {
-        const int64_t r = base + tid;
-        int64_t v = 0;
-        if (r < n_reads) {
-            int64_t rs, re;
-            read_bounds(read_off, (int32_t)r, n, &rs, &re);
-            v = (re - rs + item - 1) / item;
-        }
-        int64_t incl = v;
-        for (int d = 1; d < 32; d <<= 1) {
-            const int64_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-            if (lane >= d) incl += o;
-        }
-        if (lane == 31) warp_sum[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            int64_t ws = lane < (int)(blockDim.x >> 5) ? warp_sum[lane] : 0;
-            for (int d = 1; d < 32; d <<= 1) {
-                const int64_t o = __shfl_up_sync(0xFFFFFFFFu, ws, d);
-                if (lane >= d) ws += o;
+    for (int64_t base0 = 0; base0 < n_reads; base0 += (int64_t)kPlanRounds * blockDim.x) {
+        int64_t items[kPlanRounds];
+#pragma unroll
+        for (int q = 0; q < kPlanRounds; q++) {
+            const int64_t r = base0 + (int64_t)q * blockDim.x + tid;
+            items[q] = 0;
+            if (r < n_reads) {
+                int64_t rs, re;
+                read_bounds(read_off, (int32_t)r, n, &rs, &re);
+                items[q] = (re - rs + item - 1) / item;
             }
-            warp_sum[lane] = ws;   // inclusive over warps
         }
-        __syncthreads();
-        const int64_t before = (warp ? warp_sum[warp - 1] : 0) + incl - v;
-        if (r < n_reads) {
-            const int64_t k0 = carry + before;
-            item_start[r] = k0;
-            // the read of each of this read's work items (items past item_cap are found
-            // by search instead)
-            const int64_t k1 = min(k0 + v, item_cap);
-            for (int64_t k = k0; k < k1; k++) item_read[k] = (int32_t)r;
+#pragma unroll
+        for (int q = 0; q < kPlanRounds; q++) {
+            const int64_t base = base0 + (int64_t)q * blockDim.x;
+            if (base >= n_reads) break;
+            const int64_t r = base + tid;
+            const int64_t v = items[q];
+            int64_t incl = v;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+                if (lane >= d) incl += o;
+            }
+            if (lane == 31) warp_sum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                int64_t ws = lane < (int)(blockDim.x >> 5) ? warp_sum[lane] : 0;
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int64_t o = __shfl_up_sync(0xFFFFFFFFu, ws, d);
+                    if (lane >= d) ws += o;
+                }
+                warp_sum[lane] = ws;   // inclusive over warps
+            }
+            __syncthreads();
+            const int64_t before = (warp ? warp_sum[warp - 1] : 0) + incl - v;
+            if (r < n_reads) {
+                const int64_t k0 = carry + before;
+                item_start[r] = k0;
+                // the read of each of this read's work items (items past item_cap are found
+                // by search instead)
+                const int64_t k1 = min(k0 + v, item_cap);
+                for (int64_t k = k0; k < k1; k++) item_read[k] = (int32_t)r;
+            }
+            __syncthreads();
+            if (tid == 0) carry += warp_sum[(blockDim.x >> 5) - 1];
+            __syncthreads();
         }
-        __syncthreads();
-        if (tid == 0) carry += warp_sum[(blockDim.x >> 5) - 1];
-        __syncthreads();
     }
     if (tid == 0) item_start[n_reads] = carry;
 }
