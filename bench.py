@@ -548,6 +548,8 @@ def large_suite(args):
     w = datagen.large_dict_scan(seed=3, n_bases=args.n_bases)
     n = int(w.text.size)
     kw = dict(filter_b=12, sample=-1) if args.large_structure == "order12" else {}
+    if args.large_filter_b:
+        kw["filter_b"] = args.large_filter_b
     table = b.Table((w.blob, w.offsets), **kw)
     if args.large_config:
         b.pfac_set_config(table.h, json.loads(args.large_config))
@@ -713,6 +715,7 @@ def main():
                     help="--suite large: the table's filter structure")
     ap.add_argument("--large-config", default="", help="--suite large: a launch configuration (JSON of pfac_config "
                                                         "fields) applied to the table")
+    ap.add_argument("--large-filter-b", type=int, default=0, help="--suite large: the table's filter order (0 = automatic)")
     ap.add_argument("--suite", default=None, choices=["paper", "batched", "ceilings", "configs", "large"],
                     help="paper: the paper's placement, pattern-set and input-size experiments (many lines); "
                          "batched: the batched workload alone; ceilings: store and lookup rates of the GPU; "

@@ -246,7 +246,8 @@ typedef struct {
                                 in L2 (tables with a sampled screen; both sit side by side
                                 in the table's memory) (either sets the context's
                                 persisting-L2 limit, which the next launch without a window
-                                gives back), -1 or 0 = no window */
+                                gives back; on the workloads measured both windows made the
+                                scan slower), -1 or 0 = no window */
     int32_t walk_loads;      /* kernel 2: dependent table loads a walk may take before it
                                 is handed to the tail kernel (0 = 2) */
     int32_t lane_offsets;    /* kernel 2: consecutive offsets per consumer lane, 16 or 32
