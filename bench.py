@@ -848,6 +848,30 @@ def main():
     h_text = torch.from_numpy(w.text).pin_memory()
     h_out = torch.empty(n, dtype=torch.int32).pin_memory()
     hs = HostScanner(table, chunk_bases=args.e2e_chunk)
+    n_chunks = (n + hs.chunk - 1) // hs.chunk
+    h2d_bytes = n + (n_chunks - 1) * (info["max_len"] - 1)
+    # (a) the match list: every offset with a pattern and its id; only the matches cross
+    # the host link
+    nz = torch.nonzero(out).flatten()
+    want_off, want_ids = nz.cpu().numpy(), out[nz].cpu().numpy()
+    h_moff = torch.empty(want_off.size + 1024, dtype=torch.int64).pin_memory()
+    h_mids = torch.empty(want_off.size + 1024, dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        n_match = hs.scan_matches(h_text, h_moff, h_mids)
+    list_same = bool(n_match == want_off.size and np.array_equal(h_moff.numpy()[:n_match], want_off)
+                     and np.array_equal(h_mids.numpy()[:n_match], want_ids))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        hs.scan_matches(h_text, h_moff, h_mids)
+    list_s = time.perf_counter() - t0
+    e2e = {"value": world * n * args.e2e_steps / list_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": 12 * n_match + 8 * n_chunks,
+           "steps": args.e2e_steps, "matches": n_match, "same_as_device": list_same,
+           "path": f"pinned host ASCII -> hoststream.HostScanner.scan_matches ({hs.chunk}-base chunks: H2D, "
+                   "pfac_pack, pfac_match_compact, D2H count then pairs, on three overlapped streams) -> pinned "
+                   "host (offset, id) list of every offset with a pattern, ascending"}
+    # (b) one id per base: 4 bytes per base cross the host link
     for _ in range(2):
         hs.scan(h_text, h_out)
         assert hs.synchronize() == 0
@@ -858,12 +882,11 @@ def main():
         hs.scan(h_text, h_out)
         hs.synchronize()
     e2e_s = time.perf_counter() - t0
-    n_chunks = (n + hs.chunk - 1) // hs.chunk
-    e2e = {"value": world * n * args.e2e_steps / e2e_s / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": n + (n_chunks - 1) * (info["max_len"] - 1), "d2h_bytes_per_step": 4 * n,
-           "steps": args.e2e_steps, "same_as_device": e2e_same,
-           "path": f"pinned host ASCII -> hoststream.HostScanner ({hs.chunk}-base chunks: H2D, pfac_pack, "
-                   "pfac_match_packed, D2H ids on three overlapped streams) -> pinned host ids"}
+    e2e_dense = {"value": world * n * args.e2e_steps / e2e_s / 1e9, "unit": UNIT,
+                 "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": 4 * n,
+                 "steps": args.e2e_steps, "same_as_device": e2e_same,
+                 "path": f"pinned host ASCII -> hoststream.HostScanner ({hs.chunk}-base chunks: H2D, pfac_pack, "
+                         "pfac_match_packed, D2H ids on three overlapped streams) -> pinned host ids"}
 
     line = None
     if rank == 0:
@@ -881,7 +904,8 @@ def main():
                        "input_resident": "packed text in HBM",
                        "inputs": {"seed": 2 + rank, "text_sha256": datagen.sha256(w.text),
                                   "patterns_sha256": datagen.sha256(w.blob)}},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "e2e_dense_ids": e2e_dense,
+            "gpu_launches": 2 * args.steps,
             "device_status": device_status,
             "clocks": None,
             "wall_s_timed_region": wall,

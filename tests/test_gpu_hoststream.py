@@ -30,6 +30,27 @@ def test_chunks_equal_the_oracle(genome, chunk):
     assert np.array_equal(got, want), first_diff(got, want)
 
 
+@pytest.mark.parametrize("chunk", [1 << 16, (1 << 18) + 48, 1 << 22])
+def test_match_list_equals_the_oracle(genome, chunk):
+    """The match list of a host text (only the matches cross the host link): every offset
+    with a pattern, ascending, with its id; a chunk's halo adds nothing twice."""
+    torch, w, t, want = genome
+    sc = HostScanner(t, chunk_bases=chunk)
+    h_text = torch.from_numpy(w.text).pin_memory()
+    offs_w, ids_w = oracle.compact(want)
+    h_off = torch.full((offs_w.size + 10,), -1, dtype=torch.int64).pin_memory()
+    h_ids = torch.zeros(offs_w.size + 10, dtype=torch.int32).pin_memory()
+    c = sc.scan_matches(h_text, h_off, h_ids)
+    assert c == offs_w.size
+    assert np.array_equal(h_off.numpy()[:c], offs_w) and np.array_equal(h_ids.numpy()[:c], ids_w)
+    # too small an output: an overflow error, not a truncated list
+    small_off = torch.zeros(max(1, c // 2), dtype=torch.int64).pin_memory()
+    small_ids = torch.zeros(max(1, c // 2), dtype=torch.int32).pin_memory()
+    with pytest.raises(b.PfacError) as e:
+        sc.scan_matches(h_text, small_off, small_ids)
+    assert e.value.code == b.CODE["PFAC_ERR_OVERFLOW"]
+
+
 def test_scanner_reuse_and_short_texts(genome):
     torch, w, t, want = genome
     sc = HostScanner(t, chunk_bases=1 << 18)
