@@ -704,7 +704,7 @@ def main():
     ap.add_argument("--n-bases", type=int, default=N_BASES)
     ap.add_argument("--n-patterns", type=int, default=N_PATTERNS)
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--e2e-chunk", type=int, default=1 << 24)
+    ap.add_argument("--e2e-chunk", type=int, default=1 << 25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
