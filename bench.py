@@ -281,7 +281,7 @@ def batched_measure(steps: int, tune: bool = True):
             "same_output": same,
             "autotune": {k: tuned.get(k) for k in ("lane_offsets", "threads", "ctas_per_sm", "walk_loads",
                                                    "ms", "default_ms", "candidates")},
-            "launches_per_batch": 4, "launches_per_read_pass": pg.launches,
+            "launches_per_batch": 1 if len(w.read_set) <= 8192 else 4, "launches_per_read_pass": pg.launches,
             "per_read_baseline": "one pfac_match (scan + tail kernel) per read, all captured in one CUDA graph "
                                  "and replayed; L2 flushed before each replay"}
 

@@ -366,12 +366,17 @@ int pfac_match_all(pfac_handle h, const uint32_t *d_packed, int64_t n_bases,
  * Walks never cross a read's end; bytes outside ACGT end walks as in pfac_match. A
  * read_set entry outside [0, n_sets) records PFAC_ERR_INVALID_ARG in the device status
  * of sets[0] and leaves that read's output unwritten.
- * The call packs the text, plans the work and runs one persistent scan launch (plus a
- * tail launch for the few long walks), all on `stream`, with scratch that the library
- * keeps per stream. Its launch shape comes from the configuration of sets[0]
+ * Up to 8,192 reads (6,144 with lane_offsets = 32) the call is ONE kernel launch on
+ * `stream`: every CTA plans the batch in shared memory (reads grouped by table), scans
+ * the work items dealt to it straight from the ASCII bytes, and finishes the few long
+ * walks its items deferred. Larger batches take four launches (pack the text, plan the
+ * work items, one persistent scan, a tail for the long walks). Scratch (the list of
+ * deferred walks; for large batches also the packed text and the plan) is kept by the
+ * library per stream. The launch shape comes from the configuration of sets[0]
  * (pfac_set_config): a work item is 32 x lane_offsets offsets of one read, the scan
- * kernel runs threads x ctas_per_sm threads per SM in 256-thread blocks (1 to 8 blocks),
- * and walk_loads bounds the in-kernel walks as in kernel 2. The first call with a given list of handles uploads a small
+ * runs threads x ctas_per_sm threads per SM (one CTA per SM of up to 1,024 threads in
+ * the one-launch pass; 256-thread blocks, 1 to 8 per SM, otherwise), and walk_loads
+ * bounds the in-kernel walks as in kernel 2. The first call with a given list of handles uploads a small
  * descriptor array, and the first call on a stream (or with a larger text) allocates
  * scratch; both are synchronous, so issue such a call before capturing the stream
  * into a CUDA graph; later calls with the same handle list and sizes are capturable. */

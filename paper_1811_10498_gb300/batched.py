@@ -2,9 +2,10 @@
 
 ``BatchedScanner`` keeps fixed-capacity device buffers for a batch (read bytes, read
 offsets, read-to-table map, output) and runs ``pfac_match_batched`` on them, either
-directly or by replaying a CUDA graph captured once: every replay is one pack, one
-plan, one persistent scan and one tail launch with the inputs the caller copied into
-the buffers. ``tune`` picks the launch shape with the autotuner before capturing. ``scan_per_read`` is the baseline it is measured against: one
+directly or by replaying a CUDA graph captured once: every replay is one launch (each
+CTA plans the batch, scans the work items dealt to it and finishes its long walks) with
+the inputs the caller copied into the buffers; batches of more than 8,192 reads take a
+pack, a plan, a scan and a tail launch. ``tune`` picks the launch shape with the autotuner before capturing. ``scan_per_read`` is the baseline it is measured against: one
 ``pfac_match`` launch per read.
 """
 from __future__ import annotations

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "../../include/pfac.h"
 #include "pfac_internal.h"
@@ -253,6 +254,394 @@ __global__ void __launch_bounds__(256) batched_tail_kernel(const BatchParams P)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused batched pass (batches of up to fused_max_reads reads): ONE launch, one CTA per
+// SM, no packed copy of the text, no planning or tail launch.
+//   1. Every CTA plans the whole batch in shared memory, and every CTA gets the same
+//      plan: the reads are ordered by table bucket (table index mod kFusedBuckets) by a
+//      counting sort whose ranks come from per-(bucket, warp) counts, so the order does
+//      not depend on timing; the work items are numbered in that order. A work item is
+//      one aligned 32*LW-base chunk of the concatenated text intersected with one read.
+//   2. The items are dealt to the CTAs in runs of kDealRun (run k to CTA k mod G), and
+//      a CTA's warps claim its items in order from a counter in shared memory, each claim
+//      issued one item ahead. Every CTA thus gets a sample of every table's items (the
+//      CTAs' loads even out), and at any moment all CTAs work near the same place of the
+//      order, on the same few tables, whose filter words stay in L1. A warp copies the
+//      next item's bytes (and the 64 after them) into shared memory with cp.async while
+//      it scans the current one; each lane packs its own 16 bytes and takes the rest of
+//      its 64-base window by shuffles, as kernel 2 does for ASCII text.
+//   3. After a block barrier the CTA finishes the long walks its items deferred, kept in
+//      its own slice of the deferred-walk list.
+// ---------------------------------------------------------------------------
+
+constexpr int kFusedBuckets = 128;
+constexpr int kDealRun = 8;
+
+struct FusedParams {
+    const DeviceTable *sets;
+    int32_t n_sets;
+    const uint8_t *text;
+    int64_t n;
+    const int64_t *read_off;
+    const int32_t *read_set;
+    int32_t n_reads;
+    int32_t *out;
+    DeferItem *defer;                // defer_per_cta items for each CTA
+    int64_t defer_per_cta;
+    int32_t walk_loads;
+};
+
+// Reads one fused launch plans in shared memory, for LW offsets per lane.
+static int32_t fused_max_reads(int lw) { return lw == 32 ? 6144 : 8192; }
+
+// Bytes of one warp's text buffer: a work item and the 64 bases after it.
+template <int LW>
+__host__ __device__ constexpr int fused_buf_bytes() { return 32 * LW + 64; }
+
+// Shared memory of the fused kernel for `warps` warps per CTA, n_reads reads and LW
+// offsets per lane: the plan's per-(bucket, warp) read counts and item sums, the scan's
+// warp totals, the deferred-walk count, two text buffers per warp, and per read its
+// sorted place, first item, item count, first chunk and bucket.
+static size_t fused_smem_bytes(int warps, int32_t n_reads, int lw)
+{
+    const size_t r16 = ((size_t)n_reads + 4) / 4 * 4;   // n_reads + 1 entries, rounded to 16 bytes
+    return (size_t)(warps + 1) * kFusedBuckets * 4 * 2 + 32 * 8 + 16 + (size_t)warps * 2 * (32 * lw + 64) +
+           r16 * 4 * 4 + r16;
+}
+
+// Sixteen ASCII bytes from position p of the text (bases at or past n are bad).
+__device__ __forceinline__ uint32_t ascii16(const uint8_t *__restrict__ text, int64_t n, int64_t p, bool aligned,
+                                            uint32_t *bad16)
+{
+    if (aligned && p + 16 <= n) return pack16(__ldg(reinterpret_cast<const uint4 *>(text + p)), bad16);
+    uint32_t w = 0, b = 0;
+    for (int i = 0; i < 16; i++) {
+        const int c = p + i < n ? base_code_or_neg(__ldg(text + p + i)) : -1;
+        if (c < 0) b |= 1u << i;
+        else w |= (uint32_t)c << (2 * i);
+    }
+    *bad16 = b;
+    return w;
+}
+
+// Asynchronous 16-byte copy global -> shared that bypasses L1; the bytes past `valid`
+// (0 .. 16) are zero-filled (a zero byte is not a base).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ uint32_t fused_bucket(int32_t set) { return (uint32_t)set % (uint32_t)kFusedBuckets; }
+
+// Work items of the read [rs, re): the aligned item-size chunks it touches.
+__device__ __forceinline__ int32_t fused_items(int64_t rs, int64_t re, int shift)
+{
+    return re > rs ? (int32_t)(((re - 1) >> shift) - (rs >> shift) + 1) : 0;
+}
+
+// A claimed work item: its first offset (chunk-aligned), and its read's raw bounds and
+// table as loaded (clamped only when the item is scanned, so that nothing waits on
+// these loads while the previous item is still being scanned).
+struct FusedItem {
+    int64_t base, lo, hi;
+    int32_t set;
+};
+
+template <int LW>
+__global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParams P)
+{
+    constexpr int kItem = 32 * LW;
+    constexpr int kShift = LW == 32 ? 10 : 9;
+    constexpr int kBuf = fused_buf_bytes<LW>();
+    constexpr uint32_t kFull = 0xFFFFFFFFu;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int W = blockDim.x >> 5;
+    const int R = P.n_reads;
+    const int R16 = (R + 4) / 4 * 4;
+    // per-(bucket, warp) counts at bucket * (W + 1) + warp: the lanes of a warp, each
+    // adding to its own bucket, meet different banks
+    const int WP = W + 1;
+    uint32_t *cnt_reads = reinterpret_cast<uint32_t *>(smem);                         // [bucket][W + 1]
+    uint32_t *cnt_items = cnt_reads + WP * kFusedBuckets;                             // [bucket][W + 1]
+    unsigned long long *wsum = reinterpret_cast<unsigned long long *>(cnt_items + WP * kFusedBuckets);   // [32]
+    unsigned long long *dcount = wsum + 32;                                           // deferred walks
+    unsigned int *claimed = reinterpret_cast<unsigned int *>(dcount + 1);             // items claimed
+    uint8_t *tbuf = reinterpret_cast<uint8_t *>(dcount + 2);                          // [warp][2][kBuf]
+    int32_t *sorted_read = reinterpret_cast<int32_t *>(tbuf + (size_t)W * 2 * kBuf); // [R]
+    int32_t *item_start = sorted_read + R16;                                          // [R + 1]
+    int32_t *read_items = item_start + R16;                                           // [R]
+    int32_t *read_chunk = read_items + R16;                                           // [R]
+    uint8_t *read_bucket = reinterpret_cast<uint8_t *>(read_chunk + R16);             // [R]
+
+    // ---- 1. the plan ----
+    for (int i = tid; i < 2 * WP * kFusedBuckets; i += blockDim.x) cnt_reads[i] = 0;
+    if (tid == 0) {
+        *dcount = 0;
+        *claimed = 0;
+    }
+    __syncthreads();
+    const int seg = ((R + W - 1) / W + 31) & ~31;   // reads per warp, whole rounds of 32
+    const int r0 = min(R, warp * seg), r1 = min(R, r0 + seg);
+    // the reads' bounds and tables, kPlanRounds rounds of 32 reads in flight at once
+    for (int cb = r0; cb < r1; cb += 32 * kPlanRounds) {
+        int64_t lo_[kPlanRounds], hi_[kPlanRounds];
+        int32_t set_[kPlanRounds];
+#pragma unroll
+        for (int q = 0; q < kPlanRounds; q++) {
+            const int r = cb + 32 * q + lane;
+            lo_[q] = hi_[q] = 0;
+            set_[q] = 0;
+            if (r < r1) {
+                lo_[q] = P.read_off[r];
+                hi_[q] = P.read_off[r + 1];
+                set_[q] = P.read_set[r];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kPlanRounds; q++) {
+            const int r = cb + 32 * q + lane;
+            if (r < r1) {
+                const int64_t rs = min(max(lo_[q], (int64_t)0), P.n), re = min(max(hi_[q], rs), P.n);
+                const int32_t items = fused_items(rs, re, kShift);
+                const uint32_t bk = fused_bucket(set_[q]);
+                read_items[r] = items;
+                read_chunk[r] = (int32_t)(rs >> kShift);
+                read_bucket[r] = (uint8_t)bk;
+                atomicAdd(&cnt_reads[bk * WP + warp], 1u);
+                atomicAdd(&cnt_items[bk * WP + warp], (uint32_t)items);
+            }
+        }
+    }
+    __syncthreads();
+    // exclusive scan of the (reads << 32 | items) counts in (bucket, warp) order; the
+    // item total stays below 2^31, so the low half never carries into the high one
+    {
+        constexpr int kPer = kFusedBuckets / 32;   // W * kFusedBuckets entries over 32 * W threads
+        const int lg_w = __ffs(W) - 1;              // W is 8, 16 or 32
+        unsigned long long v[kPer], sum = 0;
+        int at[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; q++) {
+            const int i = kPer * tid + q;                 // place in (bucket, warp) order
+            at[q] = (i >> lg_w) * WP + (i & (W - 1));
+            v[q] = ((unsigned long long)cnt_reads[at[q]] << 32) | cnt_items[at[q]];
+            sum += v[q];
+        }
+        unsigned long long incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long o = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += o;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long x = lane < W ? wsum[lane] : 0ull;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long o = __shfl_up_sync(kFull, x, d);
+                if (lane >= d) x += o;
+            }
+            wsum[lane] = x;   // inclusive over warps
+        }
+        __syncthreads();
+        unsigned long long run = (warp ? wsum[warp - 1] : 0ull) + incl - sum;
+#pragma unroll
+        for (int q = 0; q < kPer; q++) {
+            cnt_reads[at[q]] = (uint32_t)(run >> 32);
+            cnt_items[at[q]] = (uint32_t)run;
+            run += v[q];
+        }
+        if (tid == 0) item_start[R] = (int32_t)(uint32_t)wsum[W - 1];
+    }
+    __syncthreads();
+    // each read's place: its (bucket, warp) base, moved on past the reads of the same
+    // bucket in this warp's earlier rounds, plus those in lower lanes of this round
+    for (int cb = r0; cb < r1; cb += 32) {
+        const int r = cb + lane;
+        const bool act = r < r1;
+        const int32_t items = act ? read_items[r] : 0;
+        const uint32_t bk = act ? (uint32_t)read_bucket[r] : 0xFFFFFFFFu;
+        // the lanes with this lane's bucket: eight ballots, one per bit of the bucket
+        uint32_t grp = kFull;
+#pragma unroll
+        for (int bit = 0; bit < 8; bit++) {
+            const uint32_t set_b = __ballot_sync(kFull, (bk >> bit) & 1u);
+            grp &= ((bk >> bit) & 1u) ? set_b : ~set_b;
+        }
+        uint32_t base_r = 0, base_i = 0;
+        if (act) {
+            base_r = cnt_reads[bk * WP + warp];
+            base_i = cnt_items[bk * WP + warp];
+        }
+        __syncwarp();
+        if (act) {
+            const uint32_t lower = grp & ((1u << lane) - 1u);
+            uint32_t pre = 0;
+            for (uint32_t m = lower; m; m &= m - 1u) pre += (uint32_t)read_items[cb + __ffs(m) - 1];
+            const uint32_t pos = base_r + (uint32_t)__popc(lower);
+            sorted_read[pos] = r;
+            item_start[pos] = (int32_t)(base_i + pre);
+            if ((grp >> lane) == 1u) {   // the group's last lane moves the running base on
+                cnt_reads[bk * WP + warp] = base_r + (uint32_t)__popc(grp);
+                cnt_items[bk * WP + warp] = base_i + pre + (uint32_t)items;
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // ---- 2. work items, claimed in plan order ----
+    const int64_t I = item_start[R];
+    const bool aligned = ((uintptr_t)P.text & 15u) == 0;
+    const bool out_aligned = ((uintptr_t)P.out & 15u) == 0;
+    const uint64_t pol = policy_evict_first();
+    Sink K{};
+    K.out = P.out;
+    K.defer = P.defer + (int64_t)blockIdx.x * P.defer_per_cta;
+    K.defer_cap = P.defer_per_cta;
+    K.defer_count = dcount;
+    uint8_t *mybuf = tbuf + (size_t)warp * 2 * kBuf;
+    // work item `it`: the last sorted place whose first item is <= it (a read with no
+    // items shares its first item with the next place), its chunk from shared memory,
+    // and its read's bounds and table loaded for later
+    auto locate = [&](int64_t it) {
+        int a = 0, b = R - 1;
+        while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            if ((int64_t)item_start[mid] <= it) a = mid;
+            else b = mid - 1;
+        }
+        const int32_t r = sorted_read[a];
+        FusedItem f;
+        f.base = ((int64_t)read_chunk[r] + (it - item_start[a])) << kShift;
+        f.lo = P.read_off[r];
+        f.hi = P.read_off[r + 1];
+        f.set = P.read_set[r];
+        return f;
+    };
+    // start copying the bytes of the item at `cbase`, and the 64 after it, into buffer b
+    auto fetch = [&](int64_t cbase, int b) {
+        const uint32_t dst = smem_addr(mybuf + b * kBuf);
+        for (int c = lane; c < kBuf / 16; c += 32) {
+            const int64_t p = cbase + 16 * c;
+            const int64_t left = P.n - p;
+            const uint32_t nb = left >= 16 ? 16u : (left > 0 ? (uint32_t)left : 0u);
+            cp_async16(dst + 16 * c, P.text + (nb ? p : 0), nb);
+        }
+        cp_async_commit();
+    };
+    // the CTA's t-th item: run t / kDealRun of this CTA's runs, item t mod kDealRun of it
+    // (increasing in t, so the first one past the end ends the claims)
+    auto item_of = [&](uint32_t t) -> int64_t {
+        return ((int64_t)(t / kDealRun) * gridDim.x + blockIdx.x) * kDealRun + (t % kDealRun);
+    };
+    // claims: lane 0 holds the answer of the claim after the next
+    uint32_t pending = 0;
+    if (lane == 0) pending = atomicAdd(claimed, 1u);
+    int64_t it = item_of(__shfl_sync(kFull, pending, 0));
+    if (lane == 0) pending = atomicAdd(claimed, 1u);
+    FusedItem cur{};
+    if (it < I) {
+        cur = locate(it);
+        if (aligned) fetch(cur.base, 0);
+    }
+    for (int k = 0; it < I; k ^= 1) {
+        const int64_t nxt = item_of(__shfl_sync(kFull, pending, 0));
+        const bool more = nxt < I;
+        FusedItem nx{};
+        if (more) {
+            if (lane == 0) pending = atomicAdd(claimed, 1u);
+            nx = locate(nxt);
+            if (aligned) fetch(nx.base, k ^ 1);
+        }
+        if (aligned) {
+            if (more) cp_async_wait<1>();
+            else cp_async_wait<0>();
+            __syncwarp();
+        }
+        if (cur.set < 0 || cur.set >= P.n_sets) {
+            if (lane == 0) record_error(P.sets[0].status, PFAC_ERR_INVALID_ARG);
+        } else {
+            const DeviceTable T = P.sets[cur.set];
+            const int64_t cbase = cur.base;
+            const int64_t rs = min(max(cur.lo, (int64_t)0), P.n), re = min(max(cur.hi, rs), P.n);
+            const int64_t p0 = cbase + (int64_t)LW * lane;
+            const uint8_t *buf = mybuf + k * kBuf;
+            // 16 bytes from byte `o` of the item: from the warp's buffer, or from the text
+            auto word = [&](int o, uint32_t *bad16) -> uint32_t {
+                if (aligned) return pack16(lds_v4(buf + o), bad16);
+                return ascii16(P.text, P.n, cbase + o, false, bad16);
+            };
+            uint32_t x0, x1, x2, x3, b0, b1, b2, b3;
+            if constexpr (LW == 16) {
+                uint32_t h = 0, hb = 0xFFFFu;
+                x0 = word(16 * lane, &b0);
+                if (lane < 3) h = word(kItem + 16 * lane, &hb);
+                const uint32_t d1 = __shfl_down_sync(kFull, x0, 1), e1 = __shfl_down_sync(kFull, b0, 1);
+                const uint32_t d2 = __shfl_down_sync(kFull, x0, 2), e2 = __shfl_down_sync(kFull, b0, 2);
+                const uint32_t d3 = __shfl_down_sync(kFull, x0, 3), e3 = __shfl_down_sync(kFull, b0, 3);
+                const uint32_t g1 = __shfl_sync(kFull, h, (lane + 1) & 31), f1 = __shfl_sync(kFull, hb, (lane + 1) & 31);
+                const uint32_t g2 = __shfl_sync(kFull, h, (lane + 2) & 31), f2 = __shfl_sync(kFull, hb, (lane + 2) & 31);
+                const uint32_t g3 = __shfl_sync(kFull, h, (lane + 3) & 31), f3 = __shfl_sync(kFull, hb, (lane + 3) & 31);
+                x1 = lane < 31 ? d1 : g1;
+                b1 = lane < 31 ? e1 : f1;
+                x2 = lane < 30 ? d2 : g2;
+                b2 = lane < 30 ? e2 : f2;
+                x3 = lane < 29 ? d3 : g3;
+                b3 = lane < 29 ? e3 : f3;
+            } else {
+                uint32_t h0 = 0, h1 = 0, hb0 = 0xFFFFu, hb1 = 0xFFFFu;
+                x0 = word(32 * lane, &b0);
+                x1 = word(32 * lane + 16, &b1);
+                if (lane == 0) {
+                    h0 = word(kItem, &hb0);
+                    h1 = word(kItem + 16, &hb1);
+                }
+                const uint32_t d2 = __shfl_down_sync(kFull, x0, 1), e2 = __shfl_down_sync(kFull, b0, 1);
+                const uint32_t d3 = __shfl_down_sync(kFull, x1, 1), e3 = __shfl_down_sync(kFull, b1, 1);
+                const uint32_t g2 = __shfl_sync(kFull, h0, 0), f2 = __shfl_sync(kFull, hb0, 0);
+                const uint32_t g3 = __shfl_sync(kFull, h1, 0), f3 = __shfl_sync(kFull, hb1, 0);
+                x2 = lane < 31 ? d2 : g2;
+                b2 = lane < 31 ? e2 : f2;
+                x3 = lane < 31 ? d3 : g3;
+                b3 = lane < 31 ? e3 : f3;
+            }
+            uint64_t bad = (uint64_t)b0 | ((uint64_t)b1 << 16) | ((uint64_t)b2 << 32) | ((uint64_t)b3 << 48);
+            const int64_t rem_read = re - p0;   // walks stop at the read's end
+            if (rem_read < 64) bad |= rem_read > 0 ? (~0ull << rem_read) : ~0ull;
+            // this lane's offsets inside the read
+            const int64_t va = max(rs, p0) - p0, vb = min(re, p0 + LW) - p0;
+            uint32_t valid = 0;
+            if (vb > va) {
+                const uint32_t span = (uint32_t)(vb - va);
+                valid = (span >= 32 ? 0xFFFFFFFFu : ((1u << span) - 1u)) << (uint32_t)va;
+            }
+            scan_lane_batch<false, false, false, true, LW>(T, K, nullptr, nullptr, P.walk_loads, (uint32_t)cur.set,
+                                                           P.text, nullptr, re, cbase, lane, x0, x1, x2, x3, bad,
+                                                           valid, out_aligned, pol);
+        }
+        // the buffer just read is the one the next fetch fills
+        __syncwarp();
+        it = nxt;
+        cur = nx;
+    }
+
+    // ---- 3. the long walks this CTA's items deferred ----
+    __syncthreads();
+    const int64_t nd = min((int64_t)*dcount, P.defer_per_cta);
+    for (int64_t i = tid; i < nd; i += blockDim.x) {
+        const DeferItem d = K.defer[i];
+        const DeviceTable T = P.sets[d.q_set >> 16];
+        emit_match<false>(K, d.gp, walk_global<false>(T, P.text, nullptr, d.gp + d.span, d.gp, d.s,
+                                                       (int)(d.q_set & 0xFFFFu), d.best));
+    }
+}
+
 // Work items of reads that do not overlap: at most one partial item per read plus one
 // per 512 bases.
 static int64_t item_capacity(int64_t n, int32_t n_reads) { return n / 512 + (int64_t)n_reads + 1; }
@@ -286,6 +675,45 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
     int32_t *item_read = (int32_t *)p;
     p += (item_cap * 4 + 255) & ~255LL;
     DeferItem *defer = (DeferItem *)p;
+    const int64_t fused_items_max = n / (32 * lw) + (int64_t)n_reads + 1;
+    const int fused_threads = 256 * std::min(4, blocks_per_sm);
+    if (n_reads <= fused_max_reads(lw) && fused_items_max < (1LL << 30) &&
+        fused_smem_bytes(fused_threads / 32, n_reads, lw) <= (size_t)dp.smem_optin) {
+        // one launch: every CTA plans the batch, scans the items dealt to it and finishes
+        // the walks its items deferred
+        const size_t smem = fused_smem_bytes(fused_threads / 32, n_reads, lw);
+        {
+            // the most any batch can need, set once per kernel and device (so that a call
+            // being captured into a graph never sets it)
+            static std::mutex mu;
+            static bool done[2][64];
+            std::lock_guard<std::mutex> lk(mu);
+            bool &d = done[lw == 32][dp.device & 63];
+            if (!d) {
+                const void *kern =
+                    lw == 32 ? (const void *)fused_batched_kernel<32> : (const void *)fused_batched_kernel<16>;
+                const size_t most = std::min<size_t>(fused_smem_bytes(32, fused_max_reads(lw), lw), dp.smem_optin);
+                if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) != cudaSuccess)
+                    return PFAC_ERR_CUDA;
+                d = true;
+            }
+        }
+        FusedParams F{};
+        F.sets = d_sets;
+        F.n_sets = n_sets;
+        F.text = texts;
+        F.n = n;
+        F.read_off = read_off;
+        F.read_set = read_set;
+        F.n_reads = n_reads;
+        F.out = out;
+        F.defer = defer;
+        F.defer_per_cta = std::max<int64_t>(1, defer_cap / dp.num_sms);
+        F.walk_loads = bc.walk_loads > 0 ? bc.walk_loads : 2;
+        if (lw == 32) fused_batched_kernel<32><<<dp.num_sms, fused_threads, smem, st>>>(F);
+        else fused_batched_kernel<16><<<dp.num_sms, fused_threads, smem, st>>>(F);
+        return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
+    }
     if (cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return PFAC_ERR_CUDA;
     const int pack_blocks = (int)std::min<int64_t>((bw + 255) / 256, (int64_t)dp.num_sms * 16);
     pack_bits_kernel<<<std::max(1, pack_blocks), 256, 0, st>>>(texts, n, packed, invalid);

@@ -177,3 +177,52 @@ def test_many_tables_and_filters_of_every_size():
     assert (want != 0).sum() > 1000
     for t in tables:
         t.close()
+
+
+@pytest.mark.parametrize("cfg", [{"lane_offsets": 32}, {"threads": 256}, {"threads": 512, "walk_loads": 1}])
+def test_launch_shapes(batch, cfg):
+    """The one-launch pass with 1,024-base work items, and with 8 or 16 warps per CTA
+    (each CTA plans the whole batch itself)."""
+    w, want, tables = batch
+    b.pfac_set_config(tables[0].h, cfg)
+    try:
+        got = run_batched(tables, w.reads, w.read_offsets, w.read_set)
+    finally:
+        b.pfac_set_config(tables[0].h, None)
+    assert np.array_equal(got, want), first_diff(got, want)
+
+
+def test_unaligned_text_and_output_pointers(batch):
+    """Reads whose bytes start one byte past a 16-byte boundary and ids 4 bytes past
+    one: the 16-byte copies and stores give way to narrower ones, with the same ids."""
+    import torch
+    w, want, tables = batch
+    d = torch.zeros(w.reads.size + 1, dtype=torch.uint8, device="cuda")
+    d[1:] = to_dev(w.reads)
+    out = torch.full((w.reads.size + 1,), -9, dtype=torch.int32, device="cuda")
+    b.pfac_match_batched([t.h for t in tables], d[1:], to_dev(w.read_offsets), to_dev(w.read_set), out[1:])
+    torch.cuda.synchronize()
+    got = out[1:].cpu().numpy()
+    assert np.array_equal(got, want), first_diff(got, want)
+
+
+def test_more_reads_than_one_launch_plans():
+    """9,000 reads (more than one CTA plans in shared memory): the pass falls back to its
+    pack, plan, scan and tail launches, with the oracle's ids."""
+    rng = datagen.rng_for(77)
+    src = datagen.iid_text(1 << 18, rng)
+    pats = [src[s0:s0 + 20].tobytes() for s0 in rng.integers(0, src.size - 20, 200)]
+    sets = [pats[:120], pats[80:], [b"ACGTACGTAC"]]
+    tables = [b.Table(s) for s in sets]
+    lens = rng.integers(0, 120, 9000)
+    offs = np.zeros(lens.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=offs[1:])
+    starts = rng.integers(0, src.size - 120, lens.size)
+    reads = np.concatenate([src[s0:s0 + L] for s0, L in zip(starts, lens)]).astype(np.uint8)
+    read_set = rng.integers(0, len(sets), lens.size).astype(np.int32)
+    want = oracle.pfac_scan_reads(reads, offs, read_set, sets)
+    got = run_batched(tables, reads, offs, read_set)
+    assert np.array_equal(got, want), first_diff(got, want)
+    assert (want != 0).sum() > 100
+    for t in tables:
+        t.close()
