@@ -264,9 +264,9 @@ __global__ void __launch_bounds__(256) batched_tail_kernel(const BatchParams P)
 //      one aligned 32*LW-base chunk of the concatenated text intersected with one read.
 //   2. The items are dealt to the CTAs in runs of kDealRun (run k to CTA k mod G), and
 //      a CTA's warps claim its items in order from a counter in shared memory, each claim
-//      issued one item ahead. Every CTA thus gets a sample of every table's items (the
-//      CTAs' loads even out), and at any moment all CTAs work near the same place of the
-//      order, on the same few tables, whose filter words stay in L1. A warp copies the
+//      issued one item ahead. An SM's warps thus work on one or two runs at a time, mostly
+//      of one table, whose filter words stay in its L1, and every CTA gets a sample of
+//      every table's items, so that the CTAs' loads even out. A warp copies the
 //      next item's bytes (and the 64 after them) into shared memory with cp.async while
 //      it scans the current one; each lane packs its own 16 bytes and takes the rest of
 //      its 64-base window by shuffles, as kernel 2 does for ASCII text.
@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(256) batched_tail_kernel(const BatchParams P)
 // ---------------------------------------------------------------------------
 
 constexpr int kFusedBuckets = 128;
-constexpr int kDealRun = 8;
+constexpr int kDealRun = 16;
+constexpr int kGuide = 1024;   // guide entries: the sorted place of every (I / kGuide)-th item
 
 struct FusedParams {
     const DeviceTable *sets;
@@ -300,13 +301,14 @@ __host__ __device__ constexpr int fused_buf_bytes() { return 32 * LW + 64; }
 
 // Shared memory of the fused kernel for `warps` warps per CTA, n_reads reads and LW
 // offsets per lane: the plan's per-(bucket, warp) read counts and item sums, the scan's
-// warp totals, the deferred-walk count, two text buffers per warp, and per read its
-// sorted place, first item, item count, first chunk and bucket.
+// warp totals, the deferred-walk and claim counts, the guide to the sorted places, two
+// text buffers per warp, and per read its sorted place, first item, item count, first
+// chunk and bucket.
 static size_t fused_smem_bytes(int warps, int32_t n_reads, int lw)
 {
     const size_t r16 = ((size_t)n_reads + 4) / 4 * 4;   // n_reads + 1 entries, rounded to 16 bytes
-    return (size_t)(warps + 1) * kFusedBuckets * 4 * 2 + 32 * 8 + 16 + (size_t)warps * 2 * (32 * lw + 64) +
-           r16 * 4 * 4 + r16;
+    return (size_t)(warps + 1) * kFusedBuckets * 4 * 2 + 32 * 8 + 16 + (kGuide + 4) * 4 +
+           (size_t)warps * 2 * (32 * lw + 64) + r16 * 4 * 4 + r16;
 }
 
 // Sixteen ASCII bytes from position p of the text (bases at or past n are bad).
@@ -370,7 +372,8 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
     unsigned long long *wsum = reinterpret_cast<unsigned long long *>(cnt_items + WP * kFusedBuckets);   // [32]
     unsigned long long *dcount = wsum + 32;                                           // deferred walks
     unsigned int *claimed = reinterpret_cast<unsigned int *>(dcount + 1);             // items claimed
-    uint8_t *tbuf = reinterpret_cast<uint8_t *>(dcount + 2);                          // [warp][2][kBuf]
+    int32_t *guide = reinterpret_cast<int32_t *>(dcount + 2);                         // [kGuide + 4]
+    uint8_t *tbuf = reinterpret_cast<uint8_t *>(guide + kGuide + 4);                  // [warp][2][kBuf]
     int32_t *sorted_read = reinterpret_cast<int32_t *>(tbuf + (size_t)W * 2 * kBuf); // [R]
     int32_t *item_start = sorted_read + R16;                                          // [R + 1]
     int32_t *read_items = item_start + R16;                                           // [R]
@@ -495,8 +498,18 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
     }
     __syncthreads();
 
-    // ---- 2. work items, claimed in plan order ----
+    // the guide: the sorted place holding item g * gstep, for every g (each item lies in
+    // exactly one place's range, so each entry has one writer)
     const int64_t I = item_start[R];
+    int lg_g = 4;
+    while (((int64_t)kGuide << lg_g) < I) lg_g++;
+    for (int a = tid; a < R; a += blockDim.x) {
+        const int64_t s0 = item_start[a], s1 = item_start[a + 1];
+        for (int64_t g = (s0 + (1 << lg_g) - 1) >> lg_g; (g << lg_g) < s1; g++) guide[g] = a;
+    }
+    __syncthreads();
+
+    // ---- 2. work items, claimed in plan order ----
     const bool aligned = ((uintptr_t)P.text & 15u) == 0;
     const bool out_aligned = ((uintptr_t)P.out & 15u) == 0;
     const uint64_t pol = policy_evict_first();
@@ -510,7 +523,8 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
     // items shares its first item with the next place), its chunk from shared memory,
     // and its read's bounds and table loaded for later
     auto locate = [&](int64_t it) {
-        int a = 0, b = R - 1;
+        const int64_t g = it >> lg_g;
+        int a = guide[g], b = ((g + 1) << lg_g) < I ? guide[g + 1] : R - 1;
         while (a < b) {
             const int mid = (a + b + 1) >> 1;
             if ((int64_t)item_start[mid] <= it) a = mid;
@@ -574,14 +588,15 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
             const uint8_t *buf = mybuf + k * kBuf;
             // 16 bytes from byte `o` of the item: from the warp's buffer, or from the text
             auto word = [&](int o, uint32_t *bad16) -> uint32_t {
-                if (aligned) return pack16(lds_v4(buf + o), bad16);
+                if (aligned) return pack16_scan(lds_v4(buf + o), bad16);
                 return ascii16(P.text, P.n, cbase + o, false, bad16);
             };
             uint32_t x0, x1, x2, x3, b0, b1, b2, b3;
             if constexpr (LW == 16) {
                 uint32_t h = 0, hb = 0xFFFFu;
                 x0 = word(16 * lane, &b0);
-                if (lane < 3) h = word(kItem + 16 * lane, &hb);
+                // the bases after the item, unless the read ends within it
+                if (cbase + kItem < re && lane < 3) h = word(kItem + 16 * lane, &hb);
                 const uint32_t d1 = __shfl_down_sync(kFull, x0, 1), e1 = __shfl_down_sync(kFull, b0, 1);
                 const uint32_t d2 = __shfl_down_sync(kFull, x0, 2), e2 = __shfl_down_sync(kFull, b0, 2);
                 const uint32_t d3 = __shfl_down_sync(kFull, x0, 3), e3 = __shfl_down_sync(kFull, b0, 3);
@@ -598,7 +613,7 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
                 uint32_t h0 = 0, h1 = 0, hb0 = 0xFFFFu, hb1 = 0xFFFFu;
                 x0 = word(32 * lane, &b0);
                 x1 = word(32 * lane + 16, &b1);
-                if (lane == 0) {
+                if (cbase + kItem < re && lane == 0) {
                     h0 = word(kItem, &hb0);
                     h1 = word(kItem + 16, &hb1);
                 }

@@ -142,6 +142,31 @@ __device__ __forceinline__ uint32_t pack4(uint32_t x, uint32_t *bad4)
     return ((t & ~((nz >> 7) * 0xFFu)) * 0x01041040u) >> 24;
 }
 
+// Four ASCII bytes -> four 2-bit codes and the 4-bit mask of bytes outside ACGT, as
+// pack4, except that the code of such a byte is left as the arithmetic gives it: for
+// scans, which never read a code at a position the mask marks (walks stop before it and
+// the filter bits of windows that contain it are masked off).
+__device__ __forceinline__ uint32_t pack4_scan(uint32_t x, uint32_t *bad4)
+{
+    const uint32_t t = ((x >> 1) & 0x03030303u) ^ ((x >> 2) & 0x01010101u);
+    const uint32_t c8 = (t * 0x01041040u) >> 24;
+    const uint32_t y = (c8 | (c8 << 4)) & 0x0F0Fu;
+    const uint32_t sel = (y | (y << 2)) & 0x3333u;
+    const uint32_t diff = x ^ __byte_perm(0x54474341u, 0u, sel);
+    const uint32_t nz = (((diff & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | diff) & 0x80808080u;
+    *bad4 = (nz * 0x00204081u) >> 28;
+    return c8;
+}
+
+__device__ __forceinline__ uint32_t pack16_scan(uint4 v, uint32_t *bad16)
+{
+    uint32_t b0, b1, b2, b3;
+    const uint32_t c0 = pack4_scan(v.x, &b0), c1 = pack4_scan(v.y, &b1), c2 = pack4_scan(v.z, &b2),
+                   c3 = pack4_scan(v.w, &b3);
+    *bad16 = b0 | (b1 << 4) | (b2 << 8) | (b3 << 12);
+    return c0 | (c1 << 8) | (c2 << 16) | (c3 << 24);
+}
+
 // Sixteen ASCII bytes -> one packed word, plus a 16-bit mask of invalid bytes.
 __device__ __forceinline__ uint32_t pack16(uint4 v, uint32_t *bad16)
 {
@@ -376,6 +401,15 @@ __device__ __forceinline__ uint32_t filter_bits(const DeviceTable &T, const uint
             const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
             const uint32_t word = *reinterpret_cast<const uint32_t *>(fb + ((win >> 3) & amask));
             pend = __funnelshift_l(__funnelshift_l(word, word, win), pend, 1);
+        }
+    } else if (!FSMEM && bmask >= 31u) {
+        // global memory, words as stored: a left rotate by 31 - (w mod 32), the window's
+        // complement taken as it is, brings the bit of b-mer w to the top
+#pragma unroll
+        for (int j = LW - 1; j >= 0; j--) {
+            const uint32_t win = j < 16 ? __funnelshift_r(x0, x1, 2 * j) : __funnelshift_r(x1, x2, 2 * (j - 16));
+            const uint32_t word = __ldg(T.filter + ((win & bmask) >> 5));
+            pend = __funnelshift_l(__funnelshift_l(word, word, ~win), pend, 1);
         }
     } else {
 #pragma unroll
