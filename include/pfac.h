@@ -366,7 +366,7 @@ int pfac_match_all(pfac_handle h, const uint32_t *d_packed, int64_t n_bases,
  * Walks never cross a read's end; bytes outside ACGT end walks as in pfac_match. A
  * read_set entry outside [0, n_sets) records PFAC_ERR_INVALID_ARG in the device status
  * of sets[0] and leaves that read's output unwritten.
- * Up to 8,192 reads (6,144 with lane_offsets = 32) the call is ONE kernel launch on
+ * Up to 8,192 reads the call is ONE kernel launch on
  * `stream`: every CTA plans the batch in shared memory (reads grouped by table), scans
  * the work items dealt to it straight from the ASCII bytes, and finishes the few long
  * walks its items deferred. Larger batches take four launches (pack the text, plan the

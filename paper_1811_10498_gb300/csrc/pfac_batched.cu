@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256) batched_tail_kernel(const BatchParams P)
 }
 
 // ---------------------------------------------------------------------------
-// Fused batched pass (batches of up to fused_max_reads reads): ONE launch, one CTA per
+// Fused batched pass (batches of up to kFusedMaxReads reads): ONE launch, one CTA per
 // SM, no packed copy of the text, no planning or tail launch.
 //   1. Every CTA plans the whole batch in shared memory, and every CTA gets the same
 //      plan: the reads are ordered by table bucket (table index mod kFusedBuckets) by a
@@ -292,23 +292,28 @@ struct FusedParams {
     int32_t walk_loads;
 };
 
-// Reads one fused launch plans in shared memory, for LW offsets per lane.
-static int32_t fused_max_reads(int lw) { return lw == 32 ? 6144 : 8192; }
+// Reads one fused launch plans in shared memory.
+constexpr int32_t kFusedMaxReads = 8192;
 
 // Bytes of one warp's text buffer: a work item and the 64 bases after it.
 template <int LW>
 __host__ __device__ constexpr int fused_buf_bytes() { return 32 * LW + 64; }
 
 // Shared memory of the fused kernel for `warps` warps per CTA, n_reads reads and LW
-// offsets per lane: the plan's per-(bucket, warp) read counts and item sums, the scan's
-// warp totals, the deferred-walk and claim counts, the guide to the sorted places, two
-// text buffers per warp, and per read its sorted place, first item, item count, first
-// chunk and bucket.
+// offsets per lane. Kept throughout: the deferred-walk and claim counts, the guide to the
+// sorted places, and per read its sorted place, first item and first chunk. Then one
+// region that first holds what only the plan uses (per-(bucket, warp) read counts and
+// item sums, the scan's warp totals, per read its item count and bucket) and then the
+// two text buffers of every warp.
+static size_t fused_plan_bytes(int warps, size_t r16)
+{
+    return (size_t)(warps + 1) * kFusedBuckets * 4 * 2 + 32 * 8 + r16 * 4 + r16;
+}
 static size_t fused_smem_bytes(int warps, int32_t n_reads, int lw)
 {
     const size_t r16 = ((size_t)n_reads + 4) / 4 * 4;   // n_reads + 1 entries, rounded to 16 bytes
-    return (size_t)(warps + 1) * kFusedBuckets * 4 * 2 + 32 * 8 + 16 + (kGuide + 4) * 4 +
-           (size_t)warps * 2 * (32 * lw + 64) + r16 * 4 * 4 + r16;
+    return 16 + (kGuide + 4) * 4 + r16 * 4 * 3 +
+           std::max(fused_plan_bytes(warps, r16), (size_t)warps * 2 * (32 * lw + 64));
 }
 
 // Sixteen ASCII bytes from position p of the text (bases at or past n are bad).
@@ -367,18 +372,21 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
     // per-(bucket, warp) counts at bucket * (W + 1) + warp: the lanes of a warp, each
     // adding to its own bucket, meet different banks
     const int WP = W + 1;
-    uint32_t *cnt_reads = reinterpret_cast<uint32_t *>(smem);                         // [bucket][W + 1]
-    uint32_t *cnt_items = cnt_reads + WP * kFusedBuckets;                             // [bucket][W + 1]
-    unsigned long long *wsum = reinterpret_cast<unsigned long long *>(cnt_items + WP * kFusedBuckets);   // [32]
-    unsigned long long *dcount = wsum + 32;                                           // deferred walks
+    unsigned long long *dcount = reinterpret_cast<unsigned long long *>(smem);       // deferred walks
     unsigned int *claimed = reinterpret_cast<unsigned int *>(dcount + 1);             // items claimed
     int32_t *guide = reinterpret_cast<int32_t *>(dcount + 2);                         // [kGuide + 4]
-    uint8_t *tbuf = reinterpret_cast<uint8_t *>(guide + kGuide + 4);                  // [warp][2][kBuf]
-    int32_t *sorted_read = reinterpret_cast<int32_t *>(tbuf + (size_t)W * 2 * kBuf); // [R]
+    int32_t *sorted_read = guide + kGuide + 4;                                        // [R]
     int32_t *item_start = sorted_read + R16;                                          // [R + 1]
-    int32_t *read_items = item_start + R16;                                           // [R]
-    int32_t *read_chunk = read_items + R16;                                           // [R]
-    uint8_t *read_bucket = reinterpret_cast<uint8_t *>(read_chunk + R16);             // [R]
+    int32_t *read_chunk = item_start + R16;                                           // [R]
+    uint8_t *region = reinterpret_cast<uint8_t *>(read_chunk + R16);
+    // the plan's scratch ...
+    uint32_t *cnt_reads = reinterpret_cast<uint32_t *>(region);                       // [bucket][W + 1]
+    uint32_t *cnt_items = cnt_reads + WP * kFusedBuckets;                             // [bucket][W + 1]
+    unsigned long long *wsum = reinterpret_cast<unsigned long long *>(cnt_items + WP * kFusedBuckets);   // [32]
+    int32_t *read_items = reinterpret_cast<int32_t *>(wsum + 32);                     // [R]
+    uint8_t *read_bucket = reinterpret_cast<uint8_t *>(read_items + R16);             // [R]
+    // ... and then the text buffers, once the plan is done
+    uint8_t *tbuf = region;                                                           // [warp][2][kBuf]
 
     // ---- 1. the plan ----
     for (int i = tid; i < 2 * WP * kFusedBuckets; i += blockDim.x) cnt_reads[i] = 0;
@@ -692,7 +700,7 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
     DeferItem *defer = (DeferItem *)p;
     const int64_t fused_items_max = n / (32 * lw) + (int64_t)n_reads + 1;
     const int fused_threads = 256 * std::min(4, blocks_per_sm);
-    if (n_reads <= fused_max_reads(lw) && fused_items_max < (1LL << 30) &&
+    if (n_reads <= kFusedMaxReads && fused_items_max < (1LL << 30) &&
         fused_smem_bytes(fused_threads / 32, n_reads, lw) <= (size_t)dp.smem_optin) {
         // one launch: every CTA plans the batch, scans the items dealt to it and finishes
         // the walks its items deferred
@@ -707,7 +715,7 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
             if (!d) {
                 const void *kern =
                     lw == 32 ? (const void *)fused_batched_kernel<32> : (const void *)fused_batched_kernel<16>;
-                const size_t most = std::min<size_t>(fused_smem_bytes(32, fused_max_reads(lw), lw), dp.smem_optin);
+                const size_t most = std::min<size_t>(fused_smem_bytes(32, kFusedMaxReads, lw), dp.smem_optin);
                 if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) != cudaSuccess)
                     return PFAC_ERR_CUDA;
                 d = true;
@@ -724,7 +732,7 @@ int launch_batched(const DeviceTable *d_sets, int32_t n_sets, const uint8_t *tex
         F.out = out;
         F.defer = defer;
         F.defer_per_cta = std::max<int64_t>(1, defer_cap / dp.num_sms);
-        F.walk_loads = bc.walk_loads > 0 ? bc.walk_loads : 2;
+        F.walk_loads = bc.walk_loads > 0 ? bc.walk_loads : 4;   // measured best on the batched workload
         if (lw == 32) fused_batched_kernel<32><<<dp.num_sms, fused_threads, smem, st>>>(F);
         else fused_batched_kernel<16><<<dp.num_sms, fused_threads, smem, st>>>(F);
         return cudaGetLastError() == cudaSuccess ? PFAC_OK : PFAC_ERR_CUDA;
