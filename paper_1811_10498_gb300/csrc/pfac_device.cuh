@@ -142,28 +142,38 @@ __device__ __forceinline__ uint32_t pack4(uint32_t x, uint32_t *bad4)
     return ((t & ~((nz >> 7) * 0xFFu)) * 0x01041040u) >> 24;
 }
 
-// Four ASCII bytes -> four 2-bit codes and the 4-bit mask of bytes outside ACGT, as
-// pack4, except that the code of such a byte is left as the arithmetic gives it: for
-// scans, which never read a code at a position the mask marks (walks stop before it and
-// the filter bits of windows that contain it are masked off).
-__device__ __forceinline__ uint32_t pack4_scan(uint32_t x, uint32_t *bad4)
+// Four bytes' codes (c8, as in pack4) and the XOR of the bytes with the bases those
+// codes stand for: zero exactly in the bytes that are A, C, G or T. Unlike pack4, the
+// code of a byte outside ACGT is left as the arithmetic gives it: scans never read a
+// code at a position their mask marks (walks stop before it, and the filter bits of
+// windows that contain it are masked off).
+__device__ __forceinline__ uint32_t codes4(uint32_t x, uint32_t *diff)
 {
     const uint32_t t = ((x >> 1) & 0x03030303u) ^ ((x >> 2) & 0x01010101u);
     const uint32_t c8 = (t * 0x01041040u) >> 24;
     const uint32_t y = (c8 | (c8 << 4)) & 0x0F0Fu;
     const uint32_t sel = (y | (y << 2)) & 0x3333u;
-    const uint32_t diff = x ^ __byte_perm(0x54474341u, 0u, sel);
-    const uint32_t nz = (((diff & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | diff) & 0x80808080u;
-    *bad4 = (nz * 0x00204081u) >> 28;
+    *diff = x ^ __byte_perm(0x54474341u, 0u, sel);
     return c8;
 }
 
+// The 4-bit mask of the nonzero bytes of d.
+__device__ __forceinline__ uint32_t nonzero_bytes4(uint32_t d)
+{
+    const uint32_t nz = (((d & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | d) & 0x80808080u;
+    return (nz * 0x00204081u) >> 28;
+}
+
+// pack16 for scans (codes as codes4 leaves them); the per-byte mask is worked out only
+// when some byte of the sixteen is not a base.
 __device__ __forceinline__ uint32_t pack16_scan(uint4 v, uint32_t *bad16)
 {
-    uint32_t b0, b1, b2, b3;
-    const uint32_t c0 = pack4_scan(v.x, &b0), c1 = pack4_scan(v.y, &b1), c2 = pack4_scan(v.z, &b2),
-                   c3 = pack4_scan(v.w, &b3);
-    *bad16 = b0 | (b1 << 4) | (b2 << 8) | (b3 << 12);
+    uint32_t d0, d1, d2, d3;
+    const uint32_t c0 = codes4(v.x, &d0), c1 = codes4(v.y, &d1), c2 = codes4(v.z, &d2), c3 = codes4(v.w, &d3);
+    uint32_t b = 0;
+    if (d0 | d1 | d2 | d3)
+        b = nonzero_bytes4(d0) | (nonzero_bytes4(d1) << 4) | (nonzero_bytes4(d2) << 8) | (nonzero_bytes4(d3) << 12);
+    *bad16 = b;
     return c0 | (c1 << 8) | (c2 << 16) | (c3 << 24);
 }
 
