@@ -1,7 +1,7 @@
 // Hardware ceilings that decide the scan kernels' design (bench.py --suite ceilings):
 //   * store bandwidth for 1 GiB of int32 output: memset, 16-byte stores from grids of
-//     several shapes (with and without an evict-first L2 hint), and TMA bulk stores of a
-//     zero tile in shared memory issued by one lane per warp;
+//     several shapes (with and without an evict-first L2 hint), 32-byte stores, and TMA
+//     bulk stores of a zero tile in shared memory issued by one lane per warp;
 //   * random 4-byte lookup rates: global memory over buffers of 128 KB to 512 MB (L1, L2
 //     and HBM resident), local shared memory, and distributed shared memory of thread-block
 //     clusters of 2 to 16 CTAs (each CTA holds 128 KB; every lookup goes to a random CTA
@@ -30,6 +30,13 @@ __global__ void store_hint(int4 *out, int64_t n4)
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
         asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %1, %1, %1}, %2;" ::"l"(out + i), "r"(0), "l"(pol) : "memory");
+}
+
+// 32-byte stores (st.global.v8.b32), one per thread-iteration.
+__global__ void store_v8(int4 *out, int64_t n8)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n8; i += (int64_t)gridDim.x * blockDim.x)
+        asm volatile("st.global.v8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"l"(out + 2 * i), "r"(0) : "memory");
 }
 
 // One elected lane per warp issues bulk stores of `chunk` bytes from a zero buffer.
@@ -167,6 +174,10 @@ int main()
     printf("{\"test\": \"store\", \"kind\": \"v4 evict_first\", \"blocks_per_sm\": 8, \"threads\": 256, \"ms\": %.4f, \"gbs\": %.0f}\n", ms, gbs(ms));
     ms = time_ms([&] { store_hint<<<sms, 1024>>>((int4 *)out, n / 4); });
     printf("{\"test\": \"store\", \"kind\": \"v4 evict_first\", \"blocks_per_sm\": 1, \"threads\": 1024, \"ms\": %.4f, \"gbs\": %.0f}\n", ms, gbs(ms));
+    for (int blocks_per_sm : {2, 8}) {
+        ms = time_ms([&] { store_v8<<<sms * blocks_per_sm, 256>>>((int4 *)out, n / 8); });
+        printf("{\"test\": \"store\", \"kind\": \"v8\", \"blocks_per_sm\": %d, \"threads\": 256, \"ms\": %.4f, \"gbs\": %.0f}\n", blocks_per_sm, ms, gbs(ms));
+    }
     for (int chunk : {4096, 16384}) {
         CK(cudaFuncSetAttribute(store_bulk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, chunk));
         CK(cudaFuncSetAttribute(store_bulk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, chunk));
