@@ -672,11 +672,13 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
     if (warp == P.consumers) {
         // ---------------- producer warp ----------------
         if (lane == 0) {
-            int k = 0;
-            for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, k++) {
-                const int st = k % S;
-                if (k >= S && !wait_or_abort(smem_addr(&empty[st]), (uint32_t)(((k / S) - 1) & 1), P.timeout_ns,
-                                             abort_flag))
+            // tile k goes to stage st = k mod S in the phase ph = (k / S) mod 2 of that
+            // stage, both kept by counting (no division per tile)
+            int k = 0, st = 0;
+            uint32_t ph = 0;
+            for (int64_t t = blockIdx.x; t < P.n_tiles;
+                 t += gridDim.x, k++, ph ^= (st + 1 == S) ? 1u : 0u, st = (st + 1 == S) ? 0 : st + 1) {
+                if (k >= S && !wait_or_abort(smem_addr(&empty[st]), ph ^ 1u, P.timeout_ns, abort_flag))
                     break;
                 const int64_t u0 = t * tile_units;
                 const int64_t cnt = min((int64_t)P.stage_units, P.n_units - u0);
@@ -713,10 +715,11 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const ScanParams P)
     const uint32_t bmask = (uint32_t)((1ull << (2 * B)) - 1ull);
     volatile uint32_t *queue = reinterpret_cast<volatile uint32_t *>(smem + P.off_queue) + warp * kQueue;
     uint32_t qhead = 0, qcount = 0;   // warp-uniform
-    int k = 0;
-    for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, k++) {
-        const int st = k % S;
-        if (!wait_or_abort(smem_addr(&full[st]), (uint32_t)((k / S) & 1), P.timeout_ns, abort_flag)) {
+    int k = 0, st = 0;
+    uint32_t ph = 0;   // stage k mod S and its phase (k / S) mod 2, kept by counting
+    for (int64_t t = blockIdx.x; t < P.n_tiles;
+         t += gridDim.x, k++, ph ^= (st + 1 == S) ? 1u : 0u, st = (st + 1 == S) ? 0 : st + 1) {
+        if (!wait_or_abort(smem_addr(&full[st]), ph, P.timeout_ns, abort_flag)) {
             if (lane == 0) {
                 record_error(T.status, PFAC_ERR_TIMEOUT);
                 if (ZW == 3) bulk_wait_all();
