@@ -538,9 +538,9 @@ def paper_suite(args):
 def large_suite(args):
     """The large-dictionary workload at `--n-bases` bases (10^6 patterns of 16-64 bases),
     scanned `--steps` times (dense ids, L2 flushed before each), with the table built
-    the default way (order-14 filter, sampled 13-gram screen) or as round 1 built it
-    (`--large-structure order12`: order-12 filter behind the order-10 first-level
-    filter). One JSON line."""
+    the default way (order-14 filter, sampled 13-gram screen) or in the earlier
+    structure (`--large-structure order12`: order-12 filter behind the order-10
+    first-level filter). One JSON line."""
     import torch
     from paper_1811_10498_gb300 import _binding as b
     from paper_1811_10498_gb300 import build_ext, datagen
