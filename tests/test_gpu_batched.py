@@ -226,3 +226,32 @@ def test_more_reads_than_one_launch_plans():
     assert (want != 0).sum() > 100
     for t in tables:
         t.close()
+
+
+@pytest.mark.parametrize("lane_offsets", [16, 32])
+def test_most_reads_one_launch_plans(lane_offsets):
+    """8,192 reads, the most one launch plans in shared memory (its largest shared-memory
+    layout), with empty and one-base reads among them: the oracle's ids."""
+    rng = datagen.rng_for(91)
+    src = datagen.iid_text(1 << 18, rng)
+    pats = [src[s0:s0 + 16].tobytes() for s0 in rng.integers(0, src.size - 16, 300)]
+    sets = [pats[:200], pats[100:], [b"ACGTACGTAC", b"TTTT"]]
+    tables = [b.Table(s) for s in sets]
+    lens = rng.integers(0, 200, 8192)
+    lens[::97] = 0
+    lens[5::101] = 1
+    offs = np.zeros(lens.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=offs[1:])
+    starts = rng.integers(0, src.size - 200, lens.size)
+    reads = np.concatenate([src[s0:s0 + L] for s0, L in zip(starts, lens)]).astype(np.uint8)
+    read_set = rng.integers(0, len(sets), lens.size).astype(np.int32)
+    want = oracle.pfac_scan_reads(reads, offs, read_set, sets)
+    b.pfac_set_config(tables[0].h, {"lane_offsets": lane_offsets})
+    try:
+        got = run_batched(tables, reads, offs, read_set)
+    finally:
+        b.pfac_set_config(tables[0].h, None)
+    assert np.array_equal(got, want), first_diff(got, want)
+    assert (want != 0).sum() > 100
+    for t in tables:
+        t.close()
