@@ -299,6 +299,13 @@ constexpr int32_t kFusedMaxReads = 8192;
 template <int LW>
 __host__ __device__ constexpr int fused_buf_bytes() { return 32 * LW + 64; }
 
+// Bytes of one warp buffer slot: the text buffer, then a copy of the item's table
+// descriptor (16-byte aligned, copied with cp.async ahead of its use).
+constexpr int kTableCopy = (int)sizeof(DeviceTable);
+static_assert(kTableCopy % 16 == 0, "table descriptors are copied in whole 16-byte pieces");
+template <int LW>
+__host__ __device__ constexpr int fused_slot_bytes() { return fused_buf_bytes<LW>() + kTableCopy; }
+
 // Shared memory of the fused kernel for `warps` warps per CTA, n_reads reads and LW
 // offsets per lane. Kept throughout: the deferred-walk and claim counts, the guide to the
 // sorted places, and per read its sorted place, first item and first chunk. Then one
@@ -313,7 +320,7 @@ static size_t fused_smem_bytes(int warps, int32_t n_reads, int lw)
 {
     const size_t r16 = ((size_t)n_reads + 4) / 4 * 4;   // n_reads + 1 entries, rounded to 16 bytes
     return 16 + (kGuide + 4) * 4 + r16 * 4 * 3 +
-           std::max(fused_plan_bytes(warps, r16), (size_t)warps * 2 * (32 * lw + 64));
+           std::max(fused_plan_bytes(warps, r16), (size_t)warps * 2 * (32 * lw + 64 + kTableCopy));
 }
 
 // Sixteen ASCII bytes from position p of the text (bases at or past n are bad).
@@ -363,6 +370,7 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
     constexpr int kItem = 32 * LW;
     constexpr int kShift = LW == 32 ? 10 : 9;
     constexpr int kBuf = fused_buf_bytes<LW>();
+    constexpr int kSlot = fused_slot_bytes<LW>();
     constexpr uint32_t kFull = 0xFFFFFFFFu;
     extern __shared__ __align__(16) uint8_t smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -386,7 +394,7 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
     int32_t *read_items = reinterpret_cast<int32_t *>(wsum + 32);                     // [R]
     uint8_t *read_bucket = reinterpret_cast<uint8_t *>(read_items + R16);             // [R]
     // ... and then the text buffers, once the plan is done
-    uint8_t *tbuf = region;                                                           // [warp][2][kBuf]
+    uint8_t *tbuf = region;                                                           // [warp][2][kSlot]
 
     // ---- 1. the plan ----
     for (int i = tid; i < 2 * WP * kFusedBuckets; i += blockDim.x) cnt_reads[i] = 0;
@@ -526,7 +534,7 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
     K.defer = P.defer + (int64_t)blockIdx.x * P.defer_per_cta;
     K.defer_cap = P.defer_per_cta;
     K.defer_count = dcount;
-    uint8_t *mybuf = tbuf + (size_t)warp * 2 * kBuf;
+    uint8_t *mybuf = tbuf + (size_t)warp * 2 * kSlot;
     // work item `it`: the last sorted place whose first item is <= it (a read with no
     // items shares its first item with the next place), its chunk from shared memory,
     // and its read's bounds and table loaded for later
@@ -548,7 +556,7 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
     };
     // start copying the bytes of the item at `cbase`, and the 64 after it, into buffer b
     auto fetch = [&](int64_t cbase, int b) {
-        const uint32_t dst = smem_addr(mybuf + b * kBuf);
+        const uint32_t dst = smem_addr(mybuf + b * kSlot);
         for (int c = lane; c < kBuf / 16; c += 32) {
             const int64_t p = cbase + 16 * c;
             const int64_t left = P.n - p;
@@ -568,9 +576,18 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
     int64_t it = item_of(__shfl_sync(kFull, pending, 0));
     if (lane == 0) pending = atomicAdd(claimed, 1u);
     FusedItem cur{};
+    // start copying the table descriptor of an item into slot b (one group; empty for a
+    // table index outside the set list)
+    auto fetch_table = [&](int32_t set, int b) {
+        if (set >= 0 && set < P.n_sets && lane < kTableCopy / 16)
+            cp_async16(smem_addr(mybuf + b * kSlot + kBuf) + 16 * lane,
+                       reinterpret_cast<const uint8_t *>(P.sets + set) + 16 * lane, 16);
+        cp_async_commit();
+    };
     if (it < I) {
         cur = locate(it);
         if (aligned) fetch(cur.base, 0);
+        fetch_table(cur.set, 0);
     }
     for (int k = 0; it < I; k ^= 1) {
         const int64_t nxt = item_of(__shfl_sync(kFull, pending, 0));
@@ -581,19 +598,18 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
             nx = locate(nxt);
             if (aligned) fetch(nx.base, k ^ 1);
         }
-        if (aligned) {
-            if (more) cp_async_wait<1>();
-            else cp_async_wait<0>();
-            __syncwarp();
-        }
+        // everything but the next item's text: this item's text and table descriptor
+        if (aligned && more) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncwarp();
         if (cur.set < 0 || cur.set >= P.n_sets) {
             if (lane == 0) record_error(P.sets[0].status, PFAC_ERR_INVALID_ARG);
         } else {
-            const DeviceTable T = P.sets[cur.set];
+            const DeviceTable &T = *reinterpret_cast<const DeviceTable *>(mybuf + k * kSlot + kBuf);
             const int64_t cbase = cur.base;
             const int64_t rs = min(max(cur.lo, (int64_t)0), P.n), re = min(max(cur.hi, rs), P.n);
             const int64_t p0 = cbase + (int64_t)LW * lane;
-            const uint8_t *buf = mybuf + k * kBuf;
+            const uint8_t *buf = mybuf + k * kSlot;
             // 16 bytes from byte `o` of the item: from the warp's buffer, or from the text
             auto word = [&](int o, uint32_t *bad16) -> uint32_t {
                 if (aligned) return pack16_scan(lds_v4(buf + o), bad16);
@@ -648,8 +664,10 @@ __global__ void __launch_bounds__(1024, 1) fused_batched_kernel(const FusedParam
                                                            P.text, nullptr, re, cbase, lane, x0, x1, x2, x3, bad,
                                                            valid, out_aligned, pol);
         }
-        // the buffer just read is the one the next fetch fills
+        // the slot just read is the one the next fetches fill; the next item's table
+        // descriptor is fetched now, its table index long loaded
         __syncwarp();
+        if (more) fetch_table(nx.set, k ^ 1);
         it = nxt;
         cur = nx;
     }
