@@ -267,9 +267,10 @@ __global__ void __launch_bounds__(256) batched_tail_kernel(const BatchParams P)
 //      issued one item ahead. An SM's warps thus work on one or two runs at a time, mostly
 //      of one table, whose filter words stay in its L1, and every CTA gets a sample of
 //      every table's items, so that the CTAs' loads even out. A warp copies the
-//      next item's bytes (and the 64 after them) into shared memory with cp.async while
-//      it scans the current one; each lane packs its own 16 bytes and takes the rest of
-//      its 64-base window by shuffles, as kernel 2 does for ASCII text.
+//      next item's bytes (and the 64 after them) and its table's descriptor into shared
+//      memory with cp.async while it scans the current one; each lane packs its own 16
+//      bytes and takes the rest of its 64-base window by shuffles, as kernel 2 does for
+//      ASCII text.
 //   3. After a block barrier the CTA finishes the long walks its items deferred, kept in
 //      its own slice of the deferred-walk list.
 // ---------------------------------------------------------------------------
@@ -311,7 +312,7 @@ __host__ __device__ constexpr int fused_slot_bytes() { return fused_buf_bytes<LW
 // sorted places, and per read its sorted place, first item and first chunk. Then one
 // region that first holds what only the plan uses (per-(bucket, warp) read counts and
 // item sums, the scan's warp totals, per read its item count and bucket) and then the
-// two text buffers of every warp.
+// two buffer slots (text and table descriptor) of every warp.
 static size_t fused_plan_bytes(int warps, size_t r16)
 {
     return (size_t)(warps + 1) * kFusedBuckets * 4 * 2 + 32 * 8 + r16 * 4 + r16;
